@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle to things other than itself (CPU only, no GPU).
+
+* brute force: Python-loop filter / nested-loop join / dict group-by on tiny random inputs;
+* closed forms: a fact table with fk = i mod M, pred = i mod 100, val = i joined to a dim with
+  pk = j, grp = j mod G has arithmetic-series aggregates per group;
+* invariants: |filter| = #{pred < t}; join cardinality = sum over keys of
+  count_probe(k) * count_build(k); sum of COUNT = join cardinality; sum of SUM = the filtered
+  matched total; COUNT*MIN <= SUM <= COUNT*MAX;
+* special cases: empty tables, t = 0, no key in the dim, a single group (plain Python
+  sum / min / max / len), composite keys against Python tuples;
+* planted mistakes: each check is run against a deliberately broken copy of the oracle and must
+  fail, so a dropped term, a flipped comparison or a swapped operand cannot pass unseen.
+"""
+import types
+from collections import Counter
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+# ----------------------------------------------------------------------------- checks
+def check_filter_brute(o, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(0, 400))
+    col = rng.integers(-5, 6, size=n).astype(np.int32)
+    lit = int(rng.integers(-6, 7))
+    for op in O.OPS:
+        assert np.array_equal(o.filter_rows(col, op, lit), O.filter_rows_loop(col, op, lit)), op
+
+
+def check_filter_closed_form(o):
+    for n in (0, 1, 99, 100, 101, 12345):
+        pred = (np.arange(n) % 100).astype(np.int32)
+        for t in (0, 1, 50, 99, 100):
+            ids = o.filter_rows(pred, "lt", t)
+            want = (n // 100) * t + min(n % 100, t)
+            assert ids.size == want
+            assert np.all(np.diff(ids.astype(np.int64)) > 0)
+            assert np.all(pred[ids] < t)
+
+
+def check_join_brute(o, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(0, 2000))
+    m = int(rng.integers(0, 300))
+    dom = int(rng.integers(1, 60))
+    pk = rng.integers(-dom // 2, dom, size=n).astype(np.int64)
+    bk = rng.integers(-dom // 2, dom, size=m).astype(np.int64)
+    p, b = o.join_sorted(pk, bk)
+    card = sum(c * Counter(bk.tolist())[k] for k, c in Counter(pk.tolist()).items())
+    assert p.size == b.size == card
+    if card:
+        assert int(p.max()) < n and int(b.max()) < m
+    if n * m <= 60_000:
+        lp, lb = O.join_loop(pk, bk)
+        assert np.array_equal(p, lp) and np.array_equal(b, lb)
+    assert np.all(pk[p.astype(np.int64)] == bk[b.astype(np.int64)])
+
+
+def check_groupby_brute(o, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(0, 3000))
+    keys = rng.integers(-20, 40, size=n).astype(np.int64)
+    vals = rng.integers(-10**12, 10**12, size=n).astype(np.int64)
+    r = o.groupby_agg(keys, vals)
+    w = O.groupby_loop(keys, vals)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(r[c], w[c]), c
+
+
+def check_groupby_single_group(o):
+    rng = np.random.default_rng(5)
+    vals = rng.integers(0, 10**8, size=10_000).astype(np.int64)
+    r = o.groupby_agg(np.full(vals.size, 7), vals)
+    py = [int(v) for v in vals]
+    assert r["key"].tolist() == [7]
+    assert r["sum"].tolist() == [sum(py)]
+    assert r["count"].tolist() == [len(py)]
+    assert r["min"].tolist() == [min(py)] and r["max"].tolist() == [max(py)]
+
+
+def closed_form_tables(B, M, G):
+    """fact: fk = i mod M, pred = i mod 100, val = i (n = 100 B); dim: pk = j, grp = j mod G."""
+    n = 100 * B
+    i = np.arange(n)
+    fact = {"fk": (i % M).astype(np.int32), "pred": (i % 100).astype(np.int32),
+            "val": i.astype(np.int64)}
+    j = np.arange(M)
+    dim = {"pk": j.astype(np.int32), "grp": (j % G).astype(np.int32)}
+    return fact, dim
+
+
+def closed_form_result(B, G, t):
+    """With G | M and G | 100: row i = 100 b + r is in group g iff r < t and r = g (mod G).
+    Over b = 0..B-1: COUNT = B |R|, SUM = 100 |R| B(B-1)/2 + B sum(R), MIN = min R,
+    MAX = 100 (B-1) + max R, where R = {r < t : r = g mod G}."""
+    out = {"key": [], "sum": [], "count": [], "min": [], "max": []}
+    for g in range(G):
+        R = list(range(g, t, G))
+        if not R or B == 0:
+            continue
+        out["key"].append(g)
+        out["count"].append(B * len(R))
+        out["sum"].append(100 * len(R) * B * (B - 1) // 2 + B * sum(R))
+        out["min"].append(min(R))
+        out["max"].append(100 * (B - 1) + max(R))
+    return {k: np.array(v, dtype=np.int64) for k, v in out.items()}
+
+
+def check_pipeline_closed_form(o):
+    for B, M, G in ((1, 20, 4), (7, 20, 4), (30, 50, 10), (13, 100, 25), (5, 60, 1)):
+        fact, dim = closed_form_tables(B, M, G)
+        for t in (0, 1, 50, 100):
+            r = o.pipeline(fact, dim, "lt", t)
+            w = closed_form_result(B, G, t)
+            for c in ("key", "sum", "count", "min", "max"):
+                assert np.array_equal(r[c], w[c]), (B, M, G, t, c)
+
+
+def check_pipeline_invariants(o, seed):
+    rng = np.random.default_rng(seed)
+    n, m = int(rng.integers(0, 20_000)), int(rng.integers(0, 500))
+    dom = max(1, int(m * rng.uniform(0.5, 2.0)))
+    fact = {"fk": rng.integers(0, dom, size=n).astype(np.int32),
+            "pred": rng.integers(0, 100, size=n).astype(np.int32),
+            "val": rng.integers(0, 10**8, size=n).astype(np.int64)}
+    dim = {"pk": rng.integers(0, dom, size=m).astype(np.int32),   # duplicates allowed
+           "grp": rng.integers(0, 17, size=m).astype(np.int32)}
+    t = int(rng.integers(0, 101))
+    r = o.pipeline(fact, dim, "lt", t)
+    sel = fact["pred"] < t
+    cb = Counter(dim["pk"].tolist())
+    mult = np.array([cb.get(int(k), 0) for k in fact["fk"]], dtype=np.int64)
+    card = int(np.sum(mult[sel]))
+    assert int(r["count"].sum()) == card
+    assert int(r["sum"].sum()) == int(np.sum(fact["val"][sel] * mult[sel]))
+    assert np.all(r["count"] * r["min"] <= r["sum"]) and np.all(r["sum"] <= r["count"] * r["max"])
+    assert set(r["key"].tolist()) <= set(dim["grp"].tolist())
+    assert np.all(np.diff(r["key"]) > 0)
+    # against the brute-force pipeline on a prefix small enough for the nested loop
+    k = min(n, 600)
+    small = {c: v[:k] for c, v in fact.items()}
+    rs, wl = o.pipeline(small, dim, "lt", t), O.pipeline(small, dim, "lt", t, join="loop")
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(rs[c], wl[c]), c
+
+
+def check_special_cases(o):
+    fact, dim = closed_form_tables(3, 20, 4)
+    empty_dim = {"pk": np.zeros(0, np.int32), "grp": np.zeros(0, np.int32)}
+    empty_fact = {c: v[:0] for c, v in fact.items()}
+    assert o.pipeline(fact, empty_dim, "lt", 50)["key"].size == 0
+    assert o.pipeline(empty_fact, dim, "lt", 50)["key"].size == 0
+    assert o.pipeline(fact, dim, "lt", 0)["key"].size == 0
+    miss = dict(dim, pk=dim["pk"] + 1000)
+    assert o.pipeline(fact, miss, "lt", 50)["key"].size == 0
+
+
+def check_composite_and_group_keys(o, seed):
+    rng = np.random.default_rng(seed)
+    n, m = 3000, 200
+    pool = rng.integers(-2**31, 2**31, size=(40, 2)).astype(np.int64)
+    pool[0] = (-1, -1)
+    pool[1] = (-2**31, 0)
+    pool[2] = (0, -2**31)
+    pool[3] = (2**31 - 1, -1)
+    fi = rng.integers(0, 40, size=n)
+    bi = rng.integers(0, 40, size=m)
+    fact = {"fk_hi": pool[fi, 0].astype(np.int32), "fk": pool[fi, 1].astype(np.int32),
+            "pred": rng.integers(0, 100, size=n).astype(np.int32),
+            "val": rng.integers(0, 10**8, size=n).astype(np.int64)}
+    dim = {"pk_hi": pool[bi, 0].astype(np.int32), "pk": pool[bi, 1].astype(np.int32),
+           "grp": rng.integers(-3, 3, size=m).astype(np.int32),
+           "flag": rng.integers(-128, 128, size=m).astype(np.int8)}
+    r = o.pipeline(fact, dim, "lt", 60)
+    # brute force on Python tuples: join on (hi, lo), group on (grp, flag)
+    acc = {}
+    by_key = {}
+    for j in range(m):
+        by_key.setdefault((int(dim["pk_hi"][j]), int(dim["pk"][j])), []).append(j)
+    for i in range(n):
+        if fact["pred"][i] >= 60:
+            continue
+        for j in by_key.get((int(fact["fk_hi"][i]), int(fact["fk"][i])), []):
+            g = (int(dim["grp"][j]), int(dim["flag"][j]))
+            v = int(fact["val"][i])
+            a = acc.setdefault(g, [0, 0, v, v])
+            a[0] += v; a[1] += 1; a[2] = min(a[2], v); a[3] = max(a[3], v)
+    assert r["key"].size == len(acc)
+    # decode the packed group key: grp = floor(key / 256), flag = key mod 256 as a signed byte
+    for k, s, c, mn, mx in zip(r["key"], r["sum"], r["count"], r["min"], r["max"]):
+        k = int(k)
+        g = (k >> 8, ((k & 0xFF) ^ 0x80) - 0x80)
+        assert g in acc, g
+        assert acc[g] == [int(s), int(c), int(mn), int(mx)], g
+
+
+# ----------------------------------------------------------------------------- the pins
+@pytest.mark.parametrize("seed", range(60))
+def test_filter_brute(seed):
+    check_filter_brute(O, seed)
+
+
+def test_filter_closed_form():
+    check_filter_closed_form(O)
+
+
+@pytest.mark.parametrize("seed", range(220))
+def test_join_brute(seed):
+    check_join_brute(O, seed)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_groupby_brute(seed):
+    check_groupby_brute(O, seed)
+
+
+def test_groupby_single_group():
+    check_groupby_single_group(O)
+
+
+def test_groupby_exact_large_sums():
+    # sums beyond 2**53 (no float path) but inside int64
+    v = np.full(1000, 9 * 10**15, dtype=np.int64)
+    r = O.groupby_agg(np.zeros(1000, np.int64), v)
+    assert int(r["sum"][0]) == 9 * 10**18
+    with pytest.raises(OverflowError):
+        O.groupby_agg(np.zeros(1100, np.int64), np.full(1100, 9 * 10**15, dtype=np.int64))
+
+
+def test_pipeline_closed_form():
+    check_pipeline_closed_form(O)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_pipeline_invariants(seed):
+    check_pipeline_invariants(O, seed)
+
+
+def test_special_cases():
+    check_special_cases(O)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_composite_and_group_keys(seed):
+    check_composite_and_group_keys(O, seed)
+
+
+def test_merge_partials_equals_whole():
+    rng = np.random.default_rng(3)
+    keys = rng.integers(0, 50, size=5000)
+    vals = rng.integers(0, 10**8, size=5000)
+    parts = [O.groupby_agg(keys[a:a + 700], vals[a:a + 700]) for a in range(0, 5000, 700)]
+    m = O.merge_partials(parts)
+    w = O.groupby_agg(keys, vals)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(m[c], w[c])
+
+
+def test_restrict_dim_selects_groups():
+    rng = np.random.default_rng(4)
+    fact = {"fk": rng.integers(0, 300, size=20000).astype(np.int32),
+            "pred": rng.integers(0, 100, size=20000).astype(np.int32),
+            "val": rng.integers(0, 10**8, size=20000).astype(np.int64)}
+    dim = {"pk": np.arange(300, dtype=np.int32), "grp": rng.integers(0, 40, size=300).astype(np.int32)}
+    full = O.pipeline(fact, dim, "lt", 40)
+    pick = [3, 17, 39]
+    part = O.pipeline(fact, O.restrict_dim(dim, pick), "lt", 40)
+    keep = np.isin(full["key"], pick)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(part[c], full[c][keep])
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+def _mutant(**over):
+    """A copy of the oracle's public functions with some replaced by broken versions."""
+    ns = {name: getattr(O, name) for name in O.__all__}
+    m = types.SimpleNamespace(**ns)
+    for k, v in over.items():
+        setattr(m, k, v)
+    # pipeline must call the mutant's pieces, so rebuild it over the namespace
+    def pipeline(fact, dim, op="lt", literal=50, join="sorted"):
+        sel = m.filter_rows(fact["pred"], op, literal).astype(np.int64)
+        fk = O.join_key(fact, "fk", "fk_hi")[sel]
+        pk = O.join_key(dim, "pk", "pk_hi")
+        p, b = m.join_sorted(fk, pk)
+        rows = sel[p.astype(np.int64)]
+        gkey = m.pack_group(dim["grp"], dim.get("flag"))[b.astype(np.int64)]
+        return m.groupby_agg(gkey, np.asarray(fact["val"], np.int64)[rows])
+    if "pipeline" not in over:
+        m.pipeline = pipeline
+    return m
+
+
+def _le_instead_of_lt(col, op, lit):
+    return O.filter_rows(col, "le" if op == "lt" else op, lit)
+
+
+def _swapped_join(pk, bk):
+    return O.join_sorted(bk, pk)      # outputs (build ids, probe ids) in the wrong slots
+
+
+def _first_match_only(pk, bk):
+    p, b = O.join_sorted(pk, bk)
+    keep = np.ones(p.size, bool)
+    keep[1:] = p[1:] != p[:-1]
+    return p[keep], b[keep]
+
+
+def _sum_drops_last(keys, vals):
+    r = O.groupby_agg(keys, vals)
+    if len(keys):
+        r = O.groupby_agg(keys[:-1], vals[:-1]) if len(keys) > 1 else r
+    return r
+
+
+def _min_is_first(keys, vals):
+    r = O.groupby_agg(keys, vals)
+    order = np.argsort(np.asarray(keys), kind="stable")
+    k = np.asarray(keys)[order]
+    _, start = np.unique(k, return_index=True)
+    r["min"] = np.asarray(vals)[order][start]
+    return r
+
+
+def _flag_signed_shift(grp, flag=None):
+    g = np.asarray(grp, dtype=np.int64)
+    if flag is None:
+        return g
+    return g * 256 + np.asarray(flag, dtype=np.int64)   # sign-extended byte: (g, -1) == (g-1, 255)
+
+
+MUTANTS = [
+    ("filter le for lt", dict(filter_rows=_le_instead_of_lt),
+     lambda m: check_filter_closed_form(m)),
+    ("filter le for lt (pipeline)", dict(filter_rows=_le_instead_of_lt),
+     lambda m: check_pipeline_closed_form(m)),
+    ("join operands swapped", dict(join_sorted=_swapped_join),
+     lambda m: [check_join_brute(m, s) for s in range(20)]),
+    ("join keeps first match only", dict(join_sorted=_first_match_only),
+     lambda m: [check_join_brute(m, s) for s in range(20)]),
+    ("groupby drops a row", dict(groupby_agg=_sum_drops_last),
+     lambda m: check_groupby_single_group(m)),
+    ("groupby drops a row (pipeline)", dict(groupby_agg=_sum_drops_last),
+     lambda m: check_pipeline_closed_form(m)),
+    ("min is first value", dict(groupby_agg=_min_is_first),
+     lambda m: [check_groupby_brute(m, s) for s in range(5)]),
+    ("min is first value (pipeline)", dict(groupby_agg=_min_is_first),
+     lambda m: [check_pipeline_invariants(m, s) for s in range(5)]),
+    ("group flag sign-extended", dict(pack_group=_flag_signed_shift),
+     lambda m: [check_composite_and_group_keys(m, s) for s in range(3)]),
+]
+
+
+@pytest.mark.parametrize("name,over,check", MUTANTS, ids=[x[0] for x in MUTANTS])
+def test_planted_mistake_is_caught(name, over, check):
+    with pytest.raises(AssertionError):
+        check(_mutant(**over))
