@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Throughput of the fused relational pipeline (filter -> hash join -> group-by) on GB300.
+
+Default workload: the 600M-row fact / 15M-row dim star query (fk uniform over the dim keys,
+pred < 30, group by grp with 100 000 values; SUM, COUNT, MIN, MAX), seeded synthetic data
+generated on the device.  One step = one sirius_run_pipeline call: build over the dim, one
+fused filter/probe/aggregate pass over the fact table, finalize.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU: every rank runs its own query on its own
+seeded tables (independent problems: weak scaling, no data-path collective); the timed region
+is bracketed by barriers and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pipeline rows/s & HBM GB/s vs peak; batched/served vs plain; p50/p99 latency"
+WORKLOADS = ("plain_600M", "plain_600M_composite", "skewed_300M", "plain_1M")
+PROBE_SOURCES = ["paper_2508_04701_gb300/csrc/pipeline.cu", "paper_2508_04701_gb300/csrc/tables.cuh",
+                 "paper_2508_04701_gb300/csrc/common.cuh", "paper_2508_04701_gb300/csrc/pipeline.cuh"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="plain_600M", choices=WORKLOADS)
+    p.add_argument("--load-factor", type=float, default=0.0)
+    p.add_argument("--agg-mode", default="auto")
+    p.add_argument("--block-threads", type=int, default=0)
+    p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def spec_for(name: str, rank: int):
+    from paper_2508_04701_gb300 import datagen as dg
+    if name == "plain_600M":
+        return dg.plain_scale(seed=rank), 100_000
+    if name == "plain_600M_composite":
+        return dg.plain_scale(composite=True, seed=rank), 100_000
+    if name == "skewed_300M":
+        s = dg.skewed(seed=rank)
+        return s, s.m
+    if name == "plain_1M":
+        return dg.plain_small(seed=rank), 1000
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------- environment
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def probe_traffic(workload: str):
+    """Per-launch DRAM bytes of the probe kernel from the committed ncu summary, or None when
+    the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "pipe_probe_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    ent = rec.get(workload)
+    if not ent or ent.get("source_hash") != source_hash(PROBE_SOURCES):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+def cpu_baseline(spec, rows: int):
+    """The oracle as it stands, on the first `rows` fact rows against the full dim table."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_2508_04701_gb300 import datagen as dg
+    rows = min(rows, spec.n)
+    dim = dg.gen_dim_host(spec)
+    fact = dg.gen_fact_host(spec, 0, rows, dim=dim)
+    t0 = time.perf_counter()
+    res = oracle.pipeline(fact, dim, "lt", spec.t)
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} of {spec.n} fact rows of the same query against the full "
+                      f"{spec.m}-row dim table; {len(res['key'])} groups; {dt:.2f} s; numpy, one thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores for the same metric."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2508_04701_gb300 import datagen as dg
+    spec, _ = spec_for(args.workload, 0)
+    rows = min(spec.n, 2_000_000)
+    dim = dg.gen_dim_host(spec)
+    fact = dg.gen_fact_host(spec, 0, rows, dim=dim)
+    for _ in range(args.warmup):
+        oracle.pipeline(fact, dim, "lt", spec.t)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.pipeline(fact, dim, "lt", spec.t)
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    value = rows / per
+    line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "fact_rows_per_step": rows, "dim_rows": spec.m,
+                       "predicate": f"pred < {spec.t}"},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the first {rows} of {spec.n} fact rows against the "
+                                       f"full {spec.m}-row dim; numpy, one thread"},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2508_04701_gb300 import build
+    build.build()
+    from paper_2508_04701_gb300 import datagen as dg
+    from paper_2508_04701_gb300 import sirius as S
+
+    spec, hint = spec_for(args.workload, rank)
+    stream = torch.cuda.current_stream(dev)
+    dim = dg.gen_dim_device(spec, dev)
+    fact = dg.gen_fact_device(spec, dim, dev)
+    aggs = spec.aggs
+    desc = S.make_desc(fact, dim, "lt", spec.t, aggs, hint, args.load_factor, args.agg_mode,
+                       args.block_threads, args.blocks_per_sm)
+    out_cap = hint + 1
+    outs = S.PipelineOutputs(out_cap, dev)
+    scratch = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    # one synchronous run: status and group count
+    groups = S.sirius_run_pipeline(desc, outs, scratch, stream, sync=True)
+    for _ in range(max(args.warmup, 3) - 1):
+        S.sirius_run_pipeline(desc, outs, scratch, stream, sync=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    l0 = S.launch_count()
+    S.profile_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        S.sirius_run_pipeline(desc, outs, scratch, stream, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    phases = S.profile_stop()
+    launches = S.launch_count() - l0
+    barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_step = t_ms / args.steps
+    value = world * spec.n / (ms_step / 1e3)
+    status = int(outs.d_status.item())
+
+    # roofline of the dominant kernel: the fused probe pass
+    peaks, peak_kind = measured_peaks()
+    probe_ms, probe_n = phases.get("pipe_probe", (0.0, 0))
+    probe_avg_ms = probe_ms / max(probe_n, 1)
+    alg_bytes = spec.n * spec.fact_bytes_per_row
+    achieved = alg_bytes / (probe_avg_ms / 1e3) / 1e9 if probe_avg_ms > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = probe_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "pipe_probe_kernel",
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": probe_avg_ms}
+    phase_ms = {k: v[0] / max(v[1], 1) for k, v in phases.items()}
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        del fact
+        torch.cuda.empty_cache()
+        cpu = cpu_baseline(spec, args.cpu_sample_rows)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "fact_rows": spec.n, "dim_rows": spec.m,
+                       "predicate": f"pred < {spec.t}", "groups": groups, "aggregates": aggs,
+                       "fact_bytes": alg_bytes, "l2": "inputs larger than L2 (fact columns "
+                       f"{alg_bytes / 1e9:.1f} GB read once per step)",
+                       "load_factor": args.load_factor or 0.5, "agg_mode": args.agg_mode},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
+            "gpu_launches": launches, "phase_ms": phase_ms, "device_status": status,
+            "hbm_gbs_effective_step": alg_bytes / (ms_step / 1e3) / 1e9,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
+    """The same query through sirius_run_pipeline_host: fact and dim columns in pinned host
+    memory, copied to the device inside the call, results copied back."""
+    if not hasattr(S, "run_pipeline_host"):
+        return None
+    return S.bench_e2e(spec, fact, dim, hint, aggs, args.e2e_steps, dev, stream, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * sirius.h -- C ABI of the GB300 (sm_103a) relational hot path.
+ *
+ * The operators are the physical operators of a GPU-native SQL engine's pipeline (Sec. 3.2.2):
+ * a predicate filter that yields row ids, an inner hash join (build, probe) that yields row-id
+ * pairs, late materialisation of columns by row id (gather), and a hash group-by computing
+ * SUM / COUNT / MIN / MAX.  Operators are stateless; the caller (the executor) owns every
+ * buffer and pushes columns through them (push-based model, Sec. 3.2.2).  Columns are plain
+ * contiguous device arrays without validity bitmaps, passed by pointer as in an Arrow-derived
+ * columnar format (Sec. 3.2.3).  sirius_run_pipeline fuses one whole pipeline -- filter, probe,
+ * materialisation and aggregation in one pass over the fact table -- after a build over the dim
+ * table; sirius_run_pipeline_batch runs many independent pipelines in one set of launches
+ * (pipelines as tasks of a global queue, Sec. 3.2.2; batch execution, Sec. 3.4).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are device memory, h_* host memory.  The library never frees caller
+ *    memory and keeps no pointer after a call returns (hash tables live in caller memory).
+ *  - Every call is ordered on `stream` (a cudaStream_t; NULL is the legacy default stream) and
+ *    is asynchronous unless it takes a non-NULL h_* output, in which case it synchronises
+ *    `stream` before returning.
+ *  - Scratch: calls that need temporary device memory take (d_scratch, scratch_bytes).  Pass a
+ *    buffer of at least the size the matching *_scratch_bytes() query returns, 256-byte
+ *    aligned; or pass NULL to let the call allocate and free it stream-ordered
+ *    (cudaMallocAsync / cudaFreeAsync).  Two calls in flight at once must not share scratch.
+ *  - Row ids are uint32: every row count must be below 2^32 - 1 (the paper's engine uses 64-bit
+ *    row ids, Sec. 3.2.3; this library narrows them and checks the bound).
+ *  - Arithmetic is exact integer arithmetic.  SUM wraps modulo 2^64 if the true sum does not fit
+ *    int64 (the caller guarantees it fits).
+ *  - Errors: the return value is authoritative.  A call never traps or aborts the device; device
+ *    failures are reported through a status word.  sirius_last_error() returns a message for the
+ *    last failing call on the calling thread.
+ */
+#ifndef SIRIUS_H
+#define SIRIUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* sirius_stream; /* a cudaStream_t */
+
+typedef enum {
+  SIRIUS_OK = 0,
+  SIRIUS_ERR_INVALID = 1,    /* bad argument: NULL column, negative or too large size, bad enum */
+  SIRIUS_ERR_OOM = 2,        /* the call's own scratch allocation failed */
+  SIRIUS_ERR_CAPACITY = 3,   /* an output buffer is too small; the needed size is reported */
+  SIRIUS_ERR_TABLE_FULL = 4, /* a hash table ran out of slots; retry with a larger capacity */
+  SIRIUS_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up (results undefined) */
+  SIRIUS_ERR_CUDA = 6,       /* a CUDA runtime call failed; see sirius_last_error() */
+  SIRIUS_ERR_SCRATCH = 7     /* scratch buffer smaller than the *_scratch_bytes() query */
+} sirius_status;
+
+typedef enum { SIRIUS_LT = 0, SIRIUS_LE = 1, SIRIUS_GT = 2, SIRIUS_GE = 3, SIRIUS_EQ = 4,
+               SIRIUS_NE = 5 } sirius_cmp;
+
+enum { SIRIUS_AGG_SUM = 1, SIRIUS_AGG_COUNT = 2, SIRIUS_AGG_MIN = 4, SIRIUS_AGG_MAX = 8,
+       SIRIUS_AGG_ALL = 15 };
+
+/* ------------------------------------------------------------------ library */
+int32_t sirius_version(void);
+const char* sirius_last_error(void);        /* thread-local; "" when the last call succeeded */
+uint64_t sirius_launch_count(void);         /* kernels this library has launched (all threads) */
+int32_t sirius_device_sm_count(void);       /* SMs of the current device */
+
+/* Phase timing: while enabled, the library records a pair of CUDA events on the launching
+ * stream around each of its kernels, by phase.  sirius_profile_start() clears the record and
+ * enables it; sirius_profile_stop() waits for the recorded events, writes per phase the summed
+ * milliseconds (ms[p]) and launch counts (launches[p]) for p < nphases, disables recording and
+ * returns SIRIUS_OK (or SIRIUS_ERR_CUDA).  Not for use inside CUDA graph capture. */
+enum { SIRIUS_PHASE_FILTER = 0, SIRIUS_PHASE_JOIN_BUILD = 1, SIRIUS_PHASE_JOIN_PROBE = 2,
+       SIRIUS_PHASE_GATHER = 3, SIRIUS_PHASE_GROUPBY = 4, SIRIUS_PHASE_PIPE_INIT = 5,
+       SIRIUS_PHASE_PIPE_BUILD = 6, SIRIUS_PHASE_PIPE_PROBE = 7, SIRIUS_PHASE_PIPE_FINALIZE = 8,
+       SIRIUS_PHASE_BATCH_PLAN = 9, SIRIUS_PHASE_BATCH_BUILD = 10, SIRIUS_PHASE_BATCH_PROBE = 11,
+       SIRIUS_PHASE_BATCH_FINALIZE = 12, SIRIUS_PHASE_COPY = 13, SIRIUS_PHASES = 16 };
+void sirius_profile_start(void);
+sirius_status sirius_profile_stop(double* ms, int64_t* launches, int32_t nphases);
+
+/* ------------------------------------------------------------------ A2: filter
+ * Predicate filter with stream compaction (Sec. 3.2.2: predicate pushdown; Sec. 4.2: filter
+ * operator).  Writes the row ids i of d_col[0..n) with `d_col[i] <op> literal`, in ascending
+ * order (stable), to d_row_ids (capacity n), and their number to *d_count (device, nullable)
+ * and *h_count (host, nullable; synchronises).  One pass: each warp ranks its rows with
+ * ballots and popcounts, each tile finds its output offset by a decoupled look-back over the
+ * tiles before it.  Scratch: sirius_filter_scratch_bytes(n) (tile status words, zeroed by the
+ * call).  Errors: INVALID (NULL pointers with n > 0, n < 0, n >= 2^32 - 1, bad op), SCRATCH,
+ * OOM, CUDA, TIMEOUT (a look-back wait exceeded its bound). */
+size_t sirius_filter_scratch_bytes(int64_t n);
+sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t op, int32_t literal,
+                            uint32_t* d_row_ids, int64_t* d_count, int64_t* h_count,
+                            void* d_scratch, size_t scratch_bytes, sirius_stream stream);
+
+/* ------------------------------------------------------------------ A1 / A3: hash join
+ * An open-addressing hash table of the build side (Sec. 3.2.2 join operator; Sec. 4.2: joins
+ * dominate).  Keys are one int32 column or a two-column (hi, lo) int32 key compared as one
+ * 64-bit value.  Slots hold (key, build row id); linear probing from a hashed home slot;
+ * inserts claim an empty slot with one 64-bit (4-byte keys) or 128-bit (two-column keys)
+ * compare-and-swap.  Duplicate build keys are kept (a multimap) and detected during the build;
+ * a table without duplicates lets probes stop at the first match.
+ * The table lives in caller memory: d_mem of sirius_join_table_bytes(capacity, key_width)
+ * bytes, 256-byte aligned; capacity from sirius_join_table_capacity(m, load_factor) (> m). */
+typedef struct {
+  void* d_mem;         /* caller-owned device memory */
+  int64_t capacity;    /* slots; must exceed the number of build rows */
+  int32_t key_width;   /* 4 or 8 */
+  int32_t reserved;
+} sirius_join_table;
+
+int64_t sirius_join_table_capacity(int64_t m, double load_factor); /* load_factor in (0, 0.95] */
+size_t sirius_join_table_bytes(int64_t capacity, int32_t key_width);
+
+/* Build: inserts rows 0..m-1 of d_keys (low words; d_keys_hi = NULL for 4-byte keys, else the
+ * high words) with payload = row id.  Clears the table first.  Errors: INVALID (m >= capacity,
+ * key width not matching d_keys_hi, NULL memory), TABLE_FULL (cannot happen when
+ * m < capacity; reported defensively), CUDA.  h_has_dups (nullable; synchronises) receives 1
+ * if some key occurs twice. */
+sirius_status sirius_hash_join_build(const int32_t* d_keys, const int32_t* d_keys_hi, int64_t m,
+                                     sirius_join_table* table, int32_t* h_has_dups,
+                                     sirius_stream stream);
+
+/* Probe: for each i in [0, n) the probe row r = d_sel ? d_sel[i] : i with key
+ * (d_keys_hi[r], d_keys[r]) is matched against the table; every match appends the pair
+ * (r, build row id) to (d_out_probe, d_out_build) in unspecified order.  The number of pairs
+ * goes to *d_out_count / *h_out_count (synchronises).  When it exceeds out_cap only the first
+ * out_cap pairs are written and the call returns CAPACITY (h_out_count holds the size
+ * needed; with h_out_count NULL the caller checks *d_out_count > out_cap itself). */
+sirius_status sirius_hash_join_probe(const sirius_join_table* table, const int32_t* d_keys,
+                                     const int32_t* d_keys_hi, const uint32_t* d_sel, int64_t n,
+                                     uint32_t* d_out_probe, uint32_t* d_out_build, int64_t out_cap,
+                                     int64_t* d_out_count, int64_t* h_out_count,
+                                     sirius_stream stream);
+
+/* ------------------------------------------------------------------ A4: gather
+ * Late materialisation (Sec. 3.2.2 materialisation kernel): d_dst[i] = d_src[d_idx[i]].
+ * sirius_gather_group_key builds the int64 group key of build rows d_idx[i]: grp, or
+ * (grp, flag) packed as grp * 256 + (uint8)flag when d_flag is not NULL. */
+sirius_status sirius_gather_i32(const int32_t* d_src, const uint32_t* d_idx, int64_t n,
+                                int32_t* d_dst, sirius_stream stream);
+sirius_status sirius_gather_i64(const int64_t* d_src, const uint32_t* d_idx, int64_t n,
+                                int64_t* d_dst, sirius_stream stream);
+sirius_status sirius_gather_group_key(const int32_t* d_grp, const int8_t* d_flag,
+                                      const uint32_t* d_idx, int64_t n, int64_t* d_dst,
+                                      sirius_stream stream);
+
+/* ------------------------------------------------------------------ A5 / A6: group-by
+ * Hash group-by aggregation (Sec. 3.2.2; Sec. 4.2: few groups contend on memory).  Keys are
+ * int32 (key_width 4) or int64 (key_width 8); values int64.  For each distinct key: SUM,
+ * COUNT(*), MIN, MAX (those selected by `aggs`; COUNT is always computed).  Small tables are
+ * pre-aggregated per thread block in shared memory; large ones aggregate with global atomics
+ * after a warp-level combine of equal keys.  The table holds sirius_groupby_capacity(hint)
+ * slots; more distinct keys than it can take -> TABLE_FULL (retry with a larger hint).
+ * Outputs (device, out_cap each, NULL for aggregates not requested): keys, sums, counts, mins,
+ * maxs, in unspecified order; the group count G goes to *d_groups / *h_groups
+ * (synchronises).  G > out_cap -> CAPACITY with the needed G in *h_groups. */
+int64_t sirius_groupby_capacity(int64_t group_cap_hint);
+size_t sirius_groupby_scratch_bytes(int64_t group_cap_hint);
+sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_width, const int64_t* d_vals,
+                                 int64_t n, uint32_t aggs, int64_t group_cap_hint,
+                                 int64_t* d_out_keys, int64_t* d_sum, int64_t* d_count,
+                                 int64_t* d_min, int64_t* d_max, int64_t out_cap,
+                                 int64_t* d_groups, int64_t* h_groups, void* d_scratch,
+                                 size_t scratch_bytes, sirius_stream stream);
+
+/* ------------------------------------------------------------------ A7: fused pipeline
+ * SELECT g, SUM(val), COUNT(*), MIN(val), MAX(val) FROM fact JOIN dim ON fk = pk
+ * WHERE pred <op> literal GROUP BY g, with g = dim.grp or (dim.grp, dim.flag).
+ * Build phase over the dim (pipeline breaker): every dim row's group key is entered into a
+ * group table (insert-or-find), and (pk -> group slot) into a join table.  Probe phase: one
+ * pass over the fact table evaluates the predicate, probes the join table and aggregates into
+ * the group slot directly -- no intermediate row ids are materialised.  Finalize compacts the
+ * groups with at least one row.  All columns are caller device memory. */
+typedef struct {
+  /* fact (probe side), n rows */
+  const int32_t* fk;        /* join key, or its low word */
+  const int32_t* fk_hi;     /* NULL, or the high word of a two-column key */
+  const int32_t* pred;      /* filter column */
+  const int64_t* val;       /* aggregated column (fixed-point decimal as int64) */
+  int64_t n;
+  /* dim (build side), m rows */
+  const int32_t* pk;        /* join key, or its low word */
+  const int32_t* pk_hi;     /* NULL, or the high word (must match fk_hi being NULL or not) */
+  const int32_t* grp;       /* group key column */
+  const int8_t* flag;       /* NULL, or a second group key column (key = grp * 256 + (uint8)flag) */
+  int64_t m;
+  /* query */
+  int32_t op;               /* sirius_cmp */
+  int32_t literal;
+  uint32_t aggs;            /* SIRIUS_AGG_* mask (COUNT is always computed) */
+  int32_t agg_mode;         /* 0 auto, 1 shared-memory table, 2 global atomics,
+                               3 global atomics behind a per-block hot-group cache */
+  int64_t group_cap_hint;   /* expected distinct group keys in the dim; 0 -> m */
+  float load_factor;        /* join table load factor; 0 -> default 0.5 */
+  int32_t block_threads;    /* probe kernel block size; 0 -> default */
+  int32_t blocks_per_sm;    /* probe kernel residency target; 0 -> occupancy maximum */
+  int32_t reserved;
+} sirius_pipeline_desc;
+
+typedef struct {
+  int64_t* keys;            /* device outputs, out_cap entries each; NULL when not wanted */
+  int64_t* sum;
+  int64_t* count;
+  int64_t* min;
+  int64_t* max;
+  int64_t out_cap;
+  int64_t* d_groups;        /* device: receives G (nullable) */
+  int32_t* d_status;        /* device: receives the sirius_status of the device work (nullable) */
+  int32_t sync;             /* 1: synchronise and fill `groups` and `status` below */
+  int32_t status;           /* host, when sync: device-side status */
+  int64_t groups;           /* host, when sync: G */
+} sirius_result;
+
+size_t sirius_pipeline_scratch_bytes(const sirius_pipeline_desc* q);
+/* Errors: INVALID, SCRATCH, OOM, CUDA; with sync also TABLE_FULL (more distinct group keys in
+ * the dim than the group table takes: raise group_cap_hint) and CAPACITY (G > out_cap; the
+ * needed G is in result->groups). */
+sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, sirius_result* result,
+                                  void* d_scratch, size_t scratch_bytes, sirius_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIRIUS_H */

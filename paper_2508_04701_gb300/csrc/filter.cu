@@ -1,0 +1,225 @@
+// A2: predicate filter with stable stream compaction (Sec. 3.2.2 predicate pushdown; Sec. 4.2).
+//
+// One pass over the column.  A thread block owns a tile of 4096 rows (8 warps x 512 rows; a
+// lane reads four 16-byte vectors, rows 4*(lane + 32k) .. +3 of its warp's slice).  Each warp
+// ranks its selected rows with 16 ballots and popcounts; the block scans its 8 warp totals;
+// the tile's output offset comes from a decoupled look-back over the tiles before it
+// (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA
+// technical report NVR-2016-002).  Tiles take tickets from an atomic counter, so every tile a
+// look-back waits on has already started; each wait is still bounded and reports TIMEOUT.
+#include "common.cuh"
+
+namespace sirius {
+namespace {
+
+constexpr int kFilterThreads = 256;
+constexpr int kFilterK = 4;                                  // 16-byte vectors per lane
+constexpr int kWarpRows = 32 * 4 * kFilterK;                 // 512
+constexpr int kTileRows = kWarpRows * (kFilterThreads / 32);  // 4096
+constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
+constexpr int kSpinLimit = 1 << 21;
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Exclusive prefix of this tile: the sum of all earlier tiles' selected counts.  Run by one
+// whole warp; returns the same value in every lane.
+__device__ uint64_t look_back(uint64_t* status, int64_t tile, uint64_t total, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_relaxed_u64(&status[0], (total << 2) | kFlagPrefix);
+    return 0;
+  }
+  if (lane == 0) st_relaxed_u64(&status[tile], (total << 2) | kFlagAgg);
+  uint64_t excl = 0;
+  int64_t j0 = tile - 1;
+  bool timed_out = false;
+  while (true) {
+    const int64_t j = j0 - lane;
+    uint64_t w = 0;
+    int spins = 0;
+    while (true) {
+      w = (j >= 0) ? ld_relaxed_u64(&status[j]) : kFlagPrefix;
+      const bool not_ready = (w & 3) == 0;
+      if (!__any_sync(0xffffffffu, not_ready)) break;
+      if (++spins > kSpinLimit) {
+        timed_out = true;
+        break;
+      }
+      if (spins > 64) __nanosleep(256);
+    }
+    if (timed_out) break;
+    const unsigned pm = __ballot_sync(0xffffffffu, (w & 3) == kFlagPrefix);
+    const int stop = pm ? __ffs(pm) - 1 : 31;
+    excl += warp_sum_u64(lane <= stop ? (w >> 2) : 0);
+    if (pm) break;
+    j0 -= 32;
+  }
+  if (timed_out && lane == 0) set_status(err, SIRIUS_ERR_TIMEOUT);
+  if (lane == 0) st_relaxed_u64(&status[tile], ((excl + total) << 2) | kFlagPrefix);
+  return excl;
+}
+
+template <bool kVec>
+__global__ void __launch_bounds__(kFilterThreads)
+filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_t lit,
+                      uint32_t* __restrict__ out, int64_t* __restrict__ d_count,
+                      DevHeader* hdr, uint64_t* status, int64_t num_tiles) {
+  __shared__ int64_t s_tile;
+  __shared__ uint32_t s_warp_total[kFilterThreads / 32];
+  __shared__ uint64_t s_warp_excl[kFilterThreads / 32];
+  __shared__ uint64_t s_tile_excl;
+
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd((unsigned long long*)&hdr->counter, 1ull);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t warp_row0 = tile * kTileRows + (int64_t)warp * kWarpRows;
+
+  // ---- load + evaluate: bits[k] holds the 4 predicate results of vector k of this lane
+  uint32_t bits[kFilterK];
+  const bool full_tile = (tile + 1) * (int64_t)kTileRows <= n;
+  if (kVec && full_tile) {
+    const int4* p = reinterpret_cast<const int4*>(col + warp_row0);
+    int4 v[kFilterK];
+#pragma unroll
+    for (int k = 0; k < kFilterK; ++k) v[k] = __ldcs(p + lane + 32 * k);
+#pragma unroll
+    for (int k = 0; k < kFilterK; ++k)
+      bits[k] = (uint32_t)cmp_op(v[k].x, lit, op) | ((uint32_t)cmp_op(v[k].y, lit, op) << 1) |
+                ((uint32_t)cmp_op(v[k].z, lit, op) << 2) | ((uint32_t)cmp_op(v[k].w, lit, op) << 3);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kFilterK; ++k) {
+      uint32_t b = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t r = warp_row0 + 4 * (lane + 32 * k) + j;
+        if (r < n && cmp_op(col[r], lit, op)) b |= 1u << j;
+      }
+      bits[k] = b;
+    }
+  }
+
+  // ---- warp-level ranks: ballots per (k, j), popcounts below this lane
+  const unsigned lt = lanemask_lt();
+  uint32_t before[kFilterK];  // selected items of this warp ordered before (k, lane, 0)
+  uint32_t running = 0;
+#pragma unroll
+  for (int k = 0; k < kFilterK; ++k) {
+    uint32_t below = 0, tot = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned m = __ballot_sync(0xffffffffu, (bits[k] >> j) & 1u);
+      below += __popc(m & lt);
+      tot += __popc(m);
+    }
+    before[k] = running + below;
+    running += tot;
+  }
+  if (lane == 0) s_warp_total[warp] = running;
+  __syncthreads();
+
+  // ---- block scan of warp totals, then the look-back for the tile's offset
+  if (warp == 0) {
+    uint64_t v = lane < kFilterThreads / 32 ? s_warp_total[lane] : 0;
+    uint64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane < kFilterThreads / 32) s_warp_excl[lane] = incl - v;
+    const uint64_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint64_t excl = look_back(status, tile, total, &hdr->status);
+    if (lane == 0) {
+      s_tile_excl = excl;
+      if (tile == num_tiles - 1) {
+        hdr->count = excl + total;
+        if (d_count) *d_count = (int64_t)(excl + total);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- scatter the selected row ids in row order
+  const uint64_t base = s_tile_excl + s_warp_excl[warp];
+#pragma unroll
+  for (int k = 0; k < kFilterK; ++k) {
+    uint32_t b = bits[k];
+    uint32_t pos = before[k];
+    const uint32_t row0 = (uint32_t)(warp_row0 + 4 * (lane + 32 * k));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((b >> j) & 1u) out[base + pos++] = row0 + j;
+    }
+  }
+}
+
+}  // namespace
+
+size_t filter_scratch_bytes(int64_t n) {
+  const int64_t tiles = n > 0 ? (n + kTileRows - 1) / kTileRows : 0;
+  return 256 + align_up((size_t)tiles * 8, 256);
+}
+
+sirius_status filter_launch(const int32_t* d_col, int64_t n, int32_t op, int32_t literal,
+                            uint32_t* d_row_ids, int64_t* d_count, DevHeader* hdr,
+                            uint64_t* status, cudaStream_t s) {
+  const int64_t tiles = (n + kTileRows - 1) / kTileRows;
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(hdr, 0, 256 + (size_t)tiles * 8, s));
+  const bool vec = ((uintptr_t)d_col & 15) == 0;
+  PhaseTimer pt(s, SIRIUS_PHASE_FILTER);
+  if (vec)
+    filter_compact_kernel<true><<<(unsigned)tiles, kFilterThreads, 0, s>>>(
+        d_col, n, op, literal, d_row_ids, d_count, hdr, status, tiles);
+  else
+    filter_compact_kernel<false><<<(unsigned)tiles, kFilterThreads, 0, s>>>(
+        d_col, n, op, literal, d_row_ids, d_count, hdr, status, tiles);
+  SIRIUS_LAUNCH_CHECK();
+  return SIRIUS_OK;
+}
+
+}  // namespace sirius
+
+using namespace sirius;
+
+extern "C" size_t sirius_filter_scratch_bytes(int64_t n) { return filter_scratch_bytes(n); }
+
+extern "C" sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t op,
+                                       int32_t literal, uint32_t* d_row_ids, int64_t* d_count,
+                                       int64_t* h_count, void* d_scratch, size_t scratch_bytes,
+                                       sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  SIRIUS_REQUIRE(n >= 0 && n <= kMaxRows, "filter: n=%lld out of range", (long long)n);
+  SIRIUS_REQUIRE(op >= SIRIUS_LT && op <= SIRIUS_NE, "filter: bad comparison %d", op);
+  SIRIUS_REQUIRE(n == 0 || (d_col && d_row_ids), "filter: NULL column or output");
+  if (n == 0) {
+    if (d_count) SIRIUS_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int64_t), s));
+    if (h_count) *h_count = 0;
+    return SIRIUS_OK;
+  }
+  Scratch sc;
+  sirius_status st = sc.acquire(d_scratch, scratch_bytes, filter_scratch_bytes(n), s);
+  if (st != SIRIUS_OK) return st;
+  DevHeader* hdr = (DevHeader*)sc.take(256);
+  uint64_t* status = (uint64_t*)(sc.base + 256);
+  st = filter_launch(d_col, n, op, literal, d_row_ids, d_count, hdr, status, s);
+  if (st != SIRIUS_OK) return st;
+  if (h_count) {
+    DevHeader h;
+    SIRIUS_CUDA_TRY(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SIRIUS_CUDA_TRY(cudaStreamSynchronize(s));
+    *h_count = (int64_t)h.count;
+    if (h.status != 0) {
+      set_error("filter: device status %d", h.status);
+      return (sirius_status)h.status;
+    }
+  }
+  return SIRIUS_OK;
+}

@@ -1,0 +1,124 @@
+// Open-addressing hash tables of libsirius: the join table (key -> payload, a multimap) and the
+// group table (distinct key -> slot of its aggregates).  Device-side insert routines shared by
+// the stand-alone operators and the fused pipeline.
+#pragma once
+
+#include "common.cuh"
+
+namespace sirius {
+
+// 256-byte header in front of a join table's slots.
+struct JoinHeader {
+  uint32_t has_dups;   // some key was inserted twice
+  int32_t status;      // first device error of the build
+  uint64_t pairs;      // pair counter of the stand-alone probe
+  uint64_t pad[30];
+};
+static_assert(sizeof(JoinHeader) == 256, "join header is 256 bytes");
+
+// Insert (key -> payload) into a table of 8-byte slots {key low word, payload high word}.
+// The slot word is read with one aligned 64-bit load; a stale "empty" is settled by the CAS,
+// and an occupied slot never becomes empty again during a build.
+__device__ __forceinline__ bool join_insert32(uint64_t* slots, uint32_t cap, uint32_t key,
+                                              uint64_t desired, bool& dup) {
+  uint32_t s = home_slot32(key, cap);
+  for (uint32_t step = 0; step < cap; ++step) {
+    uint64_t cur = ld_relaxed_u64(&slots[s]);
+    if (cur == kEmpty64) {
+      cur = atomicCAS((unsigned long long*)&slots[s], kEmpty64, desired);
+      if (cur == kEmpty64) return true;
+    }
+    if ((uint32_t)cur == key) dup = true;
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return false;
+}
+
+// Insert into a table of 16-byte slots {uint64 key, uint32 payload, uint32 pad = ~0}.  Every
+// visited slot is read through the 128-bit CAS itself, so key and payload are seen together.
+__device__ __forceinline__ bool join_insert64(ulonglong2* slots, uint32_t cap, uint64_t key,
+                                              uint32_t payload, bool& dup) {
+  uint32_t s = home_slot64(key, cap);
+  const unsigned long long nhi = 0xFFFFFFFF00000000ull | payload;
+  for (uint32_t step = 0; step < cap; ++step) {
+    unsigned long long olo, ohi;
+    cas128((unsigned long long*)&slots[s], kEmpty64, kEmpty64, key, nhi, olo, ohi);
+    if (olo == kEmpty64 && ohi == kEmpty64) return true;
+    if (olo == key) dup = true;
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return false;
+}
+
+// Group table: keys[cap] (int64; kEmptyKey marks an empty slot) plus one extra slot `cap`
+// reserved for the key equal to kEmptyKey itself.  Returns the key's slot, inserting it if
+// new, or -1 when the table is full (more than `limit` distinct keys).
+__device__ __forceinline__ int64_t group_find_or_insert(int64_t* keys, uint32_t cap, int64_t key,
+                                                        unsigned long long* distinct,
+                                                        unsigned long long limit) {
+  if (key == kEmptyKey) return cap;
+  uint32_t s = home_slot64((uint64_t)key, cap);
+  for (uint32_t step = 0; step < cap; ++step) {
+    int64_t cur = (int64_t)ld_relaxed_u64((const uint64_t*)&keys[s]);
+    if (cur == key) return s;
+    if (cur == kEmptyKey) {
+      cur = (int64_t)atomicCAS((unsigned long long*)&keys[s], (unsigned long long)kEmptyKey,
+                               (unsigned long long)key);
+      if (cur == kEmptyKey) {
+        if (atomicAdd(distinct, 1ull) >= limit) return -1;
+        return s;
+      }
+      if (cur == key) return s;
+    }
+    s = (s + 1 == cap) ? 0 : s + 1;
+  }
+  return -1;
+}
+
+// Capacity of a group table for an expected number of distinct keys: a power of two with
+// load at most one half; `limit` = the most distinct keys accepted (7/8 of the slots).
+inline int64_t group_capacity_for(int64_t hint) {
+  if (hint < 1) hint = 1;
+  int64_t c = 16;
+  while (c < 2 * hint) c <<= 1;
+  return c;
+}
+inline unsigned long long group_limit_for(int64_t cap) { return (unsigned long long)(cap - cap / 8); }
+
+// Aggregates of one group slot.
+struct __align__(32) Agg {
+  unsigned long long sum;    // two's-complement sum (exact while the true sum fits int64)
+  unsigned long long count;
+  long long min;
+  long long max;
+};
+
+__device__ __forceinline__ void agg_update_global(Agg* a, int64_t v, uint32_t aggs) {
+  if (aggs & SIRIUS_AGG_SUM) atomicAdd(&a->sum, (unsigned long long)v);
+  atomicAdd(&a->count, 1ull);
+  // MIN/MAX only move one way: a value no better than one already seen skips the atomic.
+  if ((aggs & SIRIUS_AGG_MIN) && v < *(volatile long long*)&a->min) atomicMin(&a->min, (long long)v);
+  if ((aggs & SIRIUS_AGG_MAX) && v > *(volatile long long*)&a->max) atomicMax(&a->max, (long long)v);
+}
+
+__device__ __forceinline__ void agg_merge_global(Agg* a, unsigned long long sum, unsigned long long cnt,
+                                                 long long mn, long long mx, uint32_t aggs) {
+  if (aggs & SIRIUS_AGG_SUM) atomicAdd(&a->sum, sum);
+  atomicAdd(&a->count, cnt);
+  if ((aggs & SIRIUS_AGG_MIN) && mn < *(volatile long long*)&a->min) atomicMin(&a->min, mn);
+  if ((aggs & SIRIUS_AGG_MAX) && mx > *(volatile long long*)&a->max) atomicMax(&a->max, mx);
+}
+
+__device__ __forceinline__ void agg_identity(Agg* a) {
+  a->sum = 0;
+  a->count = 0;
+  a->min = INT64_MAX;
+  a->max = INT64_MIN;
+}
+
+// Host-side helpers shared by the operator entry points.
+sirius_status join_build(const int32_t* lo, const int32_t* hi, int64_t m, void* mem,
+                         int64_t capacity, cudaStream_t s, bool clear);
+int grid_for(int64_t n, int threads);
+
+}  // namespace sirius

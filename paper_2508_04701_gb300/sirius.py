@@ -1,0 +1,352 @@
+"""Python binding of libsirius (include/sirius.h): the same entry points, argument marshalling
+only.  Device memory and streams come from PyTorch; every step of the work runs in the
+library's CUDA kernels.  Loading fails loudly when the library is missing -- there is no CPU
+path.
+
+Entry points take torch tensors (device memory) and return Python values; a non-OK status
+raises SiriusError carrying the status code and the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsirius.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CAPACITY, ERR_TABLE_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_SCRATCH = range(8)
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CAPACITY", 4: "TABLE_FULL", 5: "TIMEOUT",
+                6: "CUDA", 7: "SCRATCH"}
+LT, LE, GT, GE, EQ, NE = range(6)
+OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
+AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
+AGG_MODES = {"auto": 0, "smem": 1, "global": 2}
+
+
+class SiriusError(RuntimeError):
+    def __init__(self, status: int, msg: str, needed: Optional[int] = None):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+        self.needed = needed
+
+
+class PipelineDesc(ctypes.Structure):
+    _fields_ = [("fk", ctypes.c_void_p), ("fk_hi", ctypes.c_void_p), ("pred", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("pk", ctypes.c_void_p), ("pk_hi", ctypes.c_void_p), ("grp", ctypes.c_void_p),
+                ("flag", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("op", ctypes.c_int32), ("literal", ctypes.c_int32), ("aggs", ctypes.c_uint32),
+                ("agg_mode", ctypes.c_int32), ("group_cap_hint", ctypes.c_int64),
+                ("load_factor", ctypes.c_float), ("block_threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("sum", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("min", ctypes.c_void_p), ("max", ctypes.c_void_p), ("out_cap", ctypes.c_int64),
+                ("d_groups", ctypes.c_void_p), ("d_status", ctypes.c_void_p),
+                ("sync", ctypes.c_int32), ("status", ctypes.c_int32), ("groups", ctypes.c_int64)]
+
+
+class JoinTable(ctypes.Structure):
+    _fields_ = [("d_mem", ctypes.c_void_p), ("capacity", ctypes.c_int64),
+                ("key_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+# (name, restype, argtypes) of every exported function
+_VP, _I32, _I64, _U32, _U64, _SZ, _F64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t,
+                                          ctypes.c_double)
+SIGNATURES = {
+    "sirius_version": (_I32, []),
+    "sirius_last_error": (ctypes.c_char_p, []),
+    "sirius_launch_count": (_U64, []),
+    "sirius_device_sm_count": (_I32, []),
+    "sirius_profile_start": (None, []),
+    "sirius_profile_stop": (_I32, [_VP, _VP, _I32]),
+    "sirius_filter_scratch_bytes": (_SZ, [_I64]),
+    "sirius_filter": (_I32, [_VP, _I64, _I32, _I32, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "sirius_join_table_capacity": (_I64, [_I64, _F64]),
+    "sirius_join_table_bytes": (_SZ, [_I64, _I32]),
+    "sirius_hash_join_build": (_I32, [_VP, _VP, _I64, ctypes.POINTER(JoinTable), _VP, _VP]),
+    "sirius_hash_join_probe": (_I32, [ctypes.POINTER(JoinTable), _VP, _VP, _VP, _I64, _VP, _VP,
+                                      _I64, _VP, _VP, _VP]),
+    "sirius_gather_i32": (_I32, [_VP, _VP, _I64, _VP, _VP]),
+    "sirius_gather_i64": (_I32, [_VP, _VP, _I64, _VP, _VP]),
+    "sirius_gather_group_key": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP]),
+    "sirius_groupby_capacity": (_I64, [_I64]),
+    "sirius_groupby_scratch_bytes": (_SZ, [_I64]),
+    "sirius_groupby_agg": (_I32, [_VP, _I32, _VP, _I64, _U32, _I64, _VP, _VP, _VP, _VP, _VP,
+                                  _I64, _VP, _VP, _VP, _SZ, _VP]),
+    "sirius_pipeline_scratch_bytes": (_SZ, [ctypes.POINTER(PipelineDesc)]),
+    "sirius_run_pipeline": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(Result), _VP, _SZ,
+                                   _VP]),
+}
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libsirius.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no fallback path)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def last_error() -> str:
+    return lib().sirius_last_error().decode()
+
+
+def _check(st: int, needed: Optional[int] = None):
+    if st != OK:
+        raise SiriusError(st, last_error(), needed)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libsirius takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libsirius takes contiguous columns")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _scratch(nbytes: int, device) -> torch.Tensor:
+    # torch allocations are 512-byte aligned; one extra page keeps the size non-zero
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def launch_count() -> int:
+    return int(lib().sirius_launch_count())
+
+
+PHASES = ["filter", "join_build", "join_probe", "gather", "groupby", "pipe_init", "pipe_build",
+          "pipe_probe", "pipe_finalize", "batch_plan", "batch_build", "batch_probe",
+          "batch_finalize", "copy", "reserved14", "reserved15"]
+
+
+def profile_start():
+    lib().sirius_profile_start()
+
+
+def profile_stop() -> Dict[str, tuple]:
+    """{phase: (total ms, launches)} for the phases that ran since profile_start()."""
+    ms = (ctypes.c_double * 16)()
+    n = (ctypes.c_int64 * 16)()
+    _check(lib().sirius_profile_stop(ms, n, 16))
+    return {PHASES[i]: (ms[i], n[i]) for i in range(16) if n[i]}
+
+
+# ---------------------------------------------------------------------------- A2: filter
+def sirius_filter(col: torch.Tensor, op="lt", literal: int = 0, out: Optional[torch.Tensor] = None,
+                  stream=None, scratch: Optional[torch.Tensor] = None, sync: bool = True):
+    """Ascending row ids of col <op> literal.  Returns the row-id tensor trimmed to the count
+    (sync=True), or (out, d_count) without synchronising."""
+    n = col.numel()
+    if col.dtype != torch.int32:
+        raise TypeError("filter column must be int32")
+    op = OPS[op] if isinstance(op, str) else int(op)
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=col.device)
+    d_count = torch.zeros(1, dtype=torch.int64, device=col.device)
+    if scratch is None:
+        scratch = _scratch(lib().sirius_filter_scratch_bytes(n), col.device)
+    h = ctypes.c_int64(0)
+    st = lib().sirius_filter(_ptr(col), n, op, int(literal), _ptr(out), _ptr(d_count),
+                             ctypes.byref(h) if sync else None, _ptr(scratch), scratch.numel(),
+                             _stream(stream))
+    _check(st)
+    if sync:
+        return out[:h.value]
+    return out, d_count
+
+
+# ---------------------------------------------------------------------------- A1/A3: join
+class HashJoinTable:
+    """A join table in a torch-owned device buffer."""
+
+    def __init__(self, m: int, key_width: int = 4, load_factor: float = 0.5, device="cuda"):
+        cap = lib().sirius_join_table_capacity(m, load_factor)
+        nbytes = lib().sirius_join_table_bytes(cap, key_width)
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.struct = JoinTable(self.mem.data_ptr(), cap, key_width, 0)
+        self.has_dups = None
+
+    @property
+    def capacity(self) -> int:
+        return self.struct.capacity
+
+
+def sirius_hash_join_build(keys: torch.Tensor, keys_hi: Optional[torch.Tensor] = None,
+                           load_factor: float = 0.5, table: Optional[HashJoinTable] = None,
+                           stream=None) -> HashJoinTable:
+    m = keys.numel()
+    if table is None:
+        table = HashJoinTable(m, 8 if keys_hi is not None else 4, load_factor, keys.device)
+    d = ctypes.c_int32(0)
+    st = lib().sirius_hash_join_build(_ptr(keys), _ptr(keys_hi), m, ctypes.byref(table.struct),
+                                      ctypes.byref(d), _stream(stream))
+    _check(st)
+    table.has_dups = bool(d.value)
+    return table
+
+
+def sirius_hash_join_probe(table: HashJoinTable, keys: torch.Tensor,
+                           keys_hi: Optional[torch.Tensor] = None,
+                           sel: Optional[torch.Tensor] = None, out_cap: Optional[int] = None,
+                           stream=None):
+    """All (probe row, build row) pairs with equal keys, unordered, as two int32 tensors
+    (uint32 bit patterns).  Retries once with the exact size when out_cap is too small."""
+    n = sel.numel() if sel is not None else keys.numel()
+    if out_cap is None:
+        out_cap = n
+    while True:
+        op_ = torch.empty(max(out_cap, 1), dtype=torch.int32, device=keys.device)
+        ob = torch.empty(max(out_cap, 1), dtype=torch.int32, device=keys.device)
+        h = ctypes.c_int64(0)
+        st = lib().sirius_hash_join_probe(ctypes.byref(table.struct), _ptr(keys), _ptr(keys_hi),
+                                          _ptr(sel), n, _ptr(op_), _ptr(ob), out_cap, None,
+                                          ctypes.byref(h), _stream(stream))
+        if st == ERR_CAPACITY:
+            out_cap = h.value
+            continue
+        _check(st)
+        return op_[:h.value], ob[:h.value]
+
+
+# ---------------------------------------------------------------------------- A4: gather
+def sirius_gather(src: torch.Tensor, idx: torch.Tensor, stream=None) -> torch.Tensor:
+    n = idx.numel()
+    dst = torch.empty(n, dtype=src.dtype, device=src.device)
+    if src.dtype == torch.int32:
+        st = lib().sirius_gather_i32(_ptr(src), _ptr(idx), n, _ptr(dst), _stream(stream))
+    elif src.dtype == torch.int64:
+        st = lib().sirius_gather_i64(_ptr(src), _ptr(idx), n, _ptr(dst), _stream(stream))
+    else:
+        raise TypeError("gather supports int32 and int64 columns")
+    _check(st)
+    return dst
+
+
+def sirius_gather_group_key(grp: torch.Tensor, flag: Optional[torch.Tensor], idx: torch.Tensor,
+                            stream=None) -> torch.Tensor:
+    n = idx.numel()
+    dst = torch.empty(n, dtype=torch.int64, device=grp.device)
+    _check(lib().sirius_gather_group_key(_ptr(grp), _ptr(flag), _ptr(idx), n, _ptr(dst),
+                                         _stream(stream)))
+    return dst
+
+
+# ---------------------------------------------------------------------------- A5/A6: group-by
+def _agg_mask(aggs) -> int:
+    if isinstance(aggs, int):
+        return aggs
+    m = 0
+    for a in aggs.split(","):
+        m |= {"sum": AGG_SUM, "count": AGG_COUNT, "min": AGG_MIN, "max": AGG_MAX}[a.strip()]
+    return m
+
+
+def sirius_groupby_agg(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,min,max",
+                       group_cap_hint: int = 1024, out_cap: Optional[int] = None,
+                       stream=None) -> Dict[str, torch.Tensor]:
+    n = keys.numel()
+    kw = {torch.int32: 4, torch.int64: 8}[keys.dtype]
+    mask = _agg_mask(aggs)
+    if out_cap is None:
+        out_cap = lib().sirius_groupby_capacity(group_cap_hint) + 1
+    dev = keys.device
+    outs = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, device=dev)
+            for c in ("key", "sum", "count", "min", "max")}
+    scratch = _scratch(lib().sirius_groupby_scratch_bytes(group_cap_hint), dev)
+    h = ctypes.c_int64(0)
+    st = lib().sirius_groupby_agg(
+        _ptr(keys), kw, _ptr(vals), n, mask, group_cap_hint, _ptr(outs["key"]),
+        _ptr(outs["sum"]) if mask & AGG_SUM else None, _ptr(outs["count"]),
+        _ptr(outs["min"]) if mask & AGG_MIN else None,
+        _ptr(outs["max"]) if mask & AGG_MAX else None, out_cap, None, ctypes.byref(h),
+        _ptr(scratch), scratch.numel(), _stream(stream))
+    _check(st, h.value)
+    g = h.value
+    return {c: t[:g] for c, t in outs.items()}
+
+
+# ---------------------------------------------------------------------------- A7: pipeline
+def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="lt",
+              literal: int = 50, aggs="sum,count,min,max", group_cap_hint: int = 0,
+              load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
+              blocks_per_sm: int = 0) -> PipelineDesc:
+    g = lambda d, k: _ptr(d.get(k)) if d.get(k) is not None else None  # noqa: E731
+    return PipelineDesc(
+        g(fact, "fk"), g(fact, "fk_hi"), g(fact, "pred"), g(fact, "val"), fact["pred"].numel(),
+        g(dim, "pk"), g(dim, "pk_hi"), g(dim, "grp"), g(dim, "flag"), dim["pk"].numel(),
+        OPS[op] if isinstance(op, str) else int(op), int(literal), _agg_mask(aggs),
+        AGG_MODES[agg_mode] if isinstance(agg_mode, str) else int(agg_mode), int(group_cap_hint),
+        float(load_factor), int(block_threads), int(blocks_per_sm), 0)
+
+
+def pipeline_scratch_bytes(desc: PipelineDesc) -> int:
+    return int(lib().sirius_pipeline_scratch_bytes(ctypes.byref(desc)))
+
+
+class PipelineOutputs:
+    """Device output arrays for one pipeline result."""
+
+    def __init__(self, out_cap: int, device="cuda"):
+        self.cap = out_cap
+        self.t = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, device=device)
+                  for c in ("key", "sum", "count", "min", "max")}
+        self.d_groups = torch.zeros(1, dtype=torch.int64, device=device)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def result(self, sync: bool) -> Result:
+        t = self.t
+        return Result(t["key"].data_ptr(), t["sum"].data_ptr(), t["count"].data_ptr(),
+                      t["min"].data_ptr(), t["max"].data_ptr(), self.cap,
+                      self.d_groups.data_ptr(), self.d_status.data_ptr(), 1 if sync else 0, 0, 0)
+
+    def trimmed(self, g: int) -> Dict[str, torch.Tensor]:
+        return {c: v[:g] for c, v in self.t.items()}
+
+
+def sirius_run_pipeline(desc: PipelineDesc, outputs: PipelineOutputs,
+                        scratch: Optional[torch.Tensor] = None, stream=None, sync: bool = True):
+    """Runs one fused pipeline.  sync=True: returns G (raises on a device error); sync=False:
+    returns None and leaves G / status in outputs.d_groups / outputs.d_status."""
+    r = outputs.result(sync)
+    if scratch is None:
+        scratch = _scratch(pipeline_scratch_bytes(desc), outputs.d_groups.device)
+    st = lib().sirius_run_pipeline(ctypes.byref(desc), ctypes.byref(r), _ptr(scratch),
+                                   scratch.numel(), _stream(stream))
+    _check(st, r.groups)
+    return r.groups if sync else None
+
+
+def run_pipeline(fact, dim, op="lt", literal=50, aggs="sum,count,min,max", group_cap_hint=0,
+                 out_cap=None, **tuning) -> Dict[str, torch.Tensor]:
+    """One query end to end on device tensors; returns the trimmed group arrays."""
+    desc = make_desc(fact, dim, op, literal, aggs, group_cap_hint, **tuning)
+    if out_cap is None:
+        out_cap = max(1, group_cap_hint or dim["pk"].numel())
+    outs = PipelineOutputs(out_cap, fact["pred"].device)
+    g = sirius_run_pipeline(desc, outs)
+    return outs.trimmed(g)

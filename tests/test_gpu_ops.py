@@ -1,0 +1,204 @@
+"""Parity of each CUDA operator with the CPU oracle, through the C-ABI (GPU).
+
+Integer work, so the bar is bit-exact: filter output in order, join pairs and groups after a
+canonical sort.  Sizes span several tiles plus a ragged tail; edge cases cover empty inputs,
+selectivity 0 % / 100 %, duplicate and sentinel-valued keys, misses, unaligned columns."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2508_04701_gb300 import datagen as dg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2508_04701_gb300 import build
+    build.build()
+    from paper_2508_04701_gb300 import sirius
+    sirius.lib()
+    return sirius
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+# ------------------------------------------------------------------------- filter
+@pytest.mark.parametrize("n", [1, 5, 4095, 4096, 4097, 12289, 100_003, 3_000_001])
+def test_filter_sizes(S, n):
+    col = np.random.default_rng(n).integers(0, 100, size=n).astype(np.int32)
+    for t in (0, 37, 100):
+        got = u32(S.sirius_filter(dev(col), "lt", t))
+        assert np.array_equal(got, O.filter_rows(col, "lt", t))
+
+
+@pytest.mark.parametrize("op", O.OPS)
+def test_filter_ops(S, op):
+    col = np.random.default_rng(1).integers(-50, 50, size=50_001).astype(np.int32)
+    col[:10] = [np.iinfo(np.int32).min, np.iinfo(np.int32).max, 0, -1, 1, 7, 7, 7, -7, 0]
+    for lit in (np.iinfo(np.int32).min, -1, 0, 7, np.iinfo(np.int32).max):
+        got = u32(S.sirius_filter(dev(col), op, int(lit)))
+        assert np.array_equal(got, O.filter_rows(col, op, int(lit))), (op, lit)
+
+
+def test_filter_empty_and_unaligned(S):
+    assert S.sirius_filter(torch.zeros(0, dtype=torch.int32, device="cuda"), "lt", 5).numel() == 0
+    col = np.random.default_rng(2).integers(0, 100, size=20_001).astype(np.int32)
+    d = dev(col)
+    got = u32(S.sirius_filter(d[1:], "ge", 42))   # 4-byte offset: scalar path
+    assert np.array_equal(got, O.filter_rows(col[1:], "ge", 42))
+
+
+def test_filter_async_count(S):
+    col = np.random.default_rng(3).integers(0, 100, size=777_777).astype(np.int32)
+    out, d_count = S.sirius_filter(dev(col), "lt", 30, sync=False)
+    torch.cuda.synchronize()
+    want = O.filter_rows(col, "lt", 30)
+    assert int(d_count.item()) == want.size
+    assert np.array_equal(u32(out[:want.size]), want)
+
+
+# ------------------------------------------------------------------------- join
+def check_join(S, probe, build, sel=None, probe_hi=None, build_hi=None, lf=0.5):
+    tab = S.sirius_hash_join_build(dev(build), dev(build_hi) if build_hi is not None else None, lf)
+    p, b = S.sirius_hash_join_probe(tab, dev(probe), dev(probe_hi) if probe_hi is not None else None,
+                                    dev(sel.view(np.int32)) if sel is not None else None)
+    got = O.sort_pairs(u32(p), u32(b))
+    pk = O.pack_composite(probe_hi, probe) if probe_hi is not None else probe.astype(np.int64)
+    bk = O.pack_composite(build_hi, build) if build_hi is not None else build.astype(np.int64)
+    rows = sel.astype(np.int64) if sel is not None else np.arange(probe.size)
+    wp, wb = O.join_sorted(pk[rows], bk)
+    want = O.sort_pairs(rows[wp.astype(np.int64)], wb)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    has_dup = np.unique(bk).size < bk.size
+    assert tab.has_dups == has_dup
+    return want[0].size
+
+
+@pytest.mark.parametrize("lf", [0.25, 0.5, 0.9])
+def test_join_unique_keys(S, lf):
+    m = 65_536
+    build = np.random.default_rng(4).permutation(m).astype(np.int32)
+    probe = np.random.default_rng(5).integers(0, 2 * m, size=300_007).astype(np.int32)
+    assert check_join(S, probe, build, lf=lf) > 0
+
+
+def test_join_with_selection_vector(S):
+    m = 10_000
+    build = np.random.default_rng(6).permutation(m).astype(np.int32)
+    probe = np.random.default_rng(7).integers(0, m, size=200_000).astype(np.int32)
+    pred = np.random.default_rng(8).integers(0, 100, size=200_000).astype(np.int32)
+    sel = O.filter_rows(pred, "lt", 30)
+    check_join(S, probe, build, sel=sel)
+
+
+def test_join_duplicates_and_sentinel_values(S):
+    rng = np.random.default_rng(9)
+    special = np.array([-1, np.iinfo(np.int32).min, 0, np.iinfo(np.int32).max], dtype=np.int32)
+    build = np.concatenate([rng.integers(-20, 20, size=3000).astype(np.int32), special, special])
+    probe = np.concatenate([rng.integers(-25, 25, size=5001).astype(np.int32), special])
+    assert check_join(S, probe, build) > 5001
+
+
+def test_join_all_miss_and_empty(S):
+    build = np.arange(1000, dtype=np.int32)
+    assert check_join(S, build + 5000, build) == 0
+    assert check_join(S, np.zeros(0, np.int32), build) == 0
+    assert check_join(S, build, np.zeros(0, np.int32)) == 0
+
+
+def test_join_composite_keys(S):
+    rng = np.random.default_rng(10)
+    pool = rng.integers(-2**31, 2**31, size=(500, 2)).astype(np.int64)
+    pool[0] = (-1, -1)
+    pool[1] = (0, -1)
+    pool[2] = (-1, 0)
+    bi = np.concatenate([np.arange(500), rng.integers(0, 500, size=100)])
+    pi = rng.integers(0, 700, size=40_001) % 600
+    pool_ext = np.concatenate([pool, rng.integers(-2**31, 2**31, size=(100, 2))])
+    b_hi, b_lo = pool[bi % 500, 0].astype(np.int32), pool[bi % 500, 1].astype(np.int32)
+    p_hi, p_lo = pool_ext[pi, 0].astype(np.int32), pool_ext[pi, 1].astype(np.int32)
+    check_join(S, p_lo, b_lo, probe_hi=p_hi, build_hi=b_hi)
+
+
+def test_join_capacity_retry(S):
+    build = np.concatenate([np.arange(100, dtype=np.int32)] * 4)
+    probe = np.arange(100, dtype=np.int32)
+    tab = S.sirius_hash_join_build(dev(build))
+    p, b = S.sirius_hash_join_probe(tab, dev(probe), out_cap=10)
+    assert p.numel() == 400
+
+
+# ------------------------------------------------------------------------- gather
+def test_gather(S):
+    rng = np.random.default_rng(11)
+    src64 = rng.integers(-2**62, 2**62, size=100_000)
+    src32 = rng.integers(-2**31, 2**31, size=100_000).astype(np.int32)
+    idx = rng.integers(0, 100_000, size=333_333).astype(np.uint32)
+    assert np.array_equal(S.sirius_gather(dev(src64), dev(idx.view(np.int32))).cpu().numpy(), src64[idx])
+    assert np.array_equal(S.sirius_gather(dev(src32), dev(idx.view(np.int32))).cpu().numpy(), src32[idx])
+    grp = rng.integers(-1000, 1000, size=100_000).astype(np.int32)
+    flag = rng.integers(-128, 128, size=100_000).astype(np.int8)
+    got = S.sirius_gather_group_key(dev(grp), dev(flag), dev(idx.view(np.int32))).cpu().numpy()
+    assert np.array_equal(got, O.pack_group(grp, flag)[idx])
+
+
+# ------------------------------------------------------------------------- group-by
+def check_groupby(S, keys, vals, hint, aggs="sum,count,min,max"):
+    got = S.sirius_groupby_agg(dev(keys), dev(vals), aggs, group_cap_hint=hint)
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in got.items()})
+    want = O.groupby_agg(keys, vals)
+    cols = ["key", "count"] + [a for a in ("sum", "min", "max") if a in aggs]
+    for c in cols:
+        assert np.array_equal(got[c], want[c]), c
+    return want["key"].size
+
+
+@pytest.mark.parametrize("n,dom,hint", [(1, 1, 1), (1000, 10, 16), (300_001, 1000, 1000),
+                                        (300_001, 100_000, 100_000), (2_000_003, 5, 8)])
+def test_groupby_int32(S, n, dom, hint):
+    rng = np.random.default_rng(n + dom)
+    keys = rng.integers(-dom // 2, dom - dom // 2, size=n).astype(np.int32)
+    vals = rng.integers(-10**10, 10**10, size=n)
+    check_groupby(S, keys, vals, hint)
+
+
+def test_groupby_int64_with_sentinel_key(S):
+    rng = np.random.default_rng(12)
+    keys = rng.integers(-2**63, 2**63 - 1, size=50_000, dtype=np.int64) % 3000
+    keys[::7] = np.iinfo(np.int64).min
+    keys[::11] = np.iinfo(np.int64).max
+    vals = rng.integers(0, 10**8, size=50_000)
+    for hint in (4000, 1_000_000):   # shared-memory and global paths
+        check_groupby(S, keys, vals, hint)
+
+
+def test_groupby_subsets_and_single_group(S):
+    rng = np.random.default_rng(13)
+    vals = rng.integers(0, 10**8, size=123_457)
+    check_groupby(S, np.zeros(vals.size, np.int32), vals, 1, "sum,count")
+    check_groupby(S, rng.integers(0, 50, size=vals.size).astype(np.int32), vals, 64, "min")
+
+
+def test_groupby_table_full_then_retry(S):
+    keys = np.arange(10_000, dtype=np.int64)
+    vals = np.ones(10_000, dtype=np.int64)
+    with pytest.raises(S.SiriusError) as e:
+        S.sirius_groupby_agg(dev(keys), dev(vals), group_cap_hint=1000)
+    assert e.value.status == S.ERR_TABLE_FULL
+    assert check_groupby(S, keys, vals, 10_000) == 10_000
+
+
+def test_groupby_capacity(S):
+    keys = np.arange(1000, dtype=np.int32)
+    vals = np.ones(1000, dtype=np.int64)
+    with pytest.raises(S.SiriusError) as e:
+        S.sirius_groupby_agg(dev(keys), dev(vals), group_cap_hint=1000, out_cap=10)
+    assert e.value.status == S.ERR_CAPACITY and e.value.needed == 1000

@@ -1,0 +1,159 @@
+"""Parity of the fused pipeline (build -> filter/probe/aggregate -> finalize) with the CPU
+oracle, bit-exact after sorting groups by key (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2508_04701_gb300 import datagen as dg
+
+pytestmark = pytest.mark.gpu
+
+COLS = ("key", "sum", "count", "min", "max")
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2508_04701_gb300 import build
+    build.build()
+    from paper_2508_04701_gb300 import sirius
+    sirius.lib()
+    return sirius
+
+
+def dev(d):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in d.items()}
+
+
+def run(S, fact, dim, op="lt", t=50, aggs="sum,count,min,max", hint=0, **kw):
+    got = S.run_pipeline(dev(fact), dev(dim), op, t, aggs, hint, **kw)
+    torch.cuda.synchronize()
+    return O.sort_groups({k: v.cpu().numpy() for k, v in got.items()})
+
+
+def check(S, fact, dim, op="lt", t=50, aggs="sum,count,min,max", hint=0, **kw):
+    got = run(S, fact, dim, op, t, aggs, hint, **kw)
+    want = O.pipeline(fact, dim, op, t)
+    for c in ["key", "count"] + [a for a in ("sum", "min", "max") if a in aggs]:
+        assert np.array_equal(got[c], want[c]), c
+    return want["key"].size
+
+
+def test_plain_small_full_size(S):
+    """The 1M-row fact / 65 536-row dim / 1 000-group query at its full size."""
+    spec = dg.plain_small()
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    assert check(S, fact, dim, "lt", spec.t, hint=spec.grp_bound) == 1000
+
+
+@pytest.mark.parametrize("mode", ["smem", "global"])
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 1023, 100_003])
+def test_ragged_sizes_both_agg_modes(S, mode, n):
+    spec = dg.StarSpec("t", n=n, m=3001, fk_domain=3500, grp_bound=300, t=60, seed=n)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=300, agg_mode=mode)
+
+
+@pytest.mark.parametrize("t", [0, 1, 99, 100])
+def test_selectivity_edges(S, t):
+    spec = dg.StarSpec("t", n=200_001, m=5000, fk_domain=5000, grp_bound=50, t=t, seed=3)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", t, hint=50)
+
+
+@pytest.mark.parametrize("op", O.OPS)
+def test_comparison_ops(S, op):
+    spec = dg.StarSpec("t", n=50_000, m=2000, fk_domain=2000, grp_bound=40, seed=4)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, op, 50, hint=40)
+
+
+@pytest.mark.parametrize("lf", [0.3, 0.5, 0.8, 0.95])
+def test_load_factors(S, lf):
+    spec = dg.plain_scale(n=400_000, m=150_000)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=100_000, load_factor=lf)
+
+
+def test_scale_shape_small(S):
+    """The 600M-row query's distributions at 1/300 of its size (100 000 groups, global path)."""
+    spec = dg.plain_scale(n=2_000_000, m=50_000)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=100_000)
+
+
+def test_composite_keys(S):
+    spec = dg.plain_scale(n=1_000_003, m=40_000, composite=True)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=100_000)
+
+
+def test_skewed_flag_groups(S):
+    spec = dg.skewed(n=1_000_000, m=100_000)
+    dim = dg.gen_dim_host(spec)
+    fact = dg.gen_fact_host(spec, dim=dim)
+    g = check(S, fact, dim, "lt", spec.t, aggs="sum,count", hint=spec.m)
+    assert g > 1000
+
+
+def test_duplicate_dim_keys_and_misses(S):
+    rng = np.random.default_rng(5)
+    m = 3000
+    dim = {"pk": rng.integers(0, 2000, size=m).astype(np.int32),
+           "grp": rng.integers(-5, 30, size=m).astype(np.int32)}
+    fact = {"fk": rng.integers(-100, 2500, size=300_001).astype(np.int32),
+            "pred": rng.integers(0, 100, size=300_001).astype(np.int32),
+            "val": rng.integers(-10**9, 10**9, size=300_001)}
+    for mode in ("smem", "global"):
+        check(S, fact, dim, "lt", 70, hint=35, agg_mode=mode)
+
+
+def test_empty_inputs(S):
+    spec = dg.StarSpec("t", n=1000, m=100, fk_domain=100, grp_bound=10, seed=6)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    empty_dim = {k: v[:0] for k, v in dim.items()}
+    empty_fact = {k: v[:0] for k, v in fact.items()}
+    assert run(S, fact, empty_dim, hint=10)["key"].size == 0
+    assert run(S, empty_fact, dim, hint=10)["key"].size == 0
+    miss = dict(dim, pk=dim["pk"] + 10_000)
+    assert run(S, fact, miss, hint=10)["key"].size == 0
+
+
+def test_unaligned_columns(S):
+    spec = dg.StarSpec("t", n=100_001, m=4000, fk_domain=4000, grp_bound=100, seed=7)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    d = dev(fact)
+    shifted = {k: v[1:] for k, v in d.items()}   # 4-byte offsets: the scalar load path
+    got = S.run_pipeline(shifted, dev(dim), "lt", 50, group_cap_hint=100)
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in got.items()})
+    want = O.pipeline({k: v[1:] for k, v in fact.items()}, dim, "lt", 50)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
+
+
+def test_group_table_full_then_retry(S):
+    spec = dg.skewed(n=200_000, m=40_000)
+    dim = dg.gen_dim_host(spec)
+    fact = dg.gen_fact_host(spec, dim=dim)
+    with pytest.raises(S.SiriusError) as e:
+        S.run_pipeline(dev(fact), dev(dim), "lt", 50, "sum,count", group_cap_hint=spec.m // 4)
+    assert e.value.status == S.ERR_TABLE_FULL
+    check(S, fact, dim, "lt", 50, aggs="sum,count", hint=spec.m)
+
+
+def test_output_capacity(S):
+    spec = dg.StarSpec("t", n=100_000, m=1000, fk_domain=1000, grp_bound=200, seed=8)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    with pytest.raises(S.SiriusError) as e:
+        S.run_pipeline(dev(fact), dev(dim), "lt", 50, group_cap_hint=200, out_cap=10)
+    assert e.value.status == S.ERR_CAPACITY and e.value.needed == 200
+
+
+def test_repeatable_across_block_shapes(S):
+    spec = dg.plain_scale(n=500_000, m=20_000)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    ref = run(S, fact, dim, "lt", 30, hint=100_000)
+    for bt, bps in ((64, 1), (128, 3), (512, 1), (256, 0)):
+        got = run(S, fact, dim, "lt", 30, hint=100_000, block_threads=bt, blocks_per_sm=bps)
+        for c in COLS:
+            assert np.array_equal(got[c], ref[c])
