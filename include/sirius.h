@@ -73,7 +73,7 @@ int32_t sirius_device_sm_count(void);       /* SMs of the current device */
 enum { SIRIUS_PHASE_FILTER = 0, SIRIUS_PHASE_JOIN_BUILD = 1, SIRIUS_PHASE_JOIN_PROBE = 2,
        SIRIUS_PHASE_GATHER = 3, SIRIUS_PHASE_GROUPBY = 4, SIRIUS_PHASE_PIPE_INIT = 5,
        SIRIUS_PHASE_PIPE_BUILD = 6, SIRIUS_PHASE_PIPE_PROBE = 7, SIRIUS_PHASE_PIPE_FINALIZE = 8,
-       SIRIUS_PHASE_BATCH_PLAN = 9, SIRIUS_PHASE_BATCH_BUILD = 10, SIRIUS_PHASE_BATCH_PROBE = 11,
+       SIRIUS_PHASE_BATCH_GRAPH = 9, SIRIUS_PHASE_BATCH_BUILD = 10, SIRIUS_PHASE_BATCH_PROBE = 11,
        SIRIUS_PHASE_BATCH_FINALIZE = 12, SIRIUS_PHASE_COPY = 13, SIRIUS_PHASES = 16 };
 void sirius_profile_start(void);
 sirius_status sirius_profile_stop(double* ms, int64_t* launches, int32_t nphases);
@@ -214,9 +214,85 @@ typedef struct {
 size_t sirius_pipeline_scratch_bytes(const sirius_pipeline_desc* q);
 /* Errors: INVALID, SCRATCH, OOM, CUDA; with sync also TABLE_FULL (more distinct group keys in
  * the dim than the group table takes: raise group_cap_hint) and CAPACITY (G > out_cap; the
- * needed G is in result->groups). */
+ * needed G is in result->groups).  Without sync the same codes reach result->d_status. */
 sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, sirius_result* result,
                                   void* d_scratch, size_t scratch_bytes, sirius_stream stream);
+
+/* ------------------------------------------------------------------ resident build side
+ * The build phase of sirius_run_pipeline as a call of its own, so that a dim table's join and
+ * group tables stay resident in device memory and serve many probe passes (the pre-allocated
+ * data caching region, Sec. 3.2.3).  The dim index depends only on the dim fields of `q`
+ * (pk, pk_hi, grp, flag, m, group_cap_hint, load_factor).  d_mem: caller device memory of
+ * sirius_dim_index_bytes(q) bytes, 256-byte aligned, passed in `bytes`.  The build fills
+ * join_capacity, group_capacity and key_width.  h_status (nullable) synchronises and receives
+ * the device status (TABLE_FULL: more distinct group keys than the hint allows). */
+typedef struct {
+  void* d_mem;
+  size_t bytes;
+  int64_t join_capacity;
+  int64_t group_capacity;
+  int32_t key_width;
+  int32_t reserved;
+} sirius_dim_index;
+
+size_t sirius_dim_index_bytes(const sirius_pipeline_desc* q);
+sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, sirius_dim_index* idx,
+                                     int32_t* h_status, sirius_stream stream);
+/* The probe, aggregate and finalize phases against a built dim index: uses the fact and query
+ * fields of `q`.  Scratch: sirius_probe_scratch_bytes(idx) (the aggregates).  The dim index is
+ * only read, so any number of probes may use it at once, each with its own scratch. */
+size_t sirius_probe_scratch_bytes(const sirius_dim_index* idx);
+sirius_status sirius_run_probe(const sirius_pipeline_desc* q, const sirius_dim_index* idx,
+                               sirius_result* result, void* d_scratch, size_t scratch_bytes,
+                               sirius_stream stream);
+
+/* ------------------------------------------------------------------ host-resident columns
+ * sirius_run_pipeline for columns in host memory (every column pointer of `q` is host memory,
+ * pinned for full copy bandwidth; the result arrays are host memory too).  The dim columns are
+ * copied and built first; the fact table then streams through the probe pass in chunks of
+ * chunk_rows rows (0 = 16 Mi rows): the copy of chunk i+1 runs on a second stream while chunk
+ * i is probed (batch execution over host data, Sec. 3.4).  The G result rows are copied back;
+ * the call synchronises and fills result->groups / result->status.  Scratch:
+ * sirius_pipeline_host_scratch_bytes(q, chunk_rows, out_cap). */
+size_t sirius_pipeline_host_scratch_bytes(const sirius_pipeline_desc* q, int64_t chunk_rows,
+                                          int64_t out_cap);
+sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q, sirius_result* result,
+                                       int64_t chunk_rows, void* d_scratch, size_t scratch_bytes,
+                                       sirius_stream stream);
+
+/* ------------------------------------------------------------------ A8: batched pipelines
+ * Many independent pipelines in one set of persistent launches: each phase (initialise, build,
+ * probe, finalize, publish) is one kernel whose blocks walk the concatenated work units of
+ * all queries, so uneven query sizes balance across the GPU and small queries cost no launches
+ * of their own (pipelines as tasks of one global queue, Sec. 3.2.2; batch execution, Sec. 3.4).
+ * A plan owns the device task table, its pinned staging copy and, once captured, a CUDA graph
+ * of the whole batch (copy in, five kernels, copy out) that serves any batch of up to
+ * max_queries queries: a replay only rewrites the staging table.
+ * indexes (nullable): indexes[i].d_mem != NULL makes query i probe that resident dim index
+ * (sirius_dim_index_build) instead of building one; it is only read, so queries may share one.
+ * results[i]: device output arrays as for sirius_run_pipeline; with sync != 0 in results[0]
+ * the call synchronises and fills every results[i].groups / .status.  The return value is the
+ * first failing query's status; per-query statuses are in results[i].status.
+ * Tuning: rows_per_unit (0 = 65536) is the probe work unit; queries whose group table fits
+ * (<= 3072 slots) aggregate each unit in shared memory.  Scratch:
+ * sirius_pipeline_batch_scratch_bytes(qs, nq, indexes); queries' tables live at fixed offsets
+ * in it, so two batches in flight need two scratch buffers (and two plans). */
+typedef struct sirius_batch_plan_s* sirius_batch_plan;
+
+size_t sirius_pipeline_batch_scratch_bytes(const sirius_pipeline_desc* qs, int32_t nq,
+                                           const sirius_dim_index* indexes);
+sirius_status sirius_batch_plan_create(int32_t max_queries, sirius_batch_plan* out);
+sirius_status sirius_batch_plan_run(sirius_batch_plan plan, const sirius_pipeline_desc* qs,
+                                    int32_t nq, const sirius_dim_index* indexes,
+                                    sirius_result* results, int64_t rows_per_unit,
+                                    int32_t use_graph, void* d_scratch, size_t scratch_bytes,
+                                    sirius_stream stream);
+void sirius_batch_plan_destroy(sirius_batch_plan plan);
+/* One-off form: creates a plan, runs without a graph, destroys the plan. */
+sirius_status sirius_run_pipeline_batch(const sirius_pipeline_desc* qs, int32_t nq,
+                                        const sirius_dim_index* indexes, sirius_result* results,
+                                        void* d_scratch, size_t scratch_bytes,
+                                        sirius_stream stream);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,11 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 void clear_error() { g_err[0] = 0; }
-void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+static thread_local bool g_count_off = false;
+void count_launch(int k) {
+  if (!g_count_off) g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed);
+}
+void set_launch_counting(bool on) { g_count_off = !on; }
 
 int sm_count() {
   int dev = 0, n = 0;
@@ -85,7 +89,7 @@ cudaEvent_t pool_event() {
 }  // namespace
 
 PhaseTimer::PhaseTimer(cudaStream_t s, int p) : phase(p), stream(s) {
-  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  if (p < 0 || !g_prof_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> g(g_prof_mu);
   cudaEvent_t e = pool_event();
   if (e && cudaEventRecord(e, s) == cudaSuccess) a = e;

@@ -1,0 +1,555 @@
+// A8: many independent pipelines in one set of persistent launches (pipelines as tasks of a
+// global queue, Sec. 3.2.2; batch execution, Sec. 3.4).
+//
+// Every query's work is cut into units per phase -- initialisation (8192 table words), build
+// (2048 dim rows), probe (rows_per_unit fact rows), finalize (4096 group slots).  One kernel per
+// phase runs a fixed grid whose blocks walk the concatenated units of all queries (grid-stride,
+// binary search for the unit's query), so a 10K-row query and a 20M-row query share the GPU
+// without a launch of their own.  Phases are ordered by the stream (no device-side waits).
+// Queries whose group table fits in shared memory aggregate each probe unit there and merge
+// it into the global table at the unit's end.  The task table lives in plan-owned device
+// memory and is refreshed by one host-to-device copy from pinned staging, so a CUDA graph
+// captured once (copy in, five kernels, copy out) serves every later batch.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "pipeline.cuh"
+
+namespace sirius {
+namespace {
+
+constexpr int kInitUnit = 8192;
+constexpr int kBuildUnit = 2048;
+constexpr int kFinUnit = 4096;
+constexpr int kBatchThreads = 256;
+constexpr int kProbeThreads = 256;
+
+enum : uint32_t { kQWide = 1, kQSmem = 2, kQVec = 4, kQBuild = 8 };
+
+struct BatchQuery {
+  ProbeArgs a;
+  DimView d;
+  PipeHeader* phdr;
+  PipeOut out;
+  const int32_t* pk;
+  const int32_t* pk_hi;
+  const int32_t* grp;
+  const int8_t* flag;
+  int64_t m;
+  int64_t jpairs;  // 16-byte words of join slots to clear (0 when the dim index is prebuilt)
+  int64_t gslots;
+  unsigned long long glimit;
+  uint32_t flags;
+  int32_t orig;    // position of the query in the caller's arrays
+  int64_t u0[4];   // first unit of this query in each phase (init, build, probe, finalize)
+  int64_t nu[4];   // units of this query in each phase
+};
+
+struct BatchHeader {
+  int32_t nq;
+  int32_t pad;
+  int64_t total[4];          // units per phase, all queries
+  int64_t quads_per_unit;
+  int32_t cls_q0[8], cls_q1[8];  // query range of each probe class (queries sorted by class)
+  int64_t cls_u0[8], cls_u1[8];  // probe-unit range of each class
+  int64_t pad2[2];
+};
+static_assert(sizeof(BatchHeader) == 256, "batch header is 256 bytes");
+
+struct BatchStatus {
+  int64_t status;
+  int64_t groups;
+};
+
+template <int P>
+__device__ __forceinline__ int find_query(const BatchQuery* __restrict__ Q, int nq, int64_t u) {
+  int lo = 0, hi = nq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (Q[mid].u0[P] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+batch_init_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
+  const int nq = H->nq;
+  const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
+  for (int64_t u = blockIdx.x; u < H->total[0]; u += gridDim.x) {
+    const BatchQuery& b = Q[find_query<0>(Q, nq, u)];
+    const int64_t local = u - b.u0[0];
+    const bool build = (b.flags & kQBuild) != 0;
+    if (local == 0 && threadIdx.x < 32) {
+      reinterpret_cast<uint64_t*>(b.phdr)[threadIdx.x] = 0;
+      if (build) {
+        reinterpret_cast<uint64_t*>(b.d.dhdr)[threadIdx.x] = 0;
+        reinterpret_cast<uint64_t*>(b.d.jhdr)[threadIdx.x] = 0;
+      }
+    }
+    const int64_t end = b.jpairs + b.gslots;
+    const int64_t i1 = (local + 1) * kInitUnit < end ? (local + 1) * kInitUnit : end;
+    for (int64_t i = local * kInitUnit + threadIdx.x; i < i1; i += blockDim.x) {
+      if (i < b.jpairs) {
+        reinterpret_cast<ulonglong2*>(b.d.jslots)[i] = ones;
+      } else {
+        const int64_t g = i - b.jpairs;
+        if (build) b.d.gkeys[g] = kEmptyKey;
+        agg_identity(&b.a.tab[g]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+batch_build_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
+  const int nq = H->nq;
+  for (int64_t u = blockIdx.x; u < H->total[1]; u += gridDim.x) {
+    const BatchQuery& b = Q[find_query<1>(Q, nq, u)];
+    const int64_t r0 = (u - b.u0[1]) * kBuildUnit;
+    const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
+    const DimView d = b.d;
+    bool dup = false;
+    for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+      const bool ok = (b.flags & kQWide) ? dim_build_row<true>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup)
+                                         : dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup);
+      if (!ok) set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
+    }
+    if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
+  }
+}
+
+// The probe phase runs one kernel per query class (key width, aggregation mode, vector
+// loads), each specialised at compile time; the host orders the task table by class, so a
+// class's queries -- and their probe units -- are contiguous.
+template <bool kWide, int kMode, bool kVec>
+__global__ void __launch_bounds__(kProbeThreads, 3)
+batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int cls) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  Agg* s_tab = reinterpret_cast<Agg*>(smem_raw);
+  const int qlo = H->cls_q0[cls], qhi = H->cls_q1[cls];
+  const int64_t qpu = H->quads_per_unit;
+  for (int64_t u = H->cls_u0[cls] + blockIdx.x; u < H->cls_u1[cls]; u += gridDim.x) {
+    int lo = qlo, hi = qhi - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (Q[mid].u0[2] <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchQuery& b = Q[lo];
+    if (b.d.dhdr->status != 0) continue;  // the build failed: nothing to aggregate
+    const ProbeArgs a = b.a;
+    const bool dups = b.d.jhdr->has_dups != 0;
+    const int64_t local = u - b.u0[2];
+    const int64_t nq4 = a.n >> 2;
+    const int64_t q0 = local * qpu;
+    const int64_t q1 = q0 + qpu < nq4 ? q0 + qpu : nq4;
+    if (kMode == kAggSmem) {
+      for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) agg_identity(&s_tab[i]);
+      __syncthreads();
+    }
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec>(a, s_tab, dups, q);
+    if (local == b.nu[2] - 1) {
+      const int64_t t0 = nq4 << 2;
+      if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, s_tab, dups, t0 + threadIdx.x);
+    }
+    if (kMode == kAggSmem) {
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) {
+        const Agg t = s_tab[i];
+        if (t.count) agg_merge_global(&a.tab[i], t.sum, t.count, t.min, t.max, a.aggs);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+batch_finalize_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
+  const int nq = H->nq;
+  for (int64_t u = blockIdx.x; u < H->total[3]; u += gridDim.x) {
+    const BatchQuery& b = Q[find_query<3>(Q, nq, u)];
+    const int64_t s0 = (u - b.u0[3]) * kFinUnit;
+    const int64_t s1 = s0 + kFinUnit < b.gslots ? s0 + kFinUnit : b.gslots;
+    const Agg* tab = b.a.tab;
+    const PipeOut out = b.out;
+    for (int64_t base = s0; base < s1; base += blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      const bool occ = i < s1 && tab[i].count > 0;
+      const uint64_t pos = warp_append(&b.phdr->groups, occ);
+      if (occ && (int64_t)pos < out.cap) {
+        const Agg t = tab[i];
+        if (out.keys) out.keys[pos] = b.d.gkeys[i];
+        if (out.sum) out.sum[pos] = (int64_t)t.sum;
+        if (out.count) out.count[pos] = (int64_t)t.count;
+        if (out.min) out.min[pos] = t.min;
+        if (out.max) out.max[pos] = t.max;
+      }
+    }
+  }
+}
+
+__global__ void batch_publish_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q,
+                                     BatchStatus* __restrict__ st) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= H->nq) return;
+  const BatchQuery& b = Q[q];
+  int32_t s = b.d.dhdr->status;
+  const unsigned long long g = b.phdr->groups;
+  if (s == 0 && (int64_t)g > b.out.cap) s = SIRIUS_ERR_CAPACITY;
+  b.phdr->status = s;
+  if (b.out.d_groups) *b.out.d_groups = (int64_t)g;
+  if (b.out.d_status) *b.out.d_status = s;
+  st[b.orig].status = s;
+  st[b.orig].groups = (int64_t)g;
+}
+
+DimLayout layout_of_index(const sirius_dim_index* idx) {
+  DimLayout L;
+  L.key_width = idx->key_width;
+  L.jcap = idx->join_capacity;
+  L.gcap = idx->group_capacity;
+  L.off_join = 256;
+  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
+  L.total = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
+  return L;
+}
+
+bool prebuilt(const sirius_dim_index* indexes, int i) { return indexes && indexes[i].d_mem; }
+
+}  // namespace
+}  // namespace sirius
+
+using namespace sirius;
+
+struct sirius_batch_plan_s {
+  int32_t max_q = 0;
+  size_t table_bytes = 0;      // header + queries
+  char* d_buf = nullptr;       // [BatchHeader | BatchQuery[max_q] | BatchStatus[max_q]]
+  char* h_buf = nullptr;       // pinned staging, same layout
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after each run: staging is free again
+  cudaGraphExec_t exec = nullptr;
+  size_t graph_smem = 0;
+  uint32_t graph_classes = 0;  // probe classes launched by the captured graph
+  int grid_small = 0;
+  int grid_probe[8] = {};
+  size_t smem_for_grid = (size_t)-1;
+};
+
+typedef void (*probe_kernel_t)(const BatchHeader*, const BatchQuery*, int);
+
+// class bits: 1 two-column keys, 2 shared-memory aggregation, 4 16-byte column loads
+static probe_kernel_t probe_kernel_for(int c) {
+  switch (c) {
+    case 0: return batch_probe_kernel<false, kAggGlobal, false>;
+    case 1: return batch_probe_kernel<true, kAggGlobal, false>;
+    case 2: return batch_probe_kernel<false, kAggSmem, false>;
+    case 3: return batch_probe_kernel<true, kAggSmem, false>;
+    case 4: return batch_probe_kernel<false, kAggGlobal, true>;
+    case 5: return batch_probe_kernel<true, kAggGlobal, true>;
+    case 6: return batch_probe_kernel<false, kAggSmem, true>;
+    default: return batch_probe_kernel<true, kAggSmem, true>;
+  }
+}
+
+static BatchHeader* hdr_of(char* buf) { return (BatchHeader*)buf; }
+static BatchQuery* queries_of(char* buf) { return (BatchQuery*)(buf + sizeof(BatchHeader)); }
+static BatchStatus* status_of(sirius_batch_plan p, char* buf) {
+  return (BatchStatus*)(buf + p->table_bytes);
+}
+
+extern "C" size_t sirius_pipeline_batch_scratch_bytes(const sirius_pipeline_desc* qs, int32_t nq,
+                                                      const sirius_dim_index* indexes) {
+  if (!qs || nq <= 0) return 0;
+  size_t off = 0;
+  for (int i = 0; i < nq; ++i) {
+    const sirius_pipeline_desc* q = &qs[i];
+    int64_t gcap;
+    if (prebuilt(indexes, i)) {
+      gcap = indexes[i].group_capacity;
+    } else {
+      const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint,
+                                     q->load_factor);
+      off += L.total;
+      gcap = L.gcap;
+    }
+    off += run_layout(gcap).total;
+  }
+  return off;
+}
+
+extern "C" sirius_status sirius_batch_plan_create(int32_t max_queries, sirius_batch_plan* out) {
+  clear_error();
+  SIRIUS_REQUIRE(out && max_queries > 0 && max_queries <= (1 << 20), "batch plan: bad max_queries");
+  sirius_batch_plan p = new (std::nothrow) sirius_batch_plan_s();
+  if (!p) return SIRIUS_ERR_OOM;
+  p->max_q = max_queries;
+  p->table_bytes = align_up(sizeof(BatchHeader) + sizeof(BatchQuery) * (size_t)max_queries, 256);
+  const size_t bytes = p->table_bytes + sizeof(BatchStatus) * (size_t)max_queries;
+  cudaError_t e = cudaMalloc(&p->d_buf, bytes);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_buf, bytes, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("batch plan: allocation failed: %s", cudaGetErrorString(e));
+    sirius_batch_plan_destroy(p);
+    return SIRIUS_ERR_OOM;
+  }
+  memset(p->h_buf, 0, bytes);
+  *out = p;
+  return SIRIUS_OK;
+}
+
+extern "C" void sirius_batch_plan_destroy(sirius_batch_plan p) {
+  if (!p) return;
+  if (p->done) cudaEventSynchronize(p->done);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->done) cudaEventDestroy(p->done);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->d_buf) cudaFree(p->d_buf);
+  if (p->h_buf) cudaFreeHost(p->h_buf);
+  delete p;
+}
+
+// Enqueue the whole batch (copy in, five phases, copy out) on stream s.
+static sirius_status enqueue_batch(sirius_batch_plan p, size_t smem, uint32_t classes, cudaStream_t s,
+                                   bool timed) {
+  const size_t copy_in = p->table_bytes;
+  BatchHeader* dH = hdr_of(p->d_buf);
+  BatchQuery* dQ = queries_of(p->d_buf);
+  SIRIUS_CUDA_TRY(cudaMemcpyAsync(p->d_buf, p->h_buf, copy_in, cudaMemcpyHostToDevice, s));
+  {
+    PhaseTimer pt(timed ? s : nullptr, timed ? SIRIUS_PHASE_BATCH_BUILD : -1);
+    batch_init_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    SIRIUS_LAUNCH_CHECK();
+    batch_build_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    SIRIUS_LAUNCH_CHECK();
+  }
+  {
+    PhaseTimer pt(timed ? s : nullptr, timed ? SIRIUS_PHASE_BATCH_PROBE : -1);
+    for (int c = 0; c < 8; ++c) {
+      if (!((classes >> c) & 1u)) continue;
+      probe_kernel_for(c)<<<p->grid_probe[c], kProbeThreads, (c & 2) ? smem : 0, s>>>(dH, dQ, c);
+      SIRIUS_LAUNCH_CHECK();
+    }
+  }
+  {
+    PhaseTimer pt(timed ? s : nullptr, timed ? SIRIUS_PHASE_BATCH_FINALIZE : -1);
+    batch_finalize_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    SIRIUS_LAUNCH_CHECK();
+    batch_publish_kernel<<<(p->max_q + 255) / 256, 256, 0, s>>>(dH, dQ, status_of(p, p->d_buf));
+    SIRIUS_LAUNCH_CHECK();
+  }
+  SIRIUS_CUDA_TRY(cudaMemcpyAsync(status_of(p, p->h_buf), status_of(p, p->d_buf),
+                                  sizeof(BatchStatus) * (size_t)p->max_q, cudaMemcpyDeviceToHost, s));
+  return SIRIUS_OK;
+}
+
+extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius_pipeline_desc* qs, int32_t nq,
+                                               const sirius_dim_index* indexes, sirius_result* results,
+                                               int64_t rows_per_unit, int32_t use_graph, void* d_scratch,
+                                               size_t scratch_bytes, sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  SIRIUS_REQUIRE(p, "batch: NULL plan");
+  SIRIUS_REQUIRE(qs && results && nq > 0 && nq <= p->max_q, "batch: nq=%d outside [1, %d]", nq, p->max_q);
+  SIRIUS_REQUIRE(rows_per_unit >= 0, "batch: negative rows_per_unit");
+  for (int i = 0; i < nq; ++i) {
+    sirius_status st = validate_fact(&qs[i]);
+    if (st == SIRIUS_OK && !prebuilt(indexes, i)) st = validate_dim(&qs[i]);
+    if (st == SIRIUS_OK && !prebuilt(indexes, i) && qs[i].n > 0 && qs[i].m > 0 &&
+        (qs[i].fk_hi == nullptr) != (qs[i].pk_hi == nullptr)) {
+      set_error("batch: query %d mixes one- and two-column keys", i);
+      st = SIRIUS_ERR_INVALID;
+    }
+    if (st == SIRIUS_OK && prebuilt(indexes, i) &&
+        (indexes[i].key_width != (qs[i].fk_hi ? 8 : 4) || indexes[i].group_capacity <= 0)) {
+      set_error("batch: query %d's dim index does not match its keys", i);
+      st = SIRIUS_ERR_INVALID;
+    }
+    if (st == SIRIUS_OK && (results[i].out_cap < 0 || (results[i].out_cap > 0 && !results[i].keys && !results[i].count))) {
+      set_error("batch: query %d has no output arrays", i);
+      st = SIRIUS_ERR_INVALID;
+    }
+    if (st != SIRIUS_OK) return st;
+  }
+  const size_t need = sirius_pipeline_batch_scratch_bytes(qs, nq, indexes);
+  Scratch sc;
+  sirius_status st = sc.acquire(d_scratch, scratch_bytes, need, s);
+  if (st != SIRIUS_OK) return st;
+
+  // the staging table may still feed the previous run's copy: wait for it
+  SIRIUS_CUDA_TRY(cudaEventSynchronize(p->done));
+  const int64_t rpu = rows_per_unit > 0 ? rows_per_unit : 65536;
+  const int64_t qpu = (rpu + 3) / 4;
+  BatchHeader* H = hdr_of(p->h_buf);
+  BatchQuery* Q = queries_of(p->h_buf);
+  memset(H, 0, sizeof(BatchHeader));
+  H->nq = nq;
+  H->quads_per_unit = qpu;
+  // probe class of every query, then the task table in class order (stable)
+  std::vector<int> cls(nq), order(nq);
+  for (int i = 0; i < nq; ++i) {
+    const sirius_pipeline_desc* q = &qs[i];
+    const bool pre = prebuilt(indexes, i);
+    const int64_t gcap = pre ? indexes[i].group_capacity : dim_layout(q->m, false, q->group_cap_hint, q->load_factor).gcap;
+    const bool wide = pre ? indexes[i].key_width == 8 : (q->pk_hi != nullptr || q->fk_hi != nullptr);
+    const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
+                     (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+    cls[i] = (wide ? 1 : 0) | (choose_mode(q->agg_mode, gcap + 1) == kAggSmem ? 2 : 0) | (vec ? 4 : 0);
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cls[x] < cls[y]; });
+  size_t off = 0;
+  int64_t max_smem_slots = 0;
+  uint32_t classes = 0;
+  for (int c = 0; c < 8; ++c) H->cls_q0[c] = H->cls_q1[c] = 0;
+  for (int k = 0; k < nq; ++k) {
+    const int i = order[k];
+    const sirius_pipeline_desc* q = &qs[i];
+    BatchQuery& b = Q[k];
+    memset(&b, 0, sizeof(b));
+    b.orig = i;
+    const bool pre = prebuilt(indexes, i);
+    DimLayout L;
+    char* dbase;
+    if (pre) {
+      L = layout_of_index(&indexes[i]);
+      dbase = (char*)indexes[i].d_mem;
+    } else {
+      L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint, q->load_factor);
+      dbase = sc.base + off;
+      off += L.total;
+    }
+    const RunLayout R = run_layout(L.gcap);
+    char* rbase = sc.base + off;
+    off += R.total;
+    b.d = dim_view(L, dbase);
+    const RunView r = run_view(R, rbase);
+    b.phdr = r.phdr;
+    b.out = PipeOut{results[i].keys, results[i].sum, results[i].count, results[i].min, results[i].max,
+                    results[i].out_cap, results[i].d_groups, results[i].d_status};
+    b.a.fk = q->fk;
+    b.a.fk_hi = q->fk_hi;
+    b.a.pred = q->pred;
+    b.a.val = q->val;
+    b.a.n = q->n;
+    b.a.op = q->op;
+    b.a.lit = q->literal;
+    b.a.aggs = q->aggs;
+    b.a.jcap = b.d.jcap;
+    b.a.jslots = b.d.jslots;
+    b.a.jhdr = b.d.jhdr;
+    b.a.dhdr = b.d.dhdr;
+    b.a.tab = r.aggs;
+    b.a.gslots = (uint32_t)R.gslots;
+    b.pk = q->pk;
+    b.pk_hi = q->pk_hi;
+    b.grp = q->grp;
+    b.flag = q->flag;
+    b.m = pre ? 0 : q->m;
+    b.gslots = R.gslots;
+    b.jpairs = pre ? 0 : (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16;
+    b.glimit = group_limit_for(L.gcap);
+    const int c = cls[i];
+    b.flags = ((c & 1) ? kQWide : 0) | ((c & 2) ? kQSmem : 0) | ((c & 4) ? kQVec : 0) | (pre ? 0 : kQBuild);
+    if ((c & 2) && R.gslots > max_smem_slots) max_smem_slots = R.gslots;
+    const bool probes = q->n > 0 && (pre || q->m > 0);
+    b.nu[0] = (b.jpairs + b.gslots + kInitUnit - 1) / kInitUnit;
+    b.nu[1] = (b.m + kBuildUnit - 1) / kBuildUnit;
+    const int64_t nq4 = q->n >> 2;
+    b.nu[2] = probes ? ((nq4 + qpu - 1) / qpu > 0 ? (nq4 + qpu - 1) / qpu : 1) : 0;
+    b.nu[3] = (b.gslots + kFinUnit - 1) / kFinUnit;
+    for (int ph = 0; ph < 4; ++ph) {
+      b.u0[ph] = H->total[ph];
+      H->total[ph] += b.nu[ph];
+    }
+    if (k == 0 || cls[order[k - 1]] != c) {
+      H->cls_q0[c] = k;
+      H->cls_u0[c] = b.u0[2];
+    }
+    H->cls_q1[c] = k + 1;
+    H->cls_u1[c] = H->total[2];
+    if (b.nu[2] > 0) classes |= 1u << c;
+  }
+  const size_t smem = (size_t)max_smem_slots * sizeof(Agg);
+  if (p->smem_for_grid != smem) {
+    for (int c = 0; c < 8; ++c) {
+      const size_t sm = (c & 2) ? smem : 0;
+      if (sm > 48 * 1024)
+        SIRIUS_CUDA_TRY(cudaFuncSetAttribute(probe_kernel_for(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemAggMaxBytes));
+      int per = 0;
+      SIRIUS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, probe_kernel_for(c), kProbeThreads, sm));
+      p->grid_probe[c] = sm_count() * (per > 0 ? per : 1);
+    }
+    p->grid_small = sm_count() * 8;
+    p->smem_for_grid = smem;
+  }
+
+  if (use_graph) {
+    if (!p->exec || p->graph_smem != smem || p->graph_classes != classes) {
+      if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      SIRIUS_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+      set_launch_counting(false);
+      sirius_status est = enqueue_batch(p, smem, classes, p->cap_stream, false);
+      set_launch_counting(true);
+      cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+      if (est != SIRIUS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return est;
+      }
+      if (ce != cudaSuccess) {
+        set_error("batch: graph capture failed: %s", cudaGetErrorString(ce));
+        return SIRIUS_ERR_CUDA;
+      }
+      ce = cudaGraphInstantiate(&p->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        p->exec = nullptr;
+        set_error("batch: graph instantiation failed: %s", cudaGetErrorString(ce));
+        return SIRIUS_ERR_CUDA;
+      }
+      p->graph_smem = smem;
+      p->graph_classes = classes;
+    }
+    PhaseTimer pt(s, SIRIUS_PHASE_BATCH_GRAPH);
+    SIRIUS_CUDA_TRY(cudaGraphLaunch(p->exec, s));
+    count_launch(4 + __builtin_popcount(classes));
+  } else {
+    st = enqueue_batch(p, smem, classes, s, true);
+    if (st != SIRIUS_OK) return st;
+  }
+  SIRIUS_CUDA_TRY(cudaEventRecord(p->done, s));
+  if (!results[0].sync) return SIRIUS_OK;
+  SIRIUS_CUDA_TRY(cudaEventSynchronize(p->done));
+  const BatchStatus* hs = status_of(p, p->h_buf);
+  sirius_status first = SIRIUS_OK;
+  for (int i = 0; i < nq; ++i) {
+    results[i].groups = hs[i].groups;
+    results[i].status = (int32_t)hs[i].status;
+    if (first == SIRIUS_OK && hs[i].status != 0) {
+      first = (sirius_status)hs[i].status;
+      set_error("batch: query %d finished with status %d", i, (int)hs[i].status);
+    }
+  }
+  return first;
+}
+
+extern "C" sirius_status sirius_run_pipeline_batch(const sirius_pipeline_desc* qs, int32_t nq,
+                                                   const sirius_dim_index* indexes, sirius_result* results,
+                                                   void* d_scratch, size_t scratch_bytes, sirius_stream stream) {
+  sirius_batch_plan p = nullptr;
+  sirius_status st = sirius_batch_plan_create(nq > 0 ? nq : 1, &p);
+  if (st != SIRIUS_OK) return st;
+  st = sirius_batch_plan_run(p, qs, nq, indexes, results, 0, 0, d_scratch, scratch_bytes, stream);
+  sirius_batch_plan_destroy(p);  // waits for the batch: the plan's task table feeds its kernels
+  return st;
+}

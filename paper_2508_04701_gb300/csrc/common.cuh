@@ -14,6 +14,7 @@ namespace sirius {
 void set_error(const char* fmt, ...);
 void clear_error();
 void count_launch(int k = 1);
+void set_launch_counting(bool on);  // off while a CUDA graph is captured: replays count instead
 int sm_count();
 
 // Phase timing (see sirius_profile_start): records a CUDA event pair around a scope when on.
@@ -114,11 +115,19 @@ __host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
 __host__ __device__ __forceinline__ uint32_t reduce_range(uint32_t h, uint32_t cap) {
   return (uint32_t)(((uint64_t)h * (uint64_t)cap) >> 32);
 }
+// Home slots start a 32-byte bucket (one DRAM sector): four 8-byte slots or two 16-byte slots.
+// Probing stays plain linear probing from the home slot; a probe just reads a whole bucket per
+// load.  Join-table capacities are multiples of 4.
 __host__ __device__ __forceinline__ uint32_t home_slot32(uint32_t key, uint32_t cap) {
-  return reduce_range(fmix32(key), cap);
+  return reduce_range(fmix32(key), cap >> 2) << 2;
 }
 __host__ __device__ __forceinline__ uint32_t home_slot64(uint64_t key, uint32_t cap) {
-  return reduce_range((uint32_t)(fmix64(key) >> 32), cap);
+  return reduce_range((uint32_t)(fmix64(key) >> 32), cap >> 1) << 1;
+}
+
+// 32-byte read-only load (a whole bucket); the address must be 32-byte aligned.
+__device__ __forceinline__ void ldg_bucket(const void* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
 __host__ __device__ __forceinline__ uint64_t pack_key64(int32_t hi, int32_t lo) {
   return ((uint64_t)(uint32_t)hi << 32) | (uint64_t)(uint32_t)lo;

@@ -148,7 +148,7 @@ extern "C" int64_t sirius_join_table_capacity(int64_t m, double load_factor) {
   int64_t c = (int64_t)((double)m / load_factor) + 1;
   if (c <= m) c = m + 1;
   if (c < 16) c = 16;
-  return c;
+  return (c + 3) & ~(int64_t)3;  // whole 32-byte buckets
 }
 
 extern "C" size_t sirius_join_table_bytes(int64_t capacity, int32_t key_width) {
@@ -167,6 +167,7 @@ extern "C" sirius_status sirius_hash_join_build(const int32_t* d_keys, const int
   SIRIUS_REQUIRE(m >= 0 && m <= kMaxRows && m < table->capacity && table->capacity < (1ll << 32),
                  "join build: m=%lld needs capacity > m (< 2^32), have %lld", (long long)m,
                  (long long)table->capacity);
+  SIRIUS_REQUIRE(table->capacity % 4 == 0, "join build: capacity must be a multiple of 4");
   SIRIUS_REQUIRE(m == 0 || d_keys, "join build: NULL keys");
   SIRIUS_REQUIRE(((uintptr_t)table->d_mem & 255) == 0, "join build: table memory must be 256-byte aligned");
   sirius_status st = join_build(d_keys, d_keys_hi, m, table->d_mem, table->capacity, s, true);

@@ -14,138 +14,55 @@
 //   - with global atomics otherwise (SUM and COUNT as reductions; MIN/MAX only when the value
 //     beats the one already stored).
 // Finalize compacts the slots with COUNT > 0 into the caller's output arrays.
-#include "tables.cuh"
+//
+// The build side ("dim index") and the per-query run state live in separate memory, so a dim
+// index can stay resident and serve many probes (the caching region, Sec. 3.2.3), and a fact
+// table in host memory can be streamed through the probe pass chunk by chunk while the next
+// chunk is copied (batch execution over data larger than device memory, Sec. 3.4).
 #include "pipeline.cuh"
 
 namespace sirius {
 
 namespace {
 
-__global__ void pipe_init_kernel(PipeHeader* phdr, JoinHeader* jhdr, ulonglong2* jwords2,
-                                 int64_t jpairs, int64_t* gkeys, Agg* aggs, int64_t gslots) {
+__global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* jwords2, int64_t jpairs,
+                                int64_t* gkeys, int64_t gslots) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (tid < 32) {
-    reinterpret_cast<uint64_t*>(phdr)[tid] = 0;
-    if (jhdr) reinterpret_cast<uint64_t*>(jhdr)[tid] = 0;
+    reinterpret_cast<uint64_t*>(dhdr)[tid] = 0;
+    reinterpret_cast<uint64_t*>(jhdr)[tid] = 0;
   }
   const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
   for (int64_t i = tid; i < jpairs; i += stride) jwords2[i] = ones;
-  for (int64_t i = tid; i < gslots; i += stride) {
-    gkeys[i] = kEmptyKey;
-    agg_identity(&aggs[i]);
-  }
+  for (int64_t i = tid; i < gslots; i += stride) gkeys[i] = kEmptyKey;
 }
 
 template <bool kWide>
-__global__ void pipe_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
-                                  const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
-                                  int64_t m, void* jslots, uint32_t jcap, JoinHeader* jhdr,
-                                  int64_t* gkeys, uint32_t gcap, PipeHeader* phdr,
-                                  unsigned long long glimit) {
+__global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
+                                 const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
+                                 int64_t m, DimView d, unsigned long long glimit) {
   bool dup = false;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t gk = group_key(grp[j], flag, j);
-    const int64_t gs = group_find_or_insert(gkeys, gcap, gk, &phdr->distinct, glimit);
-    if (gs < 0) {
-      set_status(&phdr->status, SIRIUS_ERR_TABLE_FULL);
-      continue;
-    }
-    bool ok;
-    if (kWide) {
-      ok = join_insert64((ulonglong2*)jslots, jcap, pack_key64(pk_hi[j], pk[j]), (uint32_t)gs, dup);
-    } else {
-      const uint32_t key = (uint32_t)pk[j];
-      ok = join_insert32((uint64_t*)jslots, jcap, key, (uint64_t)key | ((uint64_t)(uint32_t)gs << 32), dup);
-    }
-    if (!ok) set_status(&phdr->status, SIRIUS_ERR_TABLE_FULL);
+    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup))
+      set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
-  if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) jhdr->has_dups = 1;
+  if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
 }
 
-struct ProbeArgs {
-  const int32_t* fk;
-  const int32_t* fk_hi;
-  const int32_t* pred;
-  const int64_t* val;
-  int64_t n;
-  int32_t op;
-  int32_t lit;
-  uint32_t aggs;
-  uint32_t jcap;
-  const void* jslots;
-  const JoinHeader* jhdr;
-  Agg* tab;
-  uint32_t gslots;
-  const PipeHeader* phdr;
-};
-
-// One join-table slot as (key, payload); payload kEmpty32 = empty.
-template <bool kWide>
-__device__ __forceinline__ void load_slot(const void* slots, uint32_t s, uint64_t& key, uint32_t& payload) {
-  if (kWide) {
-    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(slots) + s);
-    key = v.x;
-    payload = (uint32_t)v.y;
-  } else {
-    const uint64_t v = __ldg(reinterpret_cast<const uint64_t*>(slots) + s);
-    key = (uint32_t)v;
-    payload = (uint32_t)(v >> 32);
-  }
-}
-
-template <int kMode>
-__device__ __forceinline__ void aggregate(const ProbeArgs& a, Agg* s_tab, uint32_t gs, int64_t v) {
-  if (kMode == kAggSmem) {
-    Agg* t = &s_tab[gs];
-    if (a.aggs & SIRIUS_AGG_SUM) atomicAdd(&t->sum, (unsigned long long)v);
-    atomicAdd(&t->count, 1ull);
-    if ((a.aggs & SIRIUS_AGG_MIN) && v < t->min) atomicMin(&t->min, (long long)v);
-    if ((a.aggs & SIRIUS_AGG_MAX) && v > t->max) atomicMax(&t->max, (long long)v);
-  } else {
-    agg_update_global(&a.tab[gs], v, a.aggs);
-  }
-}
-
-// Probe `cnt` (<= 4) rows whose selection bits, keys and values are given; the first slot of
-// every selected row is loaded before any walk continues.
-template <bool kWide, int kMode>
-__device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, bool dups, uint32_t bits,
-                                           const uint64_t (&key)[4], const int64_t (&v)[4]) {
-  uint32_t s[4];
-  uint64_t sk[4];
-  uint32_t pl[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    if ((bits >> r) & 1u) {
-      s[r] = kWide ? home_slot64(key[r], a.jcap) : home_slot32((uint32_t)key[r], a.jcap);
-      load_slot<kWide>(a.jslots, s[r], sk[r], pl[r]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    if (!((bits >> r) & 1u)) continue;
-    uint32_t slot = s[r];
-    uint64_t k = sk[r];
-    uint32_t p = pl[r];
-    for (uint32_t step = 0; step < a.jcap && p != kEmpty32; ++step) {
-      if (k == key[r]) {
-        aggregate<kMode>(a, s_tab, p, v[r]);
-        if (!dups) break;
-      }
-      slot = (slot + 1 == a.jcap) ? 0 : slot + 1;
-      load_slot<kWide>(a.jslots, slot, k, p);
-    }
-  }
+__global__ void run_init_kernel(PipeHeader* phdr, Agg* aggs, int64_t gslots) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid < 32) reinterpret_cast<uint64_t*>(phdr)[tid] = 0;
+  for (int64_t i = tid; i < gslots; i += (int64_t)gridDim.x * blockDim.x) agg_identity(&aggs[i]);
 }
 
 template <bool kWide, int kMode, bool kVec>
 __global__ void __launch_bounds__(512)
-pipe_probe_kernel(ProbeArgs a) {
+probe_kernel(ProbeArgs a) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   Agg* s_tab = reinterpret_cast<Agg*>(smem_raw);
-  if (a.phdr->status != 0) return;  // the build failed: nothing to aggregate
+  if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
   const bool dups = a.jhdr->has_dups != 0;
   if (kMode == kAggSmem) {
     for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) agg_identity(&s_tab[i]);
@@ -153,54 +70,11 @@ pipe_probe_kernel(ProbeArgs a) {
   }
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride) {
-    const int64_t row0 = q << 2;
-    uint32_t bits = 0;
-    uint64_t key[4];
-    int64_t v[4];
-    if (kVec) {
-      const int4 p4 = __ldcs(reinterpret_cast<const int4*>(a.pred) + q);
-      bits = (uint32_t)cmp_op(p4.x, a.lit, a.op) | ((uint32_t)cmp_op(p4.y, a.lit, a.op) << 1) |
-             ((uint32_t)cmp_op(p4.z, a.lit, a.op) << 2) | ((uint32_t)cmp_op(p4.w, a.lit, a.op) << 3);
-      if (!bits) continue;
-      const int4 k4 = __ldcs(reinterpret_cast<const int4*>(a.fk) + q);
-      if (kWide) {
-        const int4 h4 = __ldcs(reinterpret_cast<const int4*>(a.fk_hi) + q);
-        key[0] = pack_key64(h4.x, k4.x);
-        key[1] = pack_key64(h4.y, k4.y);
-        key[2] = pack_key64(h4.z, k4.z);
-        key[3] = pack_key64(h4.w, k4.w);
-      } else {
-        key[0] = (uint32_t)k4.x;
-        key[1] = (uint32_t)k4.y;
-        key[2] = (uint32_t)k4.z;
-        key[3] = (uint32_t)k4.w;
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (cmp_op(a.pred[row0 + r], a.lit, a.op)) bits |= 1u << r;
-      if (!bits) continue;
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        key[r] = kWide ? pack_key64(a.fk_hi[row0 + r], a.fk[row0 + r]) : (uint64_t)(uint32_t)a.fk[row0 + r];
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-    probe_rows<kWide, kMode>(a, s_tab, dups, bits, key, v);
-  }
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
+    probe_quad<kWide, kMode, kVec>(a, s_tab, dups, q);
   // ragged tail: the last n % 4 rows, one per thread of block 0
-  const int64_t tail0 = nq << 2;
-  if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - tail0) {
-    const int64_t r = tail0 + threadIdx.x;
-    if (cmp_op(a.pred[r], a.lit, a.op)) {
-      uint64_t key[4] = {0, 0, 0, 0};
-      int64_t v[4] = {0, 0, 0, 0};
-      key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
-      v[0] = a.val[r];
-      probe_rows<kWide, kMode>(a, s_tab, dups, 1u, key, v);
-    }
-  }
+  if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
+    probe_one<kWide, kMode>(a, s_tab, dups, (nq << 2) + threadIdx.x);
   if (kMode == kAggSmem) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) {
@@ -210,8 +84,8 @@ pipe_probe_kernel(ProbeArgs a) {
   }
 }
 
-__global__ void pipe_finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __restrict__ tab,
-                                     int64_t gslots, uint32_t aggs, PipeOut out, PipeHeader* phdr) {
+__global__ void finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __restrict__ tab, int64_t gslots,
+                                const DimHeader* __restrict__ dhdr, PipeOut out, PipeHeader* phdr) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t rounds = (gslots + stride - 1) / stride;
   for (int64_t r = 0; r < rounds; ++r) {
@@ -235,9 +109,11 @@ __global__ void pipe_finalize_kernel(const int64_t* __restrict__ gkeys, const Ag
     if (done == gridDim.x - 1) {
       __threadfence();
       const unsigned long long g = *(volatile unsigned long long*)&phdr->groups;
-      const int32_t st = *(volatile int32_t*)&phdr->status;
+      int32_t st = *(volatile const int32_t*)&dhdr->status;
+      if (st == 0 && (int64_t)g > out.cap) st = SIRIUS_ERR_CAPACITY;
+      phdr->status = st;
       if (out.d_groups) *out.d_groups = (int64_t)g;
-      if (out.d_status) *out.d_status = (st == 0 && (int64_t)g > out.cap) ? SIRIUS_ERR_CAPACITY : st;
+      if (out.d_status) *out.d_status = st;
     }
   }
 }
@@ -254,7 +130,7 @@ int occupancy_blocks(K kernel, int threads, size_t smem) {
 
 template <bool kWide, int kMode, bool kVec>
 sirius_status launch_probe(const ProbeArgs& a, int threads, int blocks_per_sm, size_t smem, cudaStream_t s) {
-  auto k = pipe_probe_kernel<kWide, kMode, kVec>;
+  auto k = probe_kernel<kWide, kMode, kVec>;
   if (kMode == kAggSmem) {
     static bool attr = false;
     if (!attr) {
@@ -262,7 +138,18 @@ sirius_status launch_probe(const ProbeArgs& a, int threads, int blocks_per_sm, s
       attr = true;
     }
   }
-  int per_sm = blocks_per_sm > 0 ? blocks_per_sm : occupancy_blocks(k, threads, smem);
+  int per_sm = blocks_per_sm;
+  if (per_sm <= 0) {
+    // residency depends on the block size (and on the shared-memory table when there is one)
+    static int occ_by_warps[17] = {};
+    if (kMode == kAggSmem) {
+      per_sm = occupancy_blocks(k, threads, smem);
+    } else {
+      int& c = occ_by_warps[(threads / 32) & 15];
+      if (c == 0) c = occupancy_blocks(k, threads, 0);
+      per_sm = c;
+    }
+  }
   int64_t want = ((a.n >> 2) + threads - 1) / threads;
   if (want < 1) want = 1;
   int64_t g = (int64_t)sm_count() * per_sm;
@@ -284,126 +171,178 @@ sirius_status dispatch_probe(const ProbeArgs& a, int mode, bool vec, int threads
 
 }  // namespace
 
-PipeLayout pipe_layout(const sirius_pipeline_desc* q) {
-  PipeLayout L;
-  L.key_width = q->fk_hi ? 8 : 4;
-  L.jcap = sirius_join_table_capacity(q->m, q->load_factor > 0 ? q->load_factor : 0.5);
-  const int64_t hint = q->group_cap_hint > 0 ? q->group_cap_hint : (q->m > 0 ? q->m : 1);
-  L.gcap = group_capacity_for(hint);
-  L.off_phdr = 0;
+// ------------------------------------------------------------------ layouts and validation
+DimLayout dim_layout(int64_t m, bool wide, int64_t hint, float lf) {
+  DimLayout L;
+  L.key_width = wide ? 8 : 4;
+  L.jcap = sirius_join_table_capacity(m, lf > 0 ? lf : 0.5);
+  L.gcap = group_capacity_for(hint > 0 ? hint : (m > 0 ? m : 1));
   L.off_join = 256;
-  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
-  L.off_aggs = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
-  L.total = align_up(L.off_aggs + (size_t)(L.gcap + 1) * sizeof(Agg), 256);
+  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (wide ? 16 : 8), 256);
+  L.total = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
   return L;
 }
 
-sirius_status validate_desc(const sirius_pipeline_desc* q) {
+RunLayout run_layout(int64_t gcap) {
+  RunLayout R;
+  R.gslots = gcap + 1;
+  R.off_aggs = 256;
+  R.total = align_up(R.off_aggs + (size_t)R.gslots * sizeof(Agg), 256);
+  return R;
+}
+
+DimView dim_view(const DimLayout& L, char* base) {
+  DimView d;
+  d.dhdr = (DimHeader*)base;
+  d.jhdr = (JoinHeader*)(base + L.off_join);
+  d.jslots = base + L.off_join + 256;
+  d.gkeys = (int64_t*)(base + L.off_gkeys);
+  d.jcap = (uint32_t)L.jcap;
+  d.gcap = (uint32_t)L.gcap;
+  d.key_width = L.key_width;
+  return d;
+}
+
+RunView run_view(const RunLayout& R, char* base) {
+  RunView r;
+  r.phdr = (PipeHeader*)base;
+  r.aggs = (Agg*)(base + R.off_aggs);
+  return r;
+}
+
+sirius_status validate_dim(const sirius_pipeline_desc* q) {
   SIRIUS_REQUIRE(q, "pipeline: NULL descriptor");
-  SIRIUS_REQUIRE(q->n >= 0 && q->n <= kMaxRows && q->m >= 0 && q->m <= kMaxRows,
-                 "pipeline: n=%lld m=%lld out of range", (long long)q->n, (long long)q->m);
-  SIRIUS_REQUIRE(q->n == 0 || (q->fk && q->pred && q->val), "pipeline: NULL fact column");
+  SIRIUS_REQUIRE(q->m >= 0 && q->m <= kMaxRows, "pipeline: m=%lld out of range", (long long)q->m);
   SIRIUS_REQUIRE(q->m == 0 || (q->pk && q->grp), "pipeline: NULL dim column");
-  SIRIUS_REQUIRE((q->fk_hi == nullptr) == (q->pk_hi == nullptr) || q->n == 0 || q->m == 0,
-                 "pipeline: fact and dim keys must both be one- or two-column");
-  SIRIUS_REQUIRE(q->op >= SIRIUS_LT && q->op <= SIRIUS_NE, "pipeline: bad comparison %d", q->op);
-  SIRIUS_REQUIRE(q->aggs <= SIRIUS_AGG_ALL, "pipeline: bad aggregate mask");
-  SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= 2, "pipeline: bad agg_mode %d", q->agg_mode);
   SIRIUS_REQUIRE(q->load_factor >= 0 && q->load_factor <= 0.95f, "pipeline: load_factor out of (0, 0.95]");
-  SIRIUS_REQUIRE(q->block_threads == 0 || (q->block_threads % 32 == 0 && q->block_threads >= 64 &&
-                                           q->block_threads <= 512),
-                 "pipeline: block_threads must be a multiple of 32 in [64, 512]");
   const int64_t hint = q->group_cap_hint > 0 ? q->group_cap_hint : q->m;
   SIRIUS_REQUIRE(hint < (1ll << 30), "pipeline: group_cap_hint too large");
   return SIRIUS_OK;
 }
 
-int choose_mode(const sirius_pipeline_desc* q, const PipeLayout& L) {
-  const bool fits = (L.gcap + 1) * (int64_t)sizeof(Agg) <= kSmemAggMaxBytes;
-  if (q->agg_mode == kAggGlobal || !fits) return kAggGlobal;
+sirius_status validate_fact(const sirius_pipeline_desc* q) {
+  SIRIUS_REQUIRE(q, "pipeline: NULL descriptor");
+  SIRIUS_REQUIRE(q->n >= 0 && q->n <= kMaxRows, "pipeline: n=%lld out of range", (long long)q->n);
+  SIRIUS_REQUIRE(q->n == 0 || (q->fk && q->pred && q->val), "pipeline: NULL fact column");
+  SIRIUS_REQUIRE(q->op >= SIRIUS_LT && q->op <= SIRIUS_NE, "pipeline: bad comparison %d", q->op);
+  SIRIUS_REQUIRE(q->aggs <= SIRIUS_AGG_ALL, "pipeline: bad aggregate mask");
+  SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= 2, "pipeline: bad agg_mode %d", q->agg_mode);
+  SIRIUS_REQUIRE(q->block_threads == 0 || (q->block_threads % 32 == 0 && q->block_threads >= 64 &&
+                                           q->block_threads <= 512),
+                 "pipeline: block_threads must be a multiple of 32 in [64, 512]");
+  SIRIUS_REQUIRE(q->blocks_per_sm >= 0 && q->blocks_per_sm <= 32, "pipeline: blocks_per_sm out of range");
+  return SIRIUS_OK;
+}
+
+static sirius_status validate_pair(const sirius_pipeline_desc* q) {
+  sirius_status st = validate_dim(q);
+  if (st != SIRIUS_OK) return st;
+  st = validate_fact(q);
+  if (st != SIRIUS_OK) return st;
+  SIRIUS_REQUIRE((q->fk_hi == nullptr) == (q->pk_hi == nullptr) || q->n == 0 || q->m == 0,
+                 "pipeline: fact and dim keys must both be one- or two-column");
+  return SIRIUS_OK;
+}
+
+int choose_mode(int agg_mode, int64_t gslots) {
+  const bool fits = gslots * (int64_t)sizeof(Agg) <= kSmemAggMaxBytes;
+  if (agg_mode == kAggGlobal || !fits) return kAggGlobal;
   return kAggSmem;
 }
 
-sirius_status pipe_launch(const sirius_pipeline_desc* q, const PipeLayout& L, char* base,
-                          const PipeOut& out, cudaStream_t s, bool build) {
-  PipeHeader* phdr = (PipeHeader*)(base + L.off_phdr);
-  JoinHeader* jhdr = (JoinHeader*)(base + L.off_join);
-  void* jslots = base + L.off_join + 256;
-  int64_t* gkeys = (int64_t*)(base + L.off_gkeys);
-  Agg* tab = (Agg*)(base + L.off_aggs);
+// ------------------------------------------------------------------ host phases
+sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char* base, cudaStream_t s) {
+  DimView d = dim_view(L, base);
+  const int64_t jpairs = (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16;
   const int64_t gslots = L.gcap + 1;
-  const int64_t jpairs = build ? (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16 : 0;
-  const int64_t init_n = jpairs > gslots ? jpairs : gslots;
   {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_INIT);
-    pipe_init_kernel<<<grid_for(init_n, 256), 256, 0, s>>>(phdr, build ? jhdr : nullptr, (ulonglong2*)jslots,
-                                                           jpairs, gkeys, tab, gslots);
+    dim_init_kernel<<<grid_for(jpairs > gslots ? jpairs : gslots, 256), 256, 0, s>>>(
+        d.dhdr, d.jhdr, (ulonglong2*)d.jslots, jpairs, d.gkeys, gslots);
     SIRIUS_LAUNCH_CHECK();
   }
-  if (build && q->m > 0) {
+  if (q->m > 0) {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_BUILD);
     const int g = grid_for(q->m, 256);
+    const unsigned long long lim = group_limit_for(L.gcap);
     if (L.key_width == 8)
-      pipe_build_kernel<true><<<g, 256, 0, s>>>(q->pk, q->pk_hi, q->grp, q->flag, q->m, jslots,
-                                                (uint32_t)L.jcap, jhdr, gkeys, (uint32_t)L.gcap, phdr,
-                                                group_limit_for(L.gcap));
+      dim_build_kernel<true><<<g, 256, 0, s>>>(q->pk, q->pk_hi, q->grp, q->flag, q->m, d, lim);
     else
-      pipe_build_kernel<false><<<g, 256, 0, s>>>(q->pk, nullptr, q->grp, q->flag, q->m, jslots,
-                                                 (uint32_t)L.jcap, jhdr, gkeys, (uint32_t)L.gcap, phdr,
-                                                 group_limit_for(L.gcap));
-    SIRIUS_LAUNCH_CHECK();
-  }
-  if (q->n > 0 && q->m > 0) {
-    ProbeArgs a;
-    a.fk = q->fk;
-    a.fk_hi = q->fk_hi;
-    a.pred = q->pred;
-    a.val = q->val;
-    a.n = q->n;
-    a.op = q->op;
-    a.lit = q->literal;
-    a.aggs = q->aggs;
-    a.jcap = (uint32_t)L.jcap;
-    a.jslots = jslots;
-    a.jhdr = jhdr;
-    a.tab = tab;
-    a.gslots = (uint32_t)gslots;
-    a.phdr = phdr;
-    const int mode = choose_mode(q, L);
-    const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
-                     (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
-    const int threads = q->block_threads > 0 ? q->block_threads : (mode == kAggSmem ? 512 : 256);
-    const size_t smem = mode == kAggSmem ? (size_t)gslots * sizeof(Agg) : 0;
-    PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
-    sirius_status st = L.key_width == 8 ? dispatch_probe<true>(a, mode, vec, threads, q->blocks_per_sm, smem, s)
-                                        : dispatch_probe<false>(a, mode, vec, threads, q->blocks_per_sm, smem, s);
-    if (st != SIRIUS_OK) return st;
-  }
-  {
-    PhaseTimer pt(s, SIRIUS_PHASE_PIPE_FINALIZE);
-    pipe_finalize_kernel<<<grid_for(gslots, 256), 256, 0, s>>>(gkeys, tab, gslots, q->aggs, out, phdr);
+      dim_build_kernel<false><<<g, 256, 0, s>>>(q->pk, nullptr, q->grp, q->flag, q->m, d, lim);
     SIRIUS_LAUNCH_CHECK();
   }
   return SIRIUS_OK;
 }
 
-sirius_status pipe_sync_result(const PipeLayout& L, char* base, sirius_result* r, cudaStream_t s) {
+sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s) {
+  RunView r = run_view(R, base);
+  PhaseTimer pt(s, SIRIUS_PHASE_PIPE_INIT);
+  run_init_kernel<<<grid_for(R.gslots, 256), 256, 0, s>>>(r.phdr, r.aggs, R.gslots);
+  SIRIUS_LAUNCH_CHECK();
+  return SIRIUS_OK;
+}
+
+sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
+                        cudaStream_t s) {
+  if (q->n == 0) return SIRIUS_OK;
+  ProbeArgs a;
+  a.fk = q->fk;
+  a.fk_hi = q->fk_hi;
+  a.pred = q->pred;
+  a.val = q->val;
+  a.n = q->n;
+  a.op = q->op;
+  a.lit = q->literal;
+  a.aggs = q->aggs;
+  a.jcap = d.jcap;
+  a.jslots = d.jslots;
+  a.jhdr = d.jhdr;
+  a.dhdr = d.dhdr;
+  a.tab = r.aggs;
+  a.gslots = (uint32_t)gslots;
+  const int mode = choose_mode(q->agg_mode, gslots);
+  const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
+                   (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+  const int threads = q->block_threads > 0 ? q->block_threads : (mode == kAggSmem ? 512 : 256);
+  const size_t smem = mode == kAggSmem ? (size_t)gslots * sizeof(Agg) : 0;
+  PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
+  return d.key_width == 8 ? dispatch_probe<true>(a, mode, vec, threads, q->blocks_per_sm, smem, s)
+                          : dispatch_probe<false>(a, mode, vec, threads, q->blocks_per_sm, smem, s);
+}
+
+sirius_status run_finalize(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
+                           const PipeOut& out, cudaStream_t s) {
+  (void)q;
+  PhaseTimer pt(s, SIRIUS_PHASE_PIPE_FINALIZE);
+  finalize_kernel<<<grid_for(gslots, 256), 256, 0, s>>>(d.gkeys, r.aggs, gslots, d.dhdr, out, r.phdr);
+  SIRIUS_LAUNCH_CHECK();
+  return SIRIUS_OK;
+}
+
+sirius_status read_run_status(const RunView& r, sirius_result* res, cudaStream_t s) {
   PipeHeader h;
-  SIRIUS_CUDA_TRY(cudaMemcpyAsync(&h, base + L.off_phdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SIRIUS_CUDA_TRY(cudaMemcpyAsync(&h, r.phdr, sizeof(h), cudaMemcpyDeviceToHost, s));
   SIRIUS_CUDA_TRY(cudaStreamSynchronize(s));
-  r->groups = (int64_t)h.groups;
-  r->status = h.status;
-  if (h.status) {
-    set_error("pipeline: device status %d (%s)", h.status,
-              h.status == SIRIUS_ERR_TABLE_FULL ? "more distinct group keys than group_cap_hint allows"
-                                                : "device error");
-    return (sirius_status)h.status;
+  res->groups = (int64_t)h.groups;
+  res->status = h.status;
+  if (h.status == SIRIUS_ERR_TABLE_FULL) {
+    set_error("pipeline: more distinct group keys in the dim than group_cap_hint allows");
+  } else if (h.status == SIRIUS_ERR_CAPACITY) {
+    set_error("pipeline: %llu groups exceed out_cap %lld", h.groups, (long long)res->out_cap);
+  } else if (h.status) {
+    set_error("pipeline: device status %d", h.status);
   }
-  if ((int64_t)h.groups > r->out_cap) {
-    r->status = SIRIUS_ERR_CAPACITY;
-    set_error("pipeline: %llu groups exceed out_cap %lld", h.groups, (long long)r->out_cap);
-    return SIRIUS_ERR_CAPACITY;
-  }
+  return (sirius_status)h.status;
+}
+
+static PipeOut pipe_out(const sirius_result* r) {
+  return PipeOut{r->keys, r->sum, r->count, r->min, r->max, r->out_cap, r->d_groups, r->d_status};
+}
+
+static sirius_status validate_result(const sirius_result* r) {
+  SIRIUS_REQUIRE(r, "pipeline: NULL result");
+  SIRIUS_REQUIRE(r->out_cap >= 0, "pipeline: negative out_cap");
+  SIRIUS_REQUIRE(r->out_cap == 0 || r->keys || r->count, "pipeline: no output arrays");
   return SIRIUS_OK;
 }
 
@@ -411,29 +350,257 @@ sirius_status pipe_sync_result(const PipeLayout& L, char* base, sirius_result* r
 
 using namespace sirius;
 
+// ------------------------------------------------------------------ single query
 extern "C" size_t sirius_pipeline_scratch_bytes(const sirius_pipeline_desc* q) {
   if (!q) return 0;
-  return pipe_layout(q).total;
+  const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint,
+                                 q->load_factor);
+  return L.total + run_layout(L.gcap).total;
 }
 
 extern "C" sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, sirius_result* result,
                                              void* d_scratch, size_t scratch_bytes, sirius_stream stream) {
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
-  sirius_status st = validate_desc(q);
+  sirius_status st = validate_pair(q);
   if (st != SIRIUS_OK) return st;
-  SIRIUS_REQUIRE(result, "pipeline: NULL result");
-  SIRIUS_REQUIRE(result->out_cap >= 0, "pipeline: negative out_cap");
-  SIRIUS_REQUIRE(result->out_cap == 0 || result->keys || result->count,
-                 "pipeline: no output arrays");
-  const PipeLayout L = pipe_layout(q);
+  st = validate_result(result);
+  if (st != SIRIUS_OK) return st;
+  const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint,
+                                 q->load_factor);
+  const RunLayout R = run_layout(L.gcap);
   Scratch sc;
-  st = sc.acquire(d_scratch, scratch_bytes, L.total, s);
+  st = sc.acquire(d_scratch, scratch_bytes, L.total + R.total, s);
   if (st != SIRIUS_OK) return st;
-  PipeOut out{result->keys, result->sum, result->count, result->min, result->max, result->out_cap,
-              result->d_groups, result->d_status};
-  st = pipe_launch(q, L, sc.base, out, s, true);
-  if (st != SIRIUS_OK) return st;
-  if (result->sync) return pipe_sync_result(L, sc.base, result, s);
+  const DimView d = dim_view(L, sc.base);
+  const RunView r = run_view(R, sc.base + L.total);
+  if ((st = dim_build(q, L, sc.base, s)) != SIRIUS_OK) return st;
+  if ((st = run_init(R, sc.base + L.total, s)) != SIRIUS_OK) return st;
+  if (q->m > 0 && (st = run_probe(q, d, r, R.gslots, s)) != SIRIUS_OK) return st;
+  if ((st = run_finalize(q, d, r, R.gslots, pipe_out(result), s)) != SIRIUS_OK) return st;
+  if (result->sync) return read_run_status(r, result, s);
   return SIRIUS_OK;
+}
+
+// ------------------------------------------------------------------ resident build side
+extern "C" size_t sirius_dim_index_bytes(const sirius_pipeline_desc* q) {
+  if (!q) return 0;
+  return dim_layout(q->m, q->pk_hi != nullptr, q->group_cap_hint, q->load_factor).total;
+}
+
+extern "C" sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, sirius_dim_index* idx,
+                                                int32_t* h_status, sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  sirius_status st = validate_dim(q);
+  if (st != SIRIUS_OK) return st;
+  SIRIUS_REQUIRE(idx && idx->d_mem, "dim index: NULL memory");
+  SIRIUS_REQUIRE(((uintptr_t)idx->d_mem & 255) == 0, "dim index: memory must be 256-byte aligned");
+  const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr, q->group_cap_hint, q->load_factor);
+  if (idx->bytes < L.total) {
+    set_error("dim index: %zu bytes given, %zu needed", idx->bytes, L.total);
+    return SIRIUS_ERR_SCRATCH;
+  }
+  idx->join_capacity = L.jcap;
+  idx->group_capacity = L.gcap;
+  idx->key_width = L.key_width;
+  if ((st = dim_build(q, L, (char*)idx->d_mem, s)) != SIRIUS_OK) return st;
+  if (h_status) {
+    DimHeader h;
+    SIRIUS_CUDA_TRY(cudaMemcpyAsync(&h, idx->d_mem, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SIRIUS_CUDA_TRY(cudaStreamSynchronize(s));
+    *h_status = h.status;
+    if (h.status) {
+      set_error("dim index: device status %d (more distinct group keys than group_cap_hint allows)", h.status);
+      return (sirius_status)h.status;
+    }
+  }
+  return SIRIUS_OK;
+}
+
+static DimLayout layout_of(const sirius_dim_index* idx) {
+  DimLayout L;
+  L.key_width = idx->key_width;
+  L.jcap = idx->join_capacity;
+  L.gcap = idx->group_capacity;
+  L.off_join = 256;
+  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
+  L.total = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
+  return L;
+}
+
+extern "C" size_t sirius_probe_scratch_bytes(const sirius_dim_index* idx) {
+  if (!idx) return 0;
+  return run_layout(idx->group_capacity).total;
+}
+
+extern "C" sirius_status sirius_run_probe(const sirius_pipeline_desc* q, const sirius_dim_index* idx,
+                                          sirius_result* result, void* d_scratch, size_t scratch_bytes,
+                                          sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  sirius_status st = validate_fact(q);
+  if (st != SIRIUS_OK) return st;
+  st = validate_result(result);
+  if (st != SIRIUS_OK) return st;
+  SIRIUS_REQUIRE(idx && idx->d_mem && idx->join_capacity > 0 && idx->group_capacity > 0,
+                 "probe: dim index not built");
+  SIRIUS_REQUIRE(idx->key_width == (q->fk_hi ? 8 : 4) || q->n == 0, "probe: key width differs from the dim index");
+  const DimLayout L = layout_of(idx);
+  const RunLayout R = run_layout(L.gcap);
+  Scratch sc;
+  st = sc.acquire(d_scratch, scratch_bytes, R.total, s);
+  if (st != SIRIUS_OK) return st;
+  const DimView d = dim_view(L, (char*)idx->d_mem);
+  const RunView r = run_view(R, sc.base);
+  if ((st = run_init(R, sc.base, s)) != SIRIUS_OK) return st;
+  if ((st = run_probe(q, d, r, R.gslots, s)) != SIRIUS_OK) return st;
+  if ((st = run_finalize(q, d, r, R.gslots, pipe_out(result), s)) != SIRIUS_OK) return st;
+  if (result->sync) return read_run_status(r, result, s);
+  return SIRIUS_OK;
+}
+
+// ------------------------------------------------------------------ host-resident columns
+namespace {
+struct HostLayout {
+  DimLayout L;
+  RunLayout R;
+  int64_t chunk = 0;
+  size_t off_run = 0, off_dimcols = 0, off_chunks = 0, chunk_bytes = 0, off_out = 0, total = 0;
+};
+
+HostLayout host_layout(const sirius_pipeline_desc* q, int64_t chunk_rows, int64_t out_cap) {
+  HostLayout H;
+  const bool wide = q->pk_hi != nullptr || q->fk_hi != nullptr;
+  H.L = dim_layout(q->m, wide, q->group_cap_hint, q->load_factor);
+  H.R = run_layout(H.L.gcap);
+  H.chunk = chunk_rows > 0 ? chunk_rows : (16ll << 20);
+  if (H.chunk > q->n && q->n > 0) H.chunk = (q->n + 3) / 4 * 4;
+  H.chunk = (H.chunk + 3) / 4 * 4;
+  H.off_run = H.L.total;
+  H.off_dimcols = H.off_run + H.R.total;
+  const size_t m = (size_t)q->m;
+  const size_t dimcols = align_up(m * 4, 256) * (wide ? 3 : 2) + align_up(q->flag ? m : 0, 256);
+  H.off_chunks = H.off_dimcols + dimcols;
+  H.chunk_bytes = align_up((size_t)H.chunk * 4, 256) * (wide ? 3 : 2) + align_up((size_t)H.chunk * 8, 256);
+  H.off_out = H.off_chunks + 2 * H.chunk_bytes;
+  H.total = H.off_out + 5 * align_up((size_t)(out_cap > 0 ? out_cap : 1) * 8, 256) + 256;
+  return H;
+}
+}  // namespace
+
+extern "C" size_t sirius_pipeline_host_scratch_bytes(const sirius_pipeline_desc* q, int64_t chunk_rows,
+                                                     int64_t out_cap) {
+  if (!q) return 0;
+  return host_layout(q, chunk_rows, out_cap).total;
+}
+
+extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q, sirius_result* result,
+                                                  int64_t chunk_rows, void* d_scratch, size_t scratch_bytes,
+                                                  sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  sirius_status st = validate_pair(q);
+  if (st != SIRIUS_OK) return st;
+  st = validate_result(result);
+  if (st != SIRIUS_OK) return st;
+  SIRIUS_REQUIRE(chunk_rows >= 0, "pipeline_host: negative chunk_rows");
+  const HostLayout H = host_layout(q, chunk_rows, result->out_cap);
+  Scratch sc;
+  st = sc.acquire(d_scratch, scratch_bytes, H.total, s);
+  if (st != SIRIUS_OK) return st;
+  char* base = sc.base;
+  const bool wide = H.L.key_width == 8;
+  const size_t m = (size_t)q->m;
+
+  // dim columns to the device, then the build (on the compute stream)
+  sirius_pipeline_desc dq = *q;
+  {
+    PhaseTimer pt(s, SIRIUS_PHASE_COPY);
+    char* p = base + H.off_dimcols;
+    auto put = [&](const void* src, size_t bytes, void** dst) -> cudaError_t {
+      *dst = p;
+      p += align_up(bytes, 256);
+      return bytes ? cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    void* d_pk = nullptr;
+    void* d_pk_hi = nullptr;
+    void* d_grp = nullptr;
+    void* d_flag = nullptr;
+    SIRIUS_CUDA_TRY(put(q->pk, m * 4, &d_pk));
+    if (wide) SIRIUS_CUDA_TRY(put(q->pk_hi, m * 4, &d_pk_hi));
+    SIRIUS_CUDA_TRY(put(q->grp, m * 4, &d_grp));
+    if (q->flag) SIRIUS_CUDA_TRY(put(q->flag, m, &d_flag));
+    dq.pk = (const int32_t*)d_pk;
+    dq.pk_hi = (const int32_t*)d_pk_hi;
+    dq.grp = (const int32_t*)d_grp;
+    dq.flag = (const int8_t*)d_flag;
+  }
+  const DimView d = dim_view(H.L, base);
+  const RunView r = run_view(H.R, base + H.off_run);
+  if ((st = dim_build(&dq, H.L, base, s)) != SIRIUS_OK) return st;
+  if ((st = run_init(H.R, base + H.off_run, s)) != SIRIUS_OK) return st;
+
+  // fact chunks: copies on a second stream, double-buffered against the probe pass
+  cudaStream_t c = nullptr;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  SIRIUS_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+  sirius_status fail = SIRIUS_OK;
+  for (int b = 0; b < 2 && fail == SIRIUS_OK; ++b) {
+    if (cudaEventCreateWithFlags(&ev_ready[b], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_free[b], cudaEventDisableTiming) != cudaSuccess)
+      fail = SIRIUS_ERR_CUDA;
+  }
+  const int64_t nchunks = q->m > 0 ? (q->n + H.chunk - 1) / H.chunk : 0;
+  for (int64_t i = 0; i < nchunks && fail == SIRIUS_OK; ++i) {
+    const int b = (int)(i & 1);
+    const int64_t r0 = i * H.chunk;
+    const int64_t rows = (q->n - r0) < H.chunk ? (q->n - r0) : H.chunk;
+    char* buf = base + H.off_chunks + (size_t)b * H.chunk_bytes;
+    const size_t a4 = align_up((size_t)H.chunk * 4, 256);
+    sirius_pipeline_desc cq = dq;
+    cq.fk = (const int32_t*)buf;
+    cq.pred = (const int32_t*)(buf + a4);
+    cq.fk_hi = wide ? (const int32_t*)(buf + 2 * a4) : nullptr;
+    cq.val = (const int64_t*)(buf + (wide ? 3 : 2) * a4);
+    cq.n = rows;
+    if (i >= 2 && cudaStreamWaitEvent(c, ev_free[b], 0) != cudaSuccess) { fail = SIRIUS_ERR_CUDA; break; }
+    if (cudaMemcpyAsync((void*)cq.fk, q->fk + r0, rows * 4, cudaMemcpyHostToDevice, c) != cudaSuccess ||
+        cudaMemcpyAsync((void*)cq.pred, q->pred + r0, rows * 4, cudaMemcpyHostToDevice, c) != cudaSuccess ||
+        (wide && cudaMemcpyAsync((void*)cq.fk_hi, q->fk_hi + r0, rows * 4, cudaMemcpyHostToDevice, c) != cudaSuccess) ||
+        cudaMemcpyAsync((void*)cq.val, q->val + r0, rows * 8, cudaMemcpyHostToDevice, c) != cudaSuccess ||
+        cudaEventRecord(ev_ready[b], c) != cudaSuccess || cudaStreamWaitEvent(s, ev_ready[b], 0) != cudaSuccess) {
+      fail = SIRIUS_ERR_CUDA;
+      break;
+    }
+    if ((st = run_probe(&cq, d, r, H.R.gslots, s)) != SIRIUS_OK) { fail = st; break; }
+    if (cudaEventRecord(ev_free[b], s) != cudaSuccess) { fail = SIRIUS_ERR_CUDA; break; }
+  }
+  if (fail == SIRIUS_ERR_CUDA) set_error("pipeline_host: CUDA error %s", cudaGetErrorString(cudaGetLastError()));
+  // results: finalize into device arrays, then copy the G rows back into the host arrays
+  int64_t* dout[5];
+  for (int k = 0; k < 5; ++k)
+    dout[k] = (int64_t*)(base + H.off_out + (size_t)k * align_up((size_t)(result->out_cap > 0 ? result->out_cap : 1) * 8, 256));
+  PipeOut out{result->keys ? dout[0] : nullptr, result->sum ? dout[1] : nullptr, result->count ? dout[2] : nullptr,
+              result->min ? dout[3] : nullptr, result->max ? dout[4] : nullptr, result->out_cap, nullptr, nullptr};
+  if (fail == SIRIUS_OK) fail = run_finalize(&dq, d, r, H.R.gslots, out, s);
+  if (fail == SIRIUS_OK) {
+    fail = read_run_status(r, result, s);
+    if (fail == SIRIUS_OK && result->groups > 0) {
+      PhaseTimer pt(s, SIRIUS_PHASE_COPY);
+      int64_t* hosts[5] = {result->keys, result->sum, result->count, result->min, result->max};
+      for (int k = 0; k < 5 && fail == SIRIUS_OK; ++k)
+        if (hosts[k] && cudaMemcpyAsync(hosts[k], dout[k], (size_t)result->groups * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+          fail = SIRIUS_ERR_CUDA;
+      if (fail == SIRIUS_OK && cudaStreamSynchronize(s) != cudaSuccess) fail = SIRIUS_ERR_CUDA;
+      if (fail == SIRIUS_ERR_CUDA) set_error("pipeline_host: result copy failed");
+    }
+  }
+  cudaStreamSynchronize(c);
+  for (int b = 0; b < 2; ++b) {
+    if (ev_ready[b]) cudaEventDestroy(ev_ready[b]);
+    if (ev_free[b]) cudaEventDestroy(ev_free[b]);
+  }
+  cudaStreamDestroy(c);
+  return fail;
 }

@@ -1,4 +1,5 @@
-// Internal interface of the fused pipeline, shared by the single-query and batched paths.
+// Internal interface of the fused pipeline, shared by the single-query, host-streamed and
+// batched paths: memory layouts, the probe pass's per-row device routines, host phases.
 #pragma once
 
 #include "tables.cuh"
@@ -8,20 +9,49 @@ namespace sirius {
 enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2 };
 constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up to 3072 slots
 
+// Build side ("dim index"): [DimHeader | JoinHeader + join slots | group keys[gcap + 1]].
+// It depends on the dim table only, so it can stay resident and serve many probes.
+struct DimHeader {
+  int32_t status;                // first device error of the build (TABLE_FULL)
+  uint32_t pad0;
+  unsigned long long distinct;   // group slots claimed
+  unsigned long long pad[30];
+};
+static_assert(sizeof(DimHeader) == 256, "dim header is 256 bytes");
+
+// Per-query run state: [PipeHeader | Agg[gcap + 1]].
 struct PipeHeader {
-  int32_t status;
+  int32_t status;                // final status of the query (dim status, then CAPACITY)
   uint32_t blocks_done;          // finalize blocks that have finished
-  unsigned long long distinct;   // group slots claimed by the build
   unsigned long long groups;     // G
-  unsigned long long pad[29];
+  unsigned long long pad[30];
 };
 static_assert(sizeof(PipeHeader) == 256, "pipeline header is 256 bytes");
 
-// Scratch layout of one pipeline: [PipeHeader | JoinHeader + join slots | group keys | aggs].
-struct PipeLayout {
+struct DimLayout {
   int key_width = 4;
   int64_t jcap = 0, gcap = 0;
-  size_t off_phdr = 0, off_join = 0, off_gkeys = 0, off_aggs = 0, total = 0;
+  size_t off_join = 256, off_gkeys = 0, total = 0;
+};
+
+struct RunLayout {
+  int64_t gslots = 0;
+  size_t off_aggs = 256, total = 0;
+};
+
+struct DimView {
+  DimHeader* dhdr;
+  JoinHeader* jhdr;
+  void* jslots;
+  int64_t* gkeys;
+  uint32_t jcap;
+  uint32_t gcap;
+  int key_width;
+};
+
+struct RunView {
+  PipeHeader* phdr;
+  Agg* aggs;
 };
 
 struct PipeOut {
@@ -35,11 +65,182 @@ struct PipeOut {
   int32_t* d_status;
 };
 
-PipeLayout pipe_layout(const sirius_pipeline_desc* q);
-sirius_status validate_desc(const sirius_pipeline_desc* q);
-int choose_mode(const sirius_pipeline_desc* q, const PipeLayout& L);
-sirius_status pipe_launch(const sirius_pipeline_desc* q, const PipeLayout& L, char* base,
-                          const PipeOut& out, cudaStream_t s, bool build);
-sirius_status pipe_sync_result(const PipeLayout& L, char* base, sirius_result* r, cudaStream_t s);
+// Everything the probe pass reads for one query.
+struct ProbeArgs {
+  const int32_t* fk;
+  const int32_t* fk_hi;
+  const int32_t* pred;
+  const int64_t* val;
+  int64_t n;
+  int32_t op;
+  int32_t lit;
+  uint32_t aggs;
+  uint32_t jcap;
+  const void* jslots;
+  const JoinHeader* jhdr;
+  const DimHeader* dhdr;
+  Agg* tab;
+  uint32_t gslots;
+};
+
+// ------------------------------------------------------------------ probe pass, per row
+// One join-table slot as (key, payload); payload kEmpty32 = empty.  The table is read-only
+// during the probe pass, so slots go through the non-coherent read-only path.
+template <bool kWide>
+__device__ __forceinline__ void load_slot(const void* slots, uint32_t s, uint64_t& key, uint32_t& payload) {
+  if (kWide) {
+    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(slots) + s);
+    key = v.x;
+    payload = (uint32_t)v.y;
+  } else {
+    const uint64_t v = __ldg(reinterpret_cast<const uint64_t*>(slots) + s);
+    key = (uint32_t)v;
+    payload = (uint32_t)(v >> 32);
+  }
+}
+
+template <int kMode>
+__device__ __forceinline__ void aggregate(const ProbeArgs& a, Agg* s_tab, uint32_t gs, int64_t v) {
+  if (kMode == kAggSmem) {
+    Agg* t = &s_tab[gs];
+    if (a.aggs & SIRIUS_AGG_SUM) atomicAdd(&t->sum, (unsigned long long)v);
+    atomicAdd(&t->count, 1ull);
+    if ((a.aggs & SIRIUS_AGG_MIN) && v < t->min) atomicMin(&t->min, (long long)v);
+    if ((a.aggs & SIRIUS_AGG_MAX) && v > t->max) atomicMax(&t->max, (long long)v);
+  } else {
+    agg_update_global(&a.tab[gs], v, a.aggs);
+  }
+}
+
+// One 32-byte bucket starting at slot s: four 8-byte slots, or two 16-byte slots.
+template <bool kWide>
+__device__ __forceinline__ void load_bucket(const void* slots, uint32_t s, uint64_t (&w)[4]) {
+  const char* p = reinterpret_cast<const char*>(slots) + (size_t)s * (kWide ? 16 : 8);
+  ldg_bucket(p, w[0], w[1], w[2], w[3]);
+}
+
+// Probe up to four rows (bit r of `bits` set = row r selected).  The home bucket of every
+// selected row is loaded before any row is examined, so four sector misses are in flight
+// together; a walk continues bucket by bucket only past full buckets.
+template <bool kWide, int kMode>
+__device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, bool dups, uint32_t bits,
+                                           const uint64_t (&key)[4], const int64_t (&v)[4]) {
+  constexpr int kPer = kWide ? 2 : 4;  // slots per bucket
+  uint32_t s[4];
+  uint64_t w[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if ((bits >> r) & 1u) {
+      s[r] = kWide ? home_slot64(key[r], a.jcap) : home_slot32((uint32_t)key[r], a.jcap);
+      load_bucket<kWide>(a.jslots, s[r], w[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (!((bits >> r) & 1u)) continue;
+    uint32_t slot = s[r];
+    for (uint32_t step = 0; step < a.jcap; step += kPer) {
+      bool stop = false;
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {  // fully unrolled: bucket words stay in registers
+        const uint64_t k = kWide ? w[r][2 * j] : (uint64_t)(uint32_t)w[r][j];
+        const uint32_t p = kWide ? (uint32_t)w[r][2 * j + 1] : (uint32_t)(w[r][j] >> 32);
+        if (!stop) {
+          if (p == kEmpty32) {
+            stop = true;
+          } else if (k == key[r]) {
+            aggregate<kMode>(a, s_tab, p, v[r]);
+            stop = !dups;
+          }
+        }
+      }
+      if (stop) break;
+      slot += kPer;
+      if (slot >= a.jcap) slot = 0;
+      load_bucket<kWide>(a.jslots, slot, w[r]);
+    }
+  }
+}
+
+// Filter, probe and aggregate the four rows of quad q (rows 4q .. 4q+3, all < n).
+template <bool kWide, int kMode, bool kVec>
+__device__ __forceinline__ void probe_quad(const ProbeArgs& a, Agg* s_tab, bool dups, int64_t q) {
+  const int64_t row0 = q << 2;
+  uint32_t bits = 0;
+  uint64_t key[4];
+  int64_t v[4];
+  if (kVec) {
+    const int4 p4 = __ldcs(reinterpret_cast<const int4*>(a.pred) + q);
+    bits = (uint32_t)cmp_op(p4.x, a.lit, a.op) | ((uint32_t)cmp_op(p4.y, a.lit, a.op) << 1) |
+           ((uint32_t)cmp_op(p4.z, a.lit, a.op) << 2) | ((uint32_t)cmp_op(p4.w, a.lit, a.op) << 3);
+    if (!bits) return;
+    const int4 k4 = __ldcs(reinterpret_cast<const int4*>(a.fk) + q);
+    if (kWide) {
+      const int4 h4 = __ldcs(reinterpret_cast<const int4*>(a.fk_hi) + q);
+      key[0] = pack_key64(h4.x, k4.x);
+      key[1] = pack_key64(h4.y, k4.y);
+      key[2] = pack_key64(h4.z, k4.z);
+      key[3] = pack_key64(h4.w, k4.w);
+    } else {
+      key[0] = (uint32_t)k4.x;
+      key[1] = (uint32_t)k4.y;
+      key[2] = (uint32_t)k4.z;
+      key[3] = (uint32_t)k4.w;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (cmp_op(a.pred[row0 + r], a.lit, a.op)) bits |= 1u << r;
+    if (!bits) return;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      key[r] = kWide ? pack_key64(a.fk_hi[row0 + r], a.fk[row0 + r]) : (uint64_t)(uint32_t)a.fk[row0 + r];
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
+  probe_rows<kWide, kMode>(a, s_tab, dups, bits, key, v);
+}
+
+// Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
+template <bool kWide, int kMode>
+__device__ __forceinline__ void probe_one(const ProbeArgs& a, Agg* s_tab, bool dups, int64_t r) {
+  if (!cmp_op(a.pred[r], a.lit, a.op)) return;
+  uint64_t key[4] = {0, 0, 0, 0};
+  int64_t v[4] = {0, 0, 0, 0};
+  key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
+  v[0] = a.val[r];
+  probe_rows<kWide, kMode>(a, s_tab, dups, 1u, key, v);
+}
+
+// Build step of one dim row j: enter its group key into the group table (slot gs), then
+// (pk -> gs) into the join table.  Returns false on TABLE_FULL.
+template <bool kWide>
+__device__ __forceinline__ bool dim_build_row(const int32_t* pk, const int32_t* pk_hi, const int32_t* grp,
+                                              const int8_t* flag, int64_t j, const DimView& d,
+                                              unsigned long long glimit, bool& dup) {
+  const int64_t gk = group_key(grp[j], flag, j);
+  const int64_t gs = group_find_or_insert(d.gkeys, d.gcap, gk, &d.dhdr->distinct, glimit);
+  if (gs < 0) return false;
+  if (kWide)
+    return join_insert64((ulonglong2*)d.jslots, d.jcap, pack_key64(pk_hi[j], pk[j]), (uint32_t)gs, dup);
+  const uint32_t key = (uint32_t)pk[j];
+  return join_insert32((uint64_t*)d.jslots, d.jcap, key, (uint64_t)key | ((uint64_t)(uint32_t)gs << 32), dup);
+}
+
+// ------------------------------------------------------------------ host phases
+DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor);
+RunLayout run_layout(int64_t gcap);
+DimView dim_view(const DimLayout& L, char* base);
+RunView run_view(const RunLayout& R, char* base);
+sirius_status validate_dim(const sirius_pipeline_desc* q);
+sirius_status validate_fact(const sirius_pipeline_desc* q);
+int choose_mode(int agg_mode, int64_t gslots);
+sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char* base, cudaStream_t s);
+sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s);
+sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
+                        cudaStream_t s);
+sirius_status run_finalize(const sirius_pipeline_desc* q, const DimView& d, const RunView& r,
+                           int64_t gslots, const PipeOut& out, cudaStream_t s);
+sirius_status read_run_status(const RunView& r, sirius_result* res, cudaStream_t s);
 
 }  // namespace sirius

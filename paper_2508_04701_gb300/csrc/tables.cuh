@@ -93,20 +93,23 @@ struct __align__(32) Agg {
   long long max;
 };
 
+// Global aggregation: four fire-and-forget reductions (no result is read back, so they
+// compile to RED operations executed at L2).  Reading MIN/MAX first to skip the atomic would
+// put an L2 round trip, ordered behind the reductions just issued to the same line, on every
+// row's critical path.
 __device__ __forceinline__ void agg_update_global(Agg* a, int64_t v, uint32_t aggs) {
   if (aggs & SIRIUS_AGG_SUM) atomicAdd(&a->sum, (unsigned long long)v);
   atomicAdd(&a->count, 1ull);
-  // MIN/MAX only move one way: a value no better than one already seen skips the atomic.
-  if ((aggs & SIRIUS_AGG_MIN) && v < *(volatile long long*)&a->min) atomicMin(&a->min, (long long)v);
-  if ((aggs & SIRIUS_AGG_MAX) && v > *(volatile long long*)&a->max) atomicMax(&a->max, (long long)v);
+  if (aggs & SIRIUS_AGG_MIN) atomicMin(&a->min, (long long)v);
+  if (aggs & SIRIUS_AGG_MAX) atomicMax(&a->max, (long long)v);
 }
 
 __device__ __forceinline__ void agg_merge_global(Agg* a, unsigned long long sum, unsigned long long cnt,
                                                  long long mn, long long mx, uint32_t aggs) {
   if (aggs & SIRIUS_AGG_SUM) atomicAdd(&a->sum, sum);
   atomicAdd(&a->count, cnt);
-  if ((aggs & SIRIUS_AGG_MIN) && mn < *(volatile long long*)&a->min) atomicMin(&a->min, mn);
-  if ((aggs & SIRIUS_AGG_MAX) && mx > *(volatile long long*)&a->max) atomicMax(&a->max, mx);
+  if (aggs & SIRIUS_AGG_MIN) atomicMin(&a->min, mn);
+  if (aggs & SIRIUS_AGG_MAX) atomicMax(&a->max, mx);
 }
 
 __device__ __forceinline__ void agg_identity(Agg* a) {

@@ -56,6 +56,12 @@ class JoinTable(ctypes.Structure):
                 ("key_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class DimIndex(ctypes.Structure):
+    _fields_ = [("d_mem", ctypes.c_void_p), ("bytes", ctypes.c_size_t),
+                ("join_capacity", ctypes.c_int64), ("group_capacity", ctypes.c_int64),
+                ("key_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 # (name, restype, argtypes) of every exported function
 _VP, _I32, _I64, _U32, _U64, _SZ, _F64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t,
@@ -84,6 +90,23 @@ SIGNATURES = {
     "sirius_pipeline_scratch_bytes": (_SZ, [ctypes.POINTER(PipelineDesc)]),
     "sirius_run_pipeline": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(Result), _VP, _SZ,
                                    _VP]),
+    "sirius_dim_index_bytes": (_SZ, [ctypes.POINTER(PipelineDesc)]),
+    "sirius_dim_index_build": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(DimIndex), _VP,
+                                      _VP]),
+    "sirius_probe_scratch_bytes": (_SZ, [ctypes.POINTER(DimIndex)]),
+    "sirius_run_probe": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(DimIndex),
+                                ctypes.POINTER(Result), _VP, _SZ, _VP]),
+    "sirius_pipeline_host_scratch_bytes": (_SZ, [ctypes.POINTER(PipelineDesc), _I64, _I64]),
+    "sirius_run_pipeline_host": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(Result), _I64,
+                                        _VP, _SZ, _VP]),
+    "sirius_pipeline_batch_scratch_bytes": (_SZ, [ctypes.POINTER(PipelineDesc), _I32,
+                                                  ctypes.POINTER(DimIndex)]),
+    "sirius_batch_plan_create": (_I32, [_I32, ctypes.POINTER(ctypes.c_void_p)]),
+    "sirius_batch_plan_run": (_I32, [_VP, ctypes.POINTER(PipelineDesc), _I32, ctypes.POINTER(DimIndex),
+                                     ctypes.POINTER(Result), _I64, _I32, _VP, _SZ, _VP]),
+    "sirius_batch_plan_destroy": (None, [_VP]),
+    "sirius_run_pipeline_batch": (_I32, [ctypes.POINTER(PipelineDesc), _I32, ctypes.POINTER(DimIndex),
+                                         ctypes.POINTER(Result), _VP, _SZ, _VP]),
 }
 
 _LIB = None
@@ -140,7 +163,7 @@ def launch_count() -> int:
 
 
 PHASES = ["filter", "join_build", "join_probe", "gather", "groupby", "pipe_init", "pipe_build",
-          "pipe_probe", "pipe_finalize", "batch_plan", "batch_build", "batch_probe",
+          "pipe_probe", "pipe_finalize", "batch_graph", "batch_build", "batch_probe",
           "batch_finalize", "copy", "reserved14", "reserved15"]
 
 
@@ -291,17 +314,31 @@ def sirius_groupby_agg(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,m
 
 
 # ---------------------------------------------------------------------------- A7: pipeline
+def _host_ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("host columns must be contiguous CPU tensors (pinned for full speed)")
+    return t.data_ptr()
+
+
 def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="lt",
               literal: int = 50, aggs="sum,count,min,max", group_cap_hint: int = 0,
               load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
-              blocks_per_sm: int = 0) -> PipelineDesc:
-    g = lambda d, k: _ptr(d.get(k)) if d.get(k) is not None else None  # noqa: E731
-    return PipelineDesc(
+              blocks_per_sm: int = 0, host: bool = False) -> PipelineDesc:
+    """A pipeline descriptor over device columns (host=True: over host columns, for
+    sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?"""
+    P = _host_ptr if host else _ptr
+    g = lambda d, k: P(d.get(k)) if d.get(k) is not None else None  # noqa: E731
+    d = PipelineDesc(
         g(fact, "fk"), g(fact, "fk_hi"), g(fact, "pred"), g(fact, "val"), fact["pred"].numel(),
         g(dim, "pk"), g(dim, "pk_hi"), g(dim, "grp"), g(dim, "flag"), dim["pk"].numel(),
         OPS[op] if isinstance(op, str) else int(op), int(literal), _agg_mask(aggs),
         AGG_MODES[agg_mode] if isinstance(agg_mode, str) else int(agg_mode), int(group_cap_hint),
         float(load_factor), int(block_threads), int(blocks_per_sm), 0)
+    # the descriptor holds raw pointers: keep the tensors they point into alive with it
+    d._columns = (dict(fact), dict(dim))
+    return d
 
 
 def pipeline_scratch_bytes(desc: PipelineDesc) -> int:
@@ -350,3 +387,153 @@ def run_pipeline(fact, dim, op="lt", literal=50, aggs="sum,count,min,max", group
     outs = PipelineOutputs(out_cap, fact["pred"].device)
     g = sirius_run_pipeline(desc, outs)
     return outs.trimmed(g)
+
+
+# ---------------------------------------------------------------------------- resident build side
+class DimIndexBuffer:
+    """A built dim index (join table + group keys) in a torch-owned device buffer."""
+
+    def __init__(self, desc: PipelineDesc, device="cuda", stream=None):
+        nbytes = int(lib().sirius_dim_index_bytes(ctypes.byref(desc)))
+        self.mem = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        self.struct = DimIndex(self.mem.data_ptr(), self.mem.numel(), 0, 0, 0, 0)
+        st = ctypes.c_int32(0)
+        _check(lib().sirius_dim_index_build(ctypes.byref(desc), ctypes.byref(self.struct),
+                                            ctypes.byref(st), _stream(stream)))
+
+    @property
+    def nbytes(self) -> int:
+        return self.mem.numel()
+
+    def probe_scratch_bytes(self) -> int:
+        return int(lib().sirius_probe_scratch_bytes(ctypes.byref(self.struct)))
+
+
+def sirius_dim_index_build(desc: PipelineDesc, device="cuda", stream=None) -> DimIndexBuffer:
+    return DimIndexBuffer(desc, device, stream)
+
+
+def sirius_run_probe(desc: PipelineDesc, index: DimIndexBuffer, outputs: PipelineOutputs,
+                     scratch: Optional[torch.Tensor] = None, stream=None, sync: bool = True):
+    r = outputs.result(sync)
+    if scratch is None:
+        scratch = _scratch(index.probe_scratch_bytes(), outputs.d_groups.device)
+    st = lib().sirius_run_probe(ctypes.byref(desc), ctypes.byref(index.struct), ctypes.byref(r),
+                                _ptr(scratch), scratch.numel(), _stream(stream))
+    _check(st, r.groups)
+    return r.groups if sync else None
+
+
+# ---------------------------------------------------------------------------- host-resident columns
+class HostOutputs:
+    """Pinned host arrays receiving one pipeline result from sirius_run_pipeline_host."""
+
+    def __init__(self, out_cap: int):
+        self.cap = out_cap
+        self.t = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, pin_memory=True)
+                  for c in ("key", "sum", "count", "min", "max")}
+
+    def result(self) -> Result:
+        t = self.t
+        return Result(t["key"].data_ptr(), t["sum"].data_ptr(), t["count"].data_ptr(),
+                      t["min"].data_ptr(), t["max"].data_ptr(), self.cap, None, None, 1, 0, 0)
+
+    def trimmed(self, g: int) -> Dict[str, torch.Tensor]:
+        return {c: v[:g] for c, v in self.t.items()}
+
+
+def pipeline_host_scratch_bytes(desc: PipelineDesc, chunk_rows: int, out_cap: int) -> int:
+    return int(lib().sirius_pipeline_host_scratch_bytes(ctypes.byref(desc), chunk_rows, out_cap))
+
+
+def sirius_run_pipeline_host(desc: PipelineDesc, outputs: HostOutputs, chunk_rows: int = 0,
+                             scratch: Optional[torch.Tensor] = None, stream=None,
+                             device="cuda") -> int:
+    """One query over host columns (desc made with host=True); synchronises; returns G."""
+    r = outputs.result()
+    if scratch is None:
+        scratch = _scratch(pipeline_host_scratch_bytes(desc, chunk_rows, outputs.cap), device)
+    st = lib().sirius_run_pipeline_host(ctypes.byref(desc), ctypes.byref(r), chunk_rows,
+                                        _ptr(scratch), scratch.numel(), _stream(stream))
+    _check(st, r.groups)
+    return r.groups
+
+
+def _index_array(indexes, nq):
+    if indexes is None:
+        return None
+    arr = (DimIndex * nq)()
+    for i, ix in enumerate(indexes):
+        if ix is not None:
+            arr[i] = ix.struct
+    return arr
+
+
+def batch_scratch_bytes(descs, indexes=None) -> int:
+    nq = len(descs)
+    d = (PipelineDesc * nq)(*descs)
+    return int(lib().sirius_pipeline_batch_scratch_bytes(d, nq, _index_array(indexes, nq)))
+
+
+class BatchPlan:
+    """A reusable batch plan (sirius_batch_plan_*): task table, staging and CUDA graph."""
+
+    def __init__(self, max_queries: int):
+        h = ctypes.c_void_p()
+        _check(lib().sirius_batch_plan_create(int(max_queries), ctypes.byref(h)))
+        self.handle = h
+        self.max_queries = max_queries
+
+    def close(self):
+        if self.handle:
+            lib().sirius_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, descs, outputs, indexes=None, rows_per_unit: int = 0, use_graph: bool = False,
+            scratch: Optional[torch.Tensor] = None, stream=None, sync: bool = True):
+        """Runs len(descs) pipelines; outputs[i] is a PipelineOutputs.  sync=True returns the
+        list of G (raises with the first failing status); sync=False returns None."""
+        nq = len(descs)
+        d = (PipelineDesc * nq)(*descs)
+        res = (Result * nq)(*[o.result(sync) for o in outputs])
+        idx = _index_array(indexes, nq)
+        if scratch is None:
+            scratch = _scratch(int(lib().sirius_pipeline_batch_scratch_bytes(d, nq, idx)),
+                               outputs[0].d_groups.device)
+        st = lib().sirius_batch_plan_run(self.handle, d, nq, idx, res, int(rows_per_unit),
+                                         1 if use_graph else 0, _ptr(scratch), scratch.numel(),
+                                         _stream(stream))
+        self.last_status = [res[i].status for i in range(nq)]
+        _check(st)
+        return [res[i].groups for i in range(nq)] if sync else None
+
+
+def sirius_run_pipeline_batch(descs, outputs, indexes=None, scratch=None, stream=None):
+    """One-off batch (plan created and destroyed inside the call); returns the list of G."""
+    nq = len(descs)
+    d = (PipelineDesc * nq)(*descs)
+    res = (Result * nq)(*[o.result(True) for o in outputs])
+    idx = _index_array(indexes, nq)
+    if scratch is None:
+        scratch = _scratch(int(lib().sirius_pipeline_batch_scratch_bytes(d, nq, idx)),
+                           outputs[0].d_groups.device)
+    st = lib().sirius_run_pipeline_batch(d, nq, idx, res, _ptr(scratch), scratch.numel(),
+                                         _stream(stream))
+    _check(st)
+    return [res[i].groups for i in range(nq)]
+
+
+def pinned_copy(cols: Dict[str, torch.Tensor]) -> Dict[str, torch.Tensor]:
+    """Pinned host copies of device columns (one allocation per column)."""
+    out = {}
+    for k, v in cols.items():
+        h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+        h.copy_(v)
+        out[k] = h
+    return out

@@ -149,6 +149,55 @@ def test_output_capacity(S):
     assert e.value.status == S.ERR_CAPACITY and e.value.needed == 200
 
 
+def test_resident_dim_index_serves_many_probes(S):
+    spec = dg.StarSpec("t", n=300_001, m=20_000, fk_domain=22_000, grp_bound=500, seed=9)
+    dim = dg.gen_dim_host(spec)
+    ddim = dev(dim)
+    desc0 = S.make_desc(dev(dg.gen_fact_host(spec)), ddim, "lt", 50, group_cap_hint=500)
+    index = S.sirius_dim_index_build(desc0)
+    for seed, op, t in ((9, "lt", 50), (10, "ge", 20), (11, "ne", 3)):
+        fs = dg.StarSpec("t", n=200_000 + seed, m=20_000, fk_domain=22_000, grp_bound=500, seed=seed)
+        fact = dg.gen_fact_host(fs)
+        dfact = dev(fact)
+        desc = S.make_desc(dfact, ddim, op, t, group_cap_hint=500)
+        outs = S.PipelineOutputs(600)
+        g = S.sirius_run_probe(desc, index, outs)
+        got = O.sort_groups({k: v.cpu().numpy() for k, v in outs.trimmed(g).items()})
+        want = O.pipeline(fact, dim, op, t)
+        for c in COLS:
+            assert np.array_equal(got[c], want[c]), (seed, c)
+
+
+@pytest.mark.parametrize("chunk", [0, 4096, 10_000, 77_777])
+def test_host_columns_streamed_in_chunks(S, chunk):
+    spec = dg.StarSpec("t", n=250_003, m=9000, fk_domain=9500, grp_bound=300, t=45, seed=12)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    hf = {k: torch.from_numpy(v).pin_memory() for k, v in fact.items()}
+    hd = {k: torch.from_numpy(v).pin_memory() for k, v in dim.items()}
+    desc = S.make_desc(hf, hd, "lt", spec.t, group_cap_hint=300, host=True)
+    outs = S.HostOutputs(400)
+    g = S.sirius_run_pipeline_host(desc, outs, chunk)
+    got = O.sort_groups({k: v.numpy() for k, v in outs.trimmed(g).items()})
+    want = O.pipeline(fact, dim, "lt", spec.t)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
+
+
+def test_host_columns_composite_and_flag(S):
+    spec = dg.StarSpec("t", n=120_001, m=5000, fk_domain=5000, t=60, composite=True, group_flag=True,
+                       seed=13)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    hf = {k: torch.from_numpy(v) for k, v in fact.items()}       # pageable host memory works too
+    hd = {k: torch.from_numpy(v) for k, v in dim.items()}
+    desc = S.make_desc(hf, hd, "lt", spec.t, group_cap_hint=5000, host=True)
+    outs = S.HostOutputs(5001)
+    g = S.sirius_run_pipeline_host(desc, outs, 30_000)
+    got = O.sort_groups({k: v.numpy() for k, v in outs.trimmed(g).items()})
+    want = O.pipeline(fact, dim, "lt", spec.t)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
+
+
 def test_repeatable_across_block_shapes(S):
     spec = dg.plain_scale(n=500_000, m=20_000)
     dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
