@@ -194,7 +194,9 @@ typedef struct {
   float load_factor;        /* join table load factor; 0 -> default 0.5 */
   int32_t block_threads;    /* probe kernel block size; 0 -> default */
   int32_t blocks_per_sm;    /* probe kernel residency target; 0 -> occupancy maximum */
-  int32_t reserved;
+  int32_t probe_variant;    /* 0 auto; 1 direct (each thread loads its rows and buckets);
+                               2 staged (TMA column tiles + cp.async bucket gathers, global
+                               aggregation, 16-byte aligned columns) */
 } sirius_pipeline_desc;
 
 typedef struct {

@@ -20,6 +20,7 @@
 // table in host memory can be streamed through the probe pass chunk by chunk while the next
 // chunk is copied (batch execution over data larger than device memory, Sec. 3.4).
 #include "pipeline.cuh"
+#include "probe_staged.cuh"
 
 namespace sirius {
 
@@ -110,6 +111,7 @@ __global__ void finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __
       __threadfence();
       const unsigned long long g = *(volatile unsigned long long*)&phdr->groups;
       int32_t st = *(volatile const int32_t*)&dhdr->status;
+      if (st == 0) st = *(volatile const int32_t*)&phdr->status;  // probe-pass errors (TIMEOUT)
       if (st == 0 && (int64_t)g > out.cap) st = SIRIUS_ERR_CAPACITY;
       phdr->status = st;
       if (out.d_groups) *out.d_groups = (int64_t)g;
@@ -155,6 +157,24 @@ sirius_status launch_probe(const ProbeArgs& a, int threads, int blocks_per_sm, s
   int64_t g = (int64_t)sm_count() * per_sm;
   if (g > want) g = want;
   k<<<(unsigned)g, threads, smem, s>>>(a);
+  SIRIUS_LAUNCH_CHECK();
+  return SIRIUS_OK;
+}
+
+template <bool kWide>
+sirius_status launch_staged(const ProbeArgs& a, PipeHeader* phdr, cudaStream_t s) {
+  auto k = staged::probe_staged_kernel<kWide>;
+  const size_t smem = staged::smem_bytes(kWide);
+  static bool attr = false;
+  if (!attr) {
+    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const int64_t tiles = (((a.n >> 2) << 2) + staged::kTile - 1) / staged::kTile;
+  int64_t g = sm_count();
+  if (g > tiles) g = tiles;
+  if (g < 1) g = 1;
+  k<<<(unsigned)g, staged::kThreads, smem, s>>>(a, &phdr->status);
   SIRIUS_LAUNCH_CHECK();
   return SIRIUS_OK;
 }
@@ -231,6 +251,8 @@ sirius_status validate_fact(const sirius_pipeline_desc* q) {
                                            q->block_threads <= 512),
                  "pipeline: block_threads must be a multiple of 32 in [64, 512]");
   SIRIUS_REQUIRE(q->blocks_per_sm >= 0 && q->blocks_per_sm <= 32, "pipeline: blocks_per_sm out of range");
+  SIRIUS_REQUIRE(q->probe_variant >= 0 && q->probe_variant <= 2, "pipeline: bad probe_variant %d",
+                 q->probe_variant);
   return SIRIUS_OK;
 }
 
@@ -303,6 +325,11 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   const int mode = choose_mode(q->agg_mode, gslots);
   const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
                    (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+  const bool staged_ok = mode == kAggGlobal && vec && ((uintptr_t)q->val & 15) == 0;
+  if (staged_ok && (q->probe_variant == 2 || (q->probe_variant == 0 && q->n >= (1 << 20)))) {
+    PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
+    return d.key_width == 8 ? launch_staged<true>(a, r.phdr, s) : launch_staged<false>(a, r.phdr, s);
+  }
   const int threads = q->block_threads > 0 ? q->block_threads : (mode == kAggSmem ? 512 : 256);
   const size_t smem = mode == kAggSmem ? (size_t)gslots * sizeof(Agg) : 0;
   PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);

@@ -24,6 +24,7 @@ LT, LE, GT, GE, EQ, NE = range(6)
 OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
 AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
 AGG_MODES = {"auto": 0, "smem": 1, "global": 2}
+PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2}
 
 
 class SiriusError(RuntimeError):
@@ -41,7 +42,7 @@ class PipelineDesc(ctypes.Structure):
                 ("op", ctypes.c_int32), ("literal", ctypes.c_int32), ("aggs", ctypes.c_uint32),
                 ("agg_mode", ctypes.c_int32), ("group_cap_hint", ctypes.c_int64),
                 ("load_factor", ctypes.c_float), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("probe_variant", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -325,7 +326,7 @@ def _host_ptr(t: Optional[torch.Tensor]) -> Optional[int]:
 def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="lt",
               literal: int = 50, aggs="sum,count,min,max", group_cap_hint: int = 0,
               load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
-              blocks_per_sm: int = 0, host: bool = False) -> PipelineDesc:
+              blocks_per_sm: int = 0, host: bool = False, probe_variant="auto") -> PipelineDesc:
     """A pipeline descriptor over device columns (host=True: over host columns, for
     sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?"""
     P = _host_ptr if host else _ptr
@@ -335,7 +336,8 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
         g(dim, "pk"), g(dim, "pk_hi"), g(dim, "grp"), g(dim, "flag"), dim["pk"].numel(),
         OPS[op] if isinstance(op, str) else int(op), int(literal), _agg_mask(aggs),
         AGG_MODES[agg_mode] if isinstance(agg_mode, str) else int(agg_mode), int(group_cap_hint),
-        float(load_factor), int(block_threads), int(blocks_per_sm), 0)
+        float(load_factor), int(block_threads), int(blocks_per_sm),
+        PROBE_VARIANTS[probe_variant] if isinstance(probe_variant, str) else int(probe_variant))
     # the descriptor holds raw pointers: keep the tensors they point into alive with it
     d._columns = (dict(fact), dict(dim))
     return d

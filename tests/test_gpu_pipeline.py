@@ -149,6 +149,30 @@ def test_output_capacity(S):
     assert e.value.status == S.ERR_CAPACITY and e.value.needed == 200
 
 
+@pytest.mark.parametrize("variant", ["direct", "staged"])
+@pytest.mark.parametrize("n", [1, 3, 4, 511, 512, 513, 4099, 1_000_003])
+def test_probe_variants(S, variant, n):
+    spec = dg.StarSpec("t", n=n, m=7001, fk_domain=7500, grp_bound=900, t=41, seed=n + 17)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=900, agg_mode="global", probe_variant=variant)
+
+
+@pytest.mark.parametrize("lf", [0.5, 0.95])
+def test_staged_probe_duplicates_composite_overflow(S, lf):
+    """Full home buckets (load factor 0.95) force walks past the gathered bucket."""
+    rng = np.random.default_rng(21)
+    m = 20_000
+    dim = {"pk": rng.integers(0, 9000, size=m).astype(np.int32),
+           "grp": rng.integers(0, 3000, size=m).astype(np.int32)}
+    fact = {"fk": rng.integers(-50, 9100, size=600_001).astype(np.int32),
+            "pred": rng.integers(0, 100, size=600_001).astype(np.int32),
+            "val": rng.integers(-10**9, 10**9, size=600_001)}
+    check(S, fact, dim, "lt", 60, hint=3000, load_factor=lf, agg_mode="global", probe_variant="staged")
+    spec = dg.plain_scale(n=700_001, m=30_000, composite=True)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=100_000, load_factor=lf, probe_variant="staged")
+
+
 def test_resident_dim_index_serves_many_probes(S):
     spec = dg.StarSpec("t", n=300_001, m=20_000, fk_domain=22_000, grp_bound=500, seed=9)
     dim = dg.gen_dim_host(spec)
