@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--agg-mode", default="auto")
     p.add_argument("--block-threads", type=int, default=0)
     p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--probe-variant", default="auto", choices=["auto", "direct", "staged"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -225,7 +226,7 @@ def main():
     fact = dg.gen_fact_device(spec, dim, dev)
     aggs = spec.aggs
     desc = S.make_desc(fact, dim, "lt", spec.t, aggs, hint, args.load_factor, args.agg_mode,
-                       args.block_threads, args.blocks_per_sm)
+                       args.block_threads, args.blocks_per_sm, probe_variant=args.probe_variant)
     out_cap = hint + 1
     outs = S.PipelineOutputs(out_cap, dev)
     scratch = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
@@ -321,7 +322,8 @@ def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
     hf = S.pinned_copy(fact)
     hd = S.pinned_copy(dim)
     desc = S.make_desc(hf, hd, "lt", spec.t, aggs, hint, args.load_factor, args.agg_mode,
-                       args.block_threads, args.blocks_per_sm, host=True)
+                       args.block_threads, args.blocks_per_sm, host=True,
+                       probe_variant=args.probe_variant)
     outs = S.HostOutputs(hint + 1)
     scratch = torch.empty(S.pipeline_host_scratch_bytes(desc, 0, outs.cap), dtype=torch.uint8, device=dev)
     g = S.sirius_run_pipeline_host(desc, outs, 0, scratch, stream, dev)   # warm-up
