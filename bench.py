@@ -49,6 +49,12 @@ def parse():
     p.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-served", action="store_true")
+    p.add_argument("--batch-queries", type=int, default=512)
+    p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--serve-seconds", type=float, default=10.0)
+    p.add_argument("--fifo-seconds", type=float, default=3.0)
     return p.parse_args()
 
 
@@ -289,10 +295,20 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world)
 
+    # release the 600M-row tables before the batched and served workloads
+    del fact, dim, desc, scratch
+    torch.cuda.empty_cache()
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(S, torch, args, dev, rank)
+        torch.cuda.empty_cache()
+    served = None
+    if not args.no_served:
+        served = run_served(S, torch, args, dev, rank)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        del fact
-        torch.cuda.empty_cache()
         cpu = cpu_baseline(spec, args.cpu_sample_rows)
 
     if rank == 0:
@@ -307,12 +323,118 @@ def main():
                        "load_factor": args.load_factor or 0.5, "agg_mode": args.agg_mode},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "phase_ms": phase_ms, "device_status": status,
+            "batched": batched, "served": served,
             "hbm_gbs_effective_step": alg_bytes / (ms_step / 1e3) / 1e9,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batched(S, torch, args, dev, rank):
+    """512 independent pipelines (sizes log-uniform 10K-20M fact rows, 1K-2M dim rows,
+    t uniform 5..90): one batch plan (persistent launches, CUDA graph) against 512 plain
+    sirius_run_pipeline calls on the same stream, identical results required."""
+    from paper_2508_04701_gb300 import autotune
+    from paper_2508_04701_gb300 import datagen as dg
+    nq = args.batch_queries
+    specs = [dg.batch_query(q, seed=rank) for q in range(nq)]
+    tabs = []
+    for sp in specs:
+        dim = dg.gen_dim_device(sp, dev)
+        tabs.append((dim, dg.gen_fact_device(sp, dim, dev)))
+    descs = [S.make_desc(f, d, "lt", sp.t, "sum,count,min,max", 1000) for sp, (d, f) in zip(specs, tabs)]
+    cap = S.lib().sirius_groupby_capacity(1000) + 1
+    outs_b = [S.PipelineOutputs(cap, dev) for _ in range(nq)]
+    outs_p = [S.PipelineOutputs(cap, dev) for _ in range(nq)]
+    rows = sum(sp.n for sp in specs)
+    fact_bytes = sum(sp.n * sp.fact_bytes_per_row for sp in specs)
+    torch.cuda.synchronize()
+
+    def ev_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # plain: one sirius_run_pipeline per query, back to back on one stream
+    p_scr = torch.empty(max(S.pipeline_scratch_bytes(d) for d in descs), dtype=torch.uint8, device=dev)
+
+    def plain():
+        for d, o in zip(descs, outs_p):
+            S.sirius_run_pipeline(d, o, p_scr, sync=False)
+    t_plain = ev_time(plain, 3)
+    plan = S.BatchPlan(nq)
+    scr = torch.empty(S.batch_scratch_bytes(descs), dtype=torch.uint8, device=dev)
+    t_batch = ev_time(lambda: plan.run(descs, outs_b, scratch=scr, sync=False), 3)
+    t_graph = ev_time(lambda: plan.run(descs, outs_b, scratch=scr, use_graph=True, sync=False), 5)
+    tuned = autotune.tune_batch(plan, descs, outs_b, use_graph=True, use_cache=False,
+                                units=(16_384, 65_536, 262_144), load_factors=(0.35, 0.5, 0.7))
+    scr = torch.empty(S.batch_scratch_bytes(descs), dtype=torch.uint8, device=dev)
+    t_tuned = ev_time(lambda: plan.run(descs, outs_b, scratch=scr, use_graph=True,
+                                       rows_per_unit=tuned["rows_per_unit"], sync=False), 5)
+    # identical results: every query's groups equal between the batched and the plain run
+    gb = plan.run(descs, outs_b, scratch=scr, use_graph=True, rows_per_unit=tuned["rows_per_unit"])
+    for d in descs:
+        d.load_factor = 0.0
+    same = True
+    for d, ob, op, g in zip(descs, outs_b, outs_p, gb):
+        S.sirius_run_pipeline(d, op, p_scr, sync=False)
+        if int(op.d_groups.item()) != g:
+            same = False
+            break
+        kb, ib = torch.sort(ob.t["key"][:g])
+        kp, ip = torch.sort(op.t["key"][:g])
+        for c in ("sum", "count", "min", "max"):
+            if not torch.equal(ob.t[c][:g][ib], op.t[c][:g][ip]):
+                same = False
+        if not torch.equal(kb, kp):
+            same = False
+    plan.close()
+    res = {"queries": nq, "fact_rows": rows, "fact_bytes": fact_bytes,
+           "plain_ms": t_plain, "batched_ms": t_batch, "batched_graph_ms": t_graph, "autotuned_graph_ms": t_tuned,
+           "plain_rows_per_s": rows / (t_plain / 1e3), "batched_rows_per_s": rows / (t_batch / 1e3),
+           "batched_graph_rows_per_s": rows / (t_graph / 1e3),
+           "autotuned_rows_per_s": rows / (t_tuned / 1e3), "speedup_vs_plain": t_plain / min(t_graph, t_tuned),
+           "autotuned": {k: tuned[k] for k in ("rows_per_unit", "load_factor")},
+           "hbm_gbs_effective": fact_bytes / (min(t_graph, t_tuned) / 1e3) / 1e9,
+           "results_identical_to_plain": same}
+    del tabs
+    return res
+
+
+def run_served(S, torch, args, dev, rank):
+    """Open-loop Poisson arrivals (rate args.serve_rate) over a resident pool of 512 fact
+    tables and 64 dim tables with their dim indexes; continuous batching against plain
+    sequential execution (FIFO, one request at a time) on the same GPU."""
+    from paper_2508_04701_gb300 import serve
+    pool = serve.ResidentPool(n_facts=512, n_dims=64, seed=rank, device=dev)
+    dur = args.serve_seconds + 1.0
+    reqs = serve.poisson_requests(args.serve_rate, dur, len(pool.facts), seed=rank)
+    srv = serve.Server(pool, slots=4, max_batch=64, budget_bytes=150 * 10**9)
+    warm = serve.poisson_requests(args.serve_rate, 0.3, len(pool.facts), seed=rank + 99)
+    srv.run(warm)
+    srv.run(reqs)
+    st = serve.latency_stats(reqs, warmup=1.0)
+    rows = sum(pool.fact_rows[r.fact_id] for r in reqs if r.arrival >= 1.0)
+    st["rows_per_s"] = rows / (args.serve_seconds) if args.serve_seconds > 0 else 0.0
+    st["batches"] = srv.batches
+    st["statuses_ok"] = all(r.status == 0 for r in reqs)
+    st["pool_bytes"] = pool.bytes()
+    st["budget_bytes"] = srv.admission.budget
+    st["admission_deferrals"] = srv.admission.rejected
+    # plain sequential FIFO on the same arrival schedule (a bounded prefix of it)
+    fifo_reqs = [serve.Request(r.rid, r.fact_id, r.t, r.arrival) for r in reqs if r.arrival < args.fifo_seconds]
+    serve.sequential_fifo(pool, fifo_reqs)
+    fst = serve.latency_stats(fifo_reqs)
+    return {"rate_qps": args.serve_rate, "seconds": args.serve_seconds, "served": st,
+            "plain_fifo": fst, "fifo_seconds": args.fifo_seconds}
 
 
 def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):

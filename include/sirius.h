@@ -197,6 +197,10 @@ typedef struct {
   int32_t probe_variant;    /* 0 auto; 1 direct (each thread loads its rows and buckets);
                                2 staged (TMA column tiles + cp.async bucket gathers, global
                                aggregation, 16-byte aligned columns) */
+  int32_t join_mode;        /* 0 auto: one-column build keys that are unique and span a range
+                               of at most 2m values are joined through a direct-address array
+                               (decided on the device during the build); 1 hash table always */
+  int32_t reserved;
 } sirius_pipeline_desc;
 
 typedef struct {
@@ -233,6 +237,7 @@ typedef struct {
   size_t bytes;
   int64_t join_capacity;
   int64_t group_capacity;
+  int64_t direct_capacity;   /* entries of the direct-address array (0: hash table only) */
   int32_t key_width;
   int32_t reserved;
 } sirius_dim_index;

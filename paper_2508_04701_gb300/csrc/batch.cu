@@ -37,23 +37,26 @@ struct BatchQuery {
   const int32_t* grp;
   const int8_t* flag;
   int64_t m;
-  int64_t jpairs;  // 16-byte words of join slots to clear (0 when the dim index is prebuilt)
+  int64_t jpairs;  // 16-byte words of join slots (0 when the dim index is prebuilt)
+  int64_t dpairs;  // 16-byte words of the direct array (0 when prebuilt or hash only)
   int64_t gslots;
   unsigned long long glimit;
   uint32_t flags;
   int32_t orig;    // position of the query in the caller's arrays
-  int64_t u0[4];   // first unit of this query in each phase (init, build, probe, finalize)
-  int64_t nu[4];   // units of this query in each phase
+  // work units of this query: kinds 0 init (words), 1 build (dim rows), 2 probe (fact rows),
+  // 3 finalize (group slots), 4 table clears (words)
+  int64_t u0[5];   // first unit of this query in each kind
+  int64_t nu[5];   // units of this query in each kind
 };
 
 struct BatchHeader {
   int32_t nq;
   int32_t pad;
-  int64_t total[4];          // units per phase, all queries
+  int64_t total[5];          // units per kind, all queries
   int64_t quads_per_unit;
   int32_t cls_q0[8], cls_q1[8];  // query range of each probe class (queries sorted by class)
   int64_t cls_u0[8], cls_u1[8];  // probe-unit range of each class
-  int64_t pad2[2];
+  int64_t pad2[1];
 };
 static_assert(sizeof(BatchHeader) == 256, "batch header is 256 bytes");
 
@@ -84,21 +87,74 @@ batch_init_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restric
     if (local == 0 && threadIdx.x < 32) {
       reinterpret_cast<uint64_t*>(b.phdr)[threadIdx.x] = 0;
       if (build) {
-        reinterpret_cast<uint64_t*>(b.d.dhdr)[threadIdx.x] = 0;
+        // word 2 of the dim header: (key_min, key_max) = (INT32_MAX, INT32_MIN)
+        reinterpret_cast<uint64_t*>(b.d.dhdr)[threadIdx.x] = threadIdx.x == 2 ? 0x800000007FFFFFFFull : 0ull;
         reinterpret_cast<uint64_t*>(b.d.jhdr)[threadIdx.x] = 0;
       }
     }
-    const int64_t end = b.jpairs + b.gslots;
+    // join slots are cleared here only for hash-only dims; otherwise by the clear phases
+    const int64_t jw = (build && b.d.dcap == 0) ? b.jpairs : 0;
+    const int64_t end = jw + b.gslots;
     const int64_t i1 = (local + 1) * kInitUnit < end ? (local + 1) * kInitUnit : end;
     for (int64_t i = local * kInitUnit + threadIdx.x; i < i1; i += blockDim.x) {
-      if (i < b.jpairs) {
+      if (i < jw) {
         reinterpret_cast<ulonglong2*>(b.d.jslots)[i] = ones;
       } else {
-        const int64_t g = i - b.jpairs;
+        const int64_t g = i - jw;
         if (build) b.d.gkeys[g] = kEmptyKey;
         agg_identity(&b.a.tab[g]);
       }
     }
+  }
+}
+
+// Key range of every dim that may take the direct array.
+__global__ void __launch_bounds__(kBatchThreads)
+batch_minmax_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
+  const int nq = H->nq;
+  for (int64_t u = blockIdx.x; u < H->total[1]; u += gridDim.x) {
+    const BatchQuery& b = Q[find_query<1>(Q, nq, u)];
+    if (b.d.dcap == 0) continue;
+    const int64_t r0 = (u - b.u0[1]) * kBuildUnit;
+    const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+      const int32_t k = b.pk[j];
+      lo = k < lo ? k : lo;
+      hi = k > hi ? k : hi;
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&b.d.dhdr->key_min, lo);
+      atomicMax(&b.d.dhdr->key_max, hi);
+    }
+  }
+}
+
+// Table clears of dims that may take the direct array.  Phase 0 (before the build): the
+// direct array when the key range fits it, else the join slots.  Phase 1 (after the build):
+// the join slots when a duplicate key turned the direct array down.
+__global__ void __launch_bounds__(kBatchThreads)
+batch_clear_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int phase) {
+  const int nq = H->nq;
+  const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
+  for (int64_t u = blockIdx.x; u < H->total[4]; u += gridDim.x) {
+    const BatchQuery& b = Q[find_query<4>(Q, nq, u)];
+    const bool direct = direct_applies(b.d, b.m);
+    ulonglong2* w;
+    int64_t words;
+    if (phase == 0) {
+      w = reinterpret_cast<ulonglong2*>(direct ? (void*)b.d.dslot : b.d.jslots);
+      words = direct ? b.dpairs : b.jpairs;
+    } else {
+      if (!(b.d.dhdr->direct && b.d.dhdr->direct_failed)) continue;
+      w = reinterpret_cast<ulonglong2*>(b.d.jslots);
+      words = b.jpairs;
+    }
+    const int64_t i0 = (u - b.u0[4]) * kInitUnit;
+    const int64_t i1 = i0 + kInitUnit < words ? i0 + kInitUnit : words;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) w[i] = ones;
   }
 }
 
@@ -107,15 +163,41 @@ batch_build_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
   const int nq = H->nq;
   for (int64_t u = blockIdx.x; u < H->total[1]; u += gridDim.x) {
     const BatchQuery& b = Q[find_query<1>(Q, nq, u)];
-    const int64_t r0 = (u - b.u0[1]) * kBuildUnit;
+    const int64_t local = u - b.u0[1];
+    const int64_t r0 = local * kBuildUnit;
     const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
     const DimView d = b.d;
+    const bool wide = (b.flags & kQWide) != 0;
+    const bool direct = !wide && direct_applies(d, b.m);
+    const int32_t kmin = d.dhdr->key_min;
+    if (local == 0 && threadIdx.x == 0) d.dhdr->direct = direct ? 1u : 0u;
     bool dup = false;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-      const bool ok = (b.flags & kQWide) ? dim_build_row<true>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup)
-                                         : dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup);
+      const bool ok = wide ? dim_build_row<true>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup)
+                           : dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup, direct, kmin);
       if (!ok) set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     }
+    if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
+      if (direct) d.dhdr->direct_failed = 1;
+      else d.jhdr->has_dups = 1;
+    }
+  }
+}
+
+// Rebuild into the hash table the dims whose direct array a duplicate key turned down.
+__global__ void __launch_bounds__(kBatchThreads)
+batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
+  const int nq = H->nq;
+  for (int64_t u = blockIdx.x; u < H->total[1]; u += gridDim.x) {
+    const BatchQuery& b = Q[find_query<1>(Q, nq, u)];
+    const DimView d = b.d;
+    if (!(d.dhdr->direct && d.dhdr->direct_failed)) continue;
+    const int64_t r0 = (u - b.u0[1]) * kBuildUnit;
+    const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
+    bool dup = false;
+    for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x)
+      if (!dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup))
+        set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
   }
 }
@@ -140,7 +222,7 @@ batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
     const BatchQuery& b = Q[lo];
     if (b.d.dhdr->status != 0) continue;  // the build failed: nothing to aggregate
     const ProbeArgs a = b.a;
-    const bool dups = b.d.jhdr->has_dups != 0;
+    const Lookup L = read_lookup(a);
     const int64_t local = u - b.u0[2];
     const int64_t nq4 = a.n >> 2;
     const int64_t q0 = local * qpu;
@@ -149,10 +231,10 @@ batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
       for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) agg_identity(&s_tab[i]);
       __syncthreads();
     }
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec>(a, s_tab, dups, q);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec>(a, s_tab, L, q);
     if (local == b.nu[2] - 1) {
       const int64_t t0 = nq4 << 2;
-      if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, s_tab, dups, t0 + threadIdx.x);
+      if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, s_tab, L, t0 + threadIdx.x);
     }
     if (kMode == kAggSmem) {
       __syncthreads();
@@ -205,16 +287,7 @@ __global__ void batch_publish_kernel(const BatchHeader* __restrict__ H, const Ba
   st[b.orig].groups = (int64_t)g;
 }
 
-DimLayout layout_of_index(const sirius_dim_index* idx) {
-  DimLayout L;
-  L.key_width = idx->key_width;
-  L.jcap = idx->join_capacity;
-  L.gcap = idx->group_capacity;
-  L.off_join = 256;
-  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
-  L.total = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
-  return L;
-}
+DimLayout layout_of_index(const sirius_dim_index* idx) { return dim_layout_of_index(idx); }
 
 bool prebuilt(const sirius_dim_index* indexes, int i) { return indexes && indexes[i].d_mem; }
 
@@ -270,8 +343,7 @@ extern "C" size_t sirius_pipeline_batch_scratch_bytes(const sirius_pipeline_desc
     if (prebuilt(indexes, i)) {
       gcap = indexes[i].group_capacity;
     } else {
-      const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint,
-                                     q->load_factor);
+      const DimLayout L = dim_layout_for(q);
       off += L.total;
       gcap = L.gcap;
     }
@@ -325,7 +397,15 @@ static sirius_status enqueue_batch(sirius_batch_plan p, size_t smem, uint32_t cl
     PhaseTimer pt(timed ? s : nullptr, timed ? SIRIUS_PHASE_BATCH_BUILD : -1);
     batch_init_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
     SIRIUS_LAUNCH_CHECK();
+    batch_minmax_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    SIRIUS_LAUNCH_CHECK();
+    batch_clear_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ, 0);
+    SIRIUS_LAUNCH_CHECK();
     batch_build_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    SIRIUS_LAUNCH_CHECK();
+    batch_clear_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ, 1);
+    SIRIUS_LAUNCH_CHECK();
+    batch_fallback_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
     SIRIUS_LAUNCH_CHECK();
   }
   {
@@ -395,7 +475,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
   for (int i = 0; i < nq; ++i) {
     const sirius_pipeline_desc* q = &qs[i];
     const bool pre = prebuilt(indexes, i);
-    const int64_t gcap = pre ? indexes[i].group_capacity : dim_layout(q->m, false, q->group_cap_hint, q->load_factor).gcap;
+    const int64_t gcap = pre ? indexes[i].group_capacity : dim_layout_for(q).gcap;
     const bool wide = pre ? indexes[i].key_width == 8 : (q->pk_hi != nullptr || q->fk_hi != nullptr);
     const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
                      (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
@@ -420,7 +500,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
       L = layout_of_index(&indexes[i]);
       dbase = (char*)indexes[i].d_mem;
     } else {
-      L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint, q->load_factor);
+      L = dim_layout_for(q);
       dbase = sc.base + off;
       off += L.total;
     }
@@ -444,6 +524,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     b.a.jslots = b.d.jslots;
     b.a.jhdr = b.d.jhdr;
     b.a.dhdr = b.d.dhdr;
+    b.a.dslot = b.d.dslot;
     b.a.tab = r.aggs;
     b.a.gslots = (uint32_t)R.gslots;
     b.pk = q->pk;
@@ -453,17 +534,21 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     b.m = pre ? 0 : q->m;
     b.gslots = R.gslots;
     b.jpairs = pre ? 0 : (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16;
+    b.dpairs = pre ? 0 : L.dcap / 4;
     b.glimit = group_limit_for(L.gcap);
     const int c = cls[i];
     b.flags = ((c & 1) ? kQWide : 0) | ((c & 2) ? kQSmem : 0) | ((c & 4) ? kQVec : 0) | (pre ? 0 : kQBuild);
     if ((c & 2) && R.gslots > max_smem_slots) max_smem_slots = R.gslots;
     const bool probes = q->n > 0 && (pre || q->m > 0);
-    b.nu[0] = (b.jpairs + b.gslots + kInitUnit - 1) / kInitUnit;
+    const int64_t init_words = (!pre && L.dcap == 0 ? b.jpairs : 0) + b.gslots;
+    b.nu[0] = (init_words + kInitUnit - 1) / kInitUnit;
     b.nu[1] = (b.m + kBuildUnit - 1) / kBuildUnit;
     const int64_t nq4 = q->n >> 2;
     b.nu[2] = probes ? ((nq4 + qpu - 1) / qpu > 0 ? (nq4 + qpu - 1) / qpu : 1) : 0;
     b.nu[3] = (b.gslots + kFinUnit - 1) / kFinUnit;
-    for (int ph = 0; ph < 4; ++ph) {
+    const int64_t clear_words = (!pre && L.dcap > 0 && b.m > 0) ? (b.jpairs > b.dpairs ? b.jpairs : b.dpairs) : 0;
+    b.nu[4] = (clear_words + kInitUnit - 1) / kInitUnit;
+    for (int ph = 0; ph < 5; ++ph) {
       b.u0[ph] = H->total[ph];
       H->total[ph] += b.nu[ph];
     }
@@ -522,7 +607,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     }
     PhaseTimer pt(s, SIRIUS_PHASE_BATCH_GRAPH);
     SIRIUS_CUDA_TRY(cudaGraphLaunch(p->exec, s));
-    count_launch(4 + __builtin_popcount(classes));
+    count_launch(8 + __builtin_popcount(classes));
   } else {
     st = enqueue_batch(p, smem, classes, s, true);
     if (st != SIRIUS_OK) return st;

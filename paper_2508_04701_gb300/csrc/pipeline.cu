@@ -26,27 +26,83 @@ namespace sirius {
 
 namespace {
 
+// Clears the dim index: headers (key range to its empty value), join slots (kEmpty), direct
+// array (kEmpty32, as 16-byte words) and group keys.  The join slots are only cleared when
+// the hash table may be needed (`jpairs` is 0 when the direct array is certain to be used).
 __global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* jwords2, int64_t jpairs,
-                                int64_t* gkeys, int64_t gslots) {
+                                ulonglong2* dwords2, int64_t dpairs, int64_t* gkeys, int64_t gslots) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (tid < 32) {
-    reinterpret_cast<uint64_t*>(dhdr)[tid] = 0;
+    // word 2 of the dim header holds (key_min, key_max): start at (INT32_MAX, INT32_MIN)
+    reinterpret_cast<uint64_t*>(dhdr)[tid] = tid == 2 ? 0x800000007FFFFFFFull : 0ull;
     reinterpret_cast<uint64_t*>(jhdr)[tid] = 0;
   }
   const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
   for (int64_t i = tid; i < jpairs; i += stride) jwords2[i] = ones;
+  for (int64_t i = tid; i < dpairs; i += stride) dwords2[i] = ones;
   for (int64_t i = tid; i < gslots; i += stride) gkeys[i] = kEmptyKey;
 }
 
+// Range of the one-column build keys (for the direct-array decision).
+__global__ void dim_minmax_kernel(const int32_t* __restrict__ pk, int64_t m, DimHeader* dhdr) {
+  int32_t lo = INT32_MAX, hi = INT32_MIN;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = pk[j];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&dhdr->key_min, lo);
+    atomicMax(&dhdr->key_max, hi);
+  }
+}
+
+// Build.  One-column keys whose range fits the direct array are entered there; otherwise (and
+// for two-column keys) into the hash table.
 template <bool kWide>
 __global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
                                  const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
                                  int64_t m, DimView d, unsigned long long glimit) {
+  const bool direct = !kWide && direct_applies(d, m);
+  const int32_t kmin = d.dhdr->key_min;
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.dhdr->direct = direct ? 1u : 0u;
   bool dup = false;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
        j += (int64_t)gridDim.x * blockDim.x) {
-    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup))
+    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup, direct, kmin))
+      set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
+  }
+  if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
+    if (direct) d.dhdr->direct_failed = 1;
+    else d.jhdr->has_dups = 1;
+  }
+}
+
+// Clears the join slots of a large table only when the hash table turns out to be needed:
+// before the build (phase 0) when the key range does not fit the direct array, after it
+// (phase 1) when a duplicate key turned the direct array down.
+__global__ void dim_clear_join_kernel(DimView d, int64_t m, int phase, int64_t jpairs) {
+  const bool need = phase == 0 ? !direct_applies(d, m) : (d.dhdr->direct && d.dhdr->direct_failed);
+  if (!need) return;
+  const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
+  ulonglong2* w = reinterpret_cast<ulonglong2*>(d.jslots);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < jpairs; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = ones;
+}
+
+// When a duplicate key turned the direct array down, enter every row into the hash table
+// (the group keys are already in their table; finding them again returns the same slots).
+__global__ void dim_fallback_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
+                                    const int8_t* __restrict__ flag, int64_t m, DimView d,
+                                    unsigned long long glimit) {
+  if (!(d.dhdr->direct && d.dhdr->direct_failed)) return;
+  bool dup = false;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    if (!dim_build_row<false>(pk, nullptr, grp, flag, j, d, glimit, dup))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
@@ -64,7 +120,7 @@ probe_kernel(ProbeArgs a) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   Agg* s_tab = reinterpret_cast<Agg*>(smem_raw);
   if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
-  const bool dups = a.jhdr->has_dups != 0;
+  const Lookup L = read_lookup(a);
   if (kMode == kAggSmem) {
     for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) agg_identity(&s_tab[i]);
     __syncthreads();
@@ -72,10 +128,10 @@ probe_kernel(ProbeArgs a) {
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
-    probe_quad<kWide, kMode, kVec>(a, s_tab, dups, q);
+    probe_quad<kWide, kMode, kVec>(a, s_tab, L, q);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-    probe_one<kWide, kMode>(a, s_tab, dups, (nq << 2) + threadIdx.x);
+    probe_one<kWide, kMode>(a, s_tab, L, (nq << 2) + threadIdx.x);
   if (kMode == kAggSmem) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) {
@@ -192,14 +248,36 @@ sirius_status dispatch_probe(const ProbeArgs& a, int mode, bool vec, int threads
 }  // namespace
 
 // ------------------------------------------------------------------ layouts and validation
-DimLayout dim_layout(int64_t m, bool wide, int64_t hint, float lf) {
+DimLayout dim_layout(int64_t m, bool wide, int64_t hint, float lf, bool allow_direct) {
   DimLayout L;
   L.key_width = wide ? 8 : 4;
   L.jcap = sirius_join_table_capacity(m, lf > 0 ? lf : 0.5);
   L.gcap = group_capacity_for(hint > 0 ? hint : (m > 0 ? m : 1));
+  // direct array: key ranges up to 2m values (64-entry granules), one-column keys only
+  L.dcap = (!wide && allow_direct && m > 0) ? ((2 * m + 63) / 64) * 64 : 0;
   L.off_join = 256;
   L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (wide ? 16 : 8), 256);
-  L.total = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
+  L.off_direct = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
+  L.total = align_up(L.off_direct + (size_t)L.dcap * 4, 256);
+  return L;
+}
+
+DimLayout dim_layout_for(const sirius_pipeline_desc* q) {
+  return dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint, q->load_factor,
+                    q->join_mode == 0);
+}
+
+// The layout of a built dim index, from the capacities its build recorded.
+DimLayout dim_layout_of_index(const sirius_dim_index* idx) {
+  DimLayout L;
+  L.key_width = idx->key_width;
+  L.jcap = idx->join_capacity;
+  L.gcap = idx->group_capacity;
+  L.dcap = idx->direct_capacity;
+  L.off_join = 256;
+  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
+  L.off_direct = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
+  L.total = align_up(L.off_direct + (size_t)L.dcap * 4, 256);
   return L;
 }
 
@@ -217,8 +295,10 @@ DimView dim_view(const DimLayout& L, char* base) {
   d.jhdr = (JoinHeader*)(base + L.off_join);
   d.jslots = base + L.off_join + 256;
   d.gkeys = (int64_t*)(base + L.off_gkeys);
+  d.dslot = (uint32_t*)(base + L.off_direct);
   d.jcap = (uint32_t)L.jcap;
   d.gcap = (uint32_t)L.gcap;
+  d.dcap = L.dcap;
   d.key_width = L.key_width;
   return d;
 }
@@ -237,6 +317,7 @@ sirius_status validate_dim(const sirius_pipeline_desc* q) {
   SIRIUS_REQUIRE(q->load_factor >= 0 && q->load_factor <= 0.95f, "pipeline: load_factor out of (0, 0.95]");
   const int64_t hint = q->group_cap_hint > 0 ? q->group_cap_hint : q->m;
   SIRIUS_REQUIRE(hint < (1ll << 30), "pipeline: group_cap_hint too large");
+  SIRIUS_REQUIRE(q->join_mode == 0 || q->join_mode == 1, "pipeline: bad join_mode %d", q->join_mode);
   return SIRIUS_OK;
 }
 
@@ -276,22 +357,46 @@ int choose_mode(int agg_mode, int64_t gslots) {
 sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char* base, cudaStream_t s) {
   DimView d = dim_view(L, base);
   const int64_t jpairs = (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16;
+  const int64_t dpairs = L.dcap / 4;
   const int64_t gslots = L.gcap + 1;
+  // a large join table is cleared only once the build knows the hash table is needed
+  const bool lazy_join = L.dcap > 0 && jpairs * 16 > (16ll << 20);
   {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_INIT);
-    dim_init_kernel<<<grid_for(jpairs > gslots ? jpairs : gslots, 256), 256, 0, s>>>(
-        d.dhdr, d.jhdr, (ulonglong2*)d.jslots, jpairs, d.gkeys, gslots);
+    const int64_t init_jpairs = lazy_join ? 0 : jpairs;
+    int64_t work = init_jpairs > gslots ? init_jpairs : gslots;
+    work = dpairs > work ? dpairs : work;
+    dim_init_kernel<<<grid_for(work, 256), 256, 0, s>>>(d.dhdr, d.jhdr, (ulonglong2*)d.jslots, init_jpairs,
+                                                       (ulonglong2*)d.dslot, dpairs, d.gkeys, gslots);
     SIRIUS_LAUNCH_CHECK();
   }
   if (q->m > 0) {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_BUILD);
     const int g = grid_for(q->m, 256);
     const unsigned long long lim = group_limit_for(L.gcap);
-    if (L.key_width == 8)
+    if (L.key_width == 8) {
       dim_build_kernel<true><<<g, 256, 0, s>>>(q->pk, q->pk_hi, q->grp, q->flag, q->m, d, lim);
-    else
+      SIRIUS_LAUNCH_CHECK();
+    } else {
+      if (L.dcap > 0) {
+        dim_minmax_kernel<<<g, 256, 0, s>>>(q->pk, q->m, d.dhdr);
+        SIRIUS_LAUNCH_CHECK();
+        if (lazy_join) {
+          dim_clear_join_kernel<<<grid_for(jpairs, 256), 256, 0, s>>>(d, q->m, 0, jpairs);
+          SIRIUS_LAUNCH_CHECK();
+        }
+      }
       dim_build_kernel<false><<<g, 256, 0, s>>>(q->pk, nullptr, q->grp, q->flag, q->m, d, lim);
-    SIRIUS_LAUNCH_CHECK();
+      SIRIUS_LAUNCH_CHECK();
+      if (L.dcap > 0) {
+        if (lazy_join) {
+          dim_clear_join_kernel<<<grid_for(jpairs, 256), 256, 0, s>>>(d, q->m, 1, jpairs);
+          SIRIUS_LAUNCH_CHECK();
+        }
+        dim_fallback_kernel<<<g, 256, 0, s>>>(q->pk, q->grp, q->flag, q->m, d, lim);
+        SIRIUS_LAUNCH_CHECK();
+      }
+    }
   }
   return SIRIUS_OK;
 }
@@ -320,13 +425,14 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   a.jslots = d.jslots;
   a.jhdr = d.jhdr;
   a.dhdr = d.dhdr;
+  a.dslot = d.dslot;
   a.tab = r.aggs;
   a.gslots = (uint32_t)gslots;
   const int mode = choose_mode(q->agg_mode, gslots);
   const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
                    (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
   const bool staged_ok = mode == kAggGlobal && vec && ((uintptr_t)q->val & 15) == 0;
-  if (staged_ok && (q->probe_variant == 2 || (q->probe_variant == 0 && q->n >= (1 << 20)))) {
+  if (staged_ok && q->probe_variant == 2) {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
     return d.key_width == 8 ? launch_staged<true>(a, r.phdr, s) : launch_staged<false>(a, r.phdr, s);
   }
@@ -380,8 +486,7 @@ using namespace sirius;
 // ------------------------------------------------------------------ single query
 extern "C" size_t sirius_pipeline_scratch_bytes(const sirius_pipeline_desc* q) {
   if (!q) return 0;
-  const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint,
-                                 q->load_factor);
+  const DimLayout L = dim_layout_for(q);
   return L.total + run_layout(L.gcap).total;
 }
 
@@ -393,8 +498,7 @@ extern "C" sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, siri
   if (st != SIRIUS_OK) return st;
   st = validate_result(result);
   if (st != SIRIUS_OK) return st;
-  const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint,
-                                 q->load_factor);
+  const DimLayout L = dim_layout_for(q);
   const RunLayout R = run_layout(L.gcap);
   Scratch sc;
   st = sc.acquire(d_scratch, scratch_bytes, L.total + R.total, s);
@@ -412,7 +516,7 @@ extern "C" sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, siri
 // ------------------------------------------------------------------ resident build side
 extern "C" size_t sirius_dim_index_bytes(const sirius_pipeline_desc* q) {
   if (!q) return 0;
-  return dim_layout(q->m, q->pk_hi != nullptr, q->group_cap_hint, q->load_factor).total;
+  return dim_layout_for(q).total;
 }
 
 extern "C" sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, sirius_dim_index* idx,
@@ -423,13 +527,14 @@ extern "C" sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, s
   if (st != SIRIUS_OK) return st;
   SIRIUS_REQUIRE(idx && idx->d_mem, "dim index: NULL memory");
   SIRIUS_REQUIRE(((uintptr_t)idx->d_mem & 255) == 0, "dim index: memory must be 256-byte aligned");
-  const DimLayout L = dim_layout(q->m, q->pk_hi != nullptr, q->group_cap_hint, q->load_factor);
+  const DimLayout L = dim_layout_for(q);
   if (idx->bytes < L.total) {
     set_error("dim index: %zu bytes given, %zu needed", idx->bytes, L.total);
     return SIRIUS_ERR_SCRATCH;
   }
   idx->join_capacity = L.jcap;
   idx->group_capacity = L.gcap;
+  idx->direct_capacity = L.dcap;
   idx->key_width = L.key_width;
   if ((st = dim_build(q, L, (char*)idx->d_mem, s)) != SIRIUS_OK) return st;
   if (h_status) {
@@ -445,16 +550,7 @@ extern "C" sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, s
   return SIRIUS_OK;
 }
 
-static DimLayout layout_of(const sirius_dim_index* idx) {
-  DimLayout L;
-  L.key_width = idx->key_width;
-  L.jcap = idx->join_capacity;
-  L.gcap = idx->group_capacity;
-  L.off_join = 256;
-  L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
-  L.total = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
-  return L;
-}
+static DimLayout layout_of(const sirius_dim_index* idx) { return dim_layout_of_index(idx); }
 
 extern "C" size_t sirius_probe_scratch_bytes(const sirius_dim_index* idx) {
   if (!idx) return 0;
@@ -499,7 +595,7 @@ struct HostLayout {
 HostLayout host_layout(const sirius_pipeline_desc* q, int64_t chunk_rows, int64_t out_cap) {
   HostLayout H;
   const bool wide = q->pk_hi != nullptr || q->fk_hi != nullptr;
-  H.L = dim_layout(q->m, wide, q->group_cap_hint, q->load_factor);
+  H.L = dim_layout(q->m, wide, q->group_cap_hint, q->load_factor, q->join_mode == 0);
   H.R = run_layout(H.L.gcap);
   H.chunk = chunk_rows > 0 ? chunk_rows : (16ll << 20);
   if (H.chunk > q->n && q->n > 0) H.chunk = (q->n + 3) / 4 * 4;

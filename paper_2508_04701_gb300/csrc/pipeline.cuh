@@ -13,9 +13,12 @@ constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up 
 // It depends on the dim table only, so it can stay resident and serve many probes.
 struct DimHeader {
   int32_t status;                // first device error of the build (TABLE_FULL)
-  uint32_t pad0;
+  uint32_t direct;               // 1: build keys dense and unique, the direct array is in use
   unsigned long long distinct;   // group slots claimed
-  unsigned long long pad[30];
+  int32_t key_min, key_max;      // range of the one-column build keys
+  uint32_t direct_failed;        // a duplicate key turned the direct array down: hash table used
+  uint32_t pad1;
+  unsigned long long pad[28];
 };
 static_assert(sizeof(DimHeader) == 256, "dim header is 256 bytes");
 
@@ -28,10 +31,16 @@ struct PipeHeader {
 };
 static_assert(sizeof(PipeHeader) == 256, "pipeline header is 256 bytes");
 
+// Dense one-column build keys (a range of at most 2m values, no duplicates) are joined through
+// a direct-address array -- dslot[key - key_min] = group slot -- instead of the hash table (the
+// "perfect hash" join of dense integer keys): 4 bytes per key value instead of 16 per key at
+// load factor one half, so the structure of a 15M-row dim stays in L2.  The decision is taken
+// on the device during the build; the hash table is built only when it is needed.
 struct DimLayout {
   int key_width = 4;
   int64_t jcap = 0, gcap = 0;
-  size_t off_join = 256, off_gkeys = 0, total = 0;
+  int64_t dcap = 0;  // direct-array entries (0: hash table only)
+  size_t off_join = 256, off_gkeys = 0, off_direct = 0, total = 0;
 };
 
 struct RunLayout {
@@ -44,8 +53,10 @@ struct DimView {
   JoinHeader* jhdr;
   void* jslots;
   int64_t* gkeys;
+  uint32_t* dslot;
   uint32_t jcap;
   uint32_t gcap;
+  int64_t dcap;
   int key_width;
 };
 
@@ -79,9 +90,27 @@ struct ProbeArgs {
   const void* jslots;
   const JoinHeader* jhdr;
   const DimHeader* dhdr;
+  const uint32_t* dslot;
   Agg* tab;
   uint32_t gslots;
 };
+
+// How the probe pass finds a key's group slot, read once from the dim header.
+struct Lookup {
+  bool direct;     // direct array in use
+  bool dups;       // hash table holds duplicate keys (walks go past the first match)
+  int32_t kmin;
+  uint32_t range;  // key_max - key_min + 1 (direct mode)
+};
+
+__device__ __forceinline__ Lookup read_lookup(const ProbeArgs& a) {
+  Lookup L;
+  L.direct = a.dhdr->direct != 0 && a.dhdr->direct_failed == 0;
+  L.dups = a.jhdr->has_dups != 0;
+  L.kmin = a.dhdr->key_min;
+  L.range = (uint32_t)((int64_t)a.dhdr->key_max - (int64_t)a.dhdr->key_min + 1);
+  return L;
+}
 
 // ------------------------------------------------------------------ probe pass, per row
 // One join-table slot as (key, payload); payload kEmpty32 = empty.  The table is read-only
@@ -123,8 +152,22 @@ __device__ __forceinline__ void load_bucket(const void* slots, uint32_t s, uint6
 // selected row is loaded before any row is examined, so four sector misses are in flight
 // together; a walk continues bucket by bucket only past full buckets.
 template <bool kWide, int kMode>
-__device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, bool dups, uint32_t bits,
+__device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, const Lookup& L, uint32_t bits,
                                            const uint64_t (&key)[4], const int64_t (&v)[4]) {
+  if (!kWide && L.direct) {
+    // dense keys: one 4-byte read of the direct array per selected row, all four in flight
+    uint32_t gs[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t k = (uint32_t)key[r] - (uint32_t)L.kmin;
+      gs[r] = (((bits >> r) & 1u) && k < L.range) ? __ldg(a.dslot + k) : kEmpty32;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (gs[r] != kEmpty32) aggregate<kMode>(a, s_tab, gs[r], v[r]);
+    return;
+  }
+  const bool dups = L.dups;
   constexpr int kPer = kWide ? 2 : 4;  // slots per bucket
   uint32_t s[4];
   uint64_t w[4][4];
@@ -164,7 +207,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, bool 
 
 // Filter, probe and aggregate the four rows of quad q (rows 4q .. 4q+3, all < n).
 template <bool kWide, int kMode, bool kVec>
-__device__ __forceinline__ void probe_quad(const ProbeArgs& a, Agg* s_tab, bool dups, int64_t q) {
+__device__ __forceinline__ void probe_quad(const ProbeArgs& a, Agg* s_tab, const Lookup& L, int64_t q) {
   const int64_t row0 = q << 2;
   uint32_t bits = 0;
   uint64_t key[4];
@@ -198,37 +241,53 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, Agg* s_tab, bool 
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-  probe_rows<kWide, kMode>(a, s_tab, dups, bits, key, v);
+  probe_rows<kWide, kMode>(a, s_tab, L, bits, key, v);
 }
 
 // Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
 template <bool kWide, int kMode>
-__device__ __forceinline__ void probe_one(const ProbeArgs& a, Agg* s_tab, bool dups, int64_t r) {
+__device__ __forceinline__ void probe_one(const ProbeArgs& a, Agg* s_tab, const Lookup& L, int64_t r) {
   if (!cmp_op(a.pred[r], a.lit, a.op)) return;
   uint64_t key[4] = {0, 0, 0, 0};
   int64_t v[4] = {0, 0, 0, 0};
   key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
   v[0] = a.val[r];
-  probe_rows<kWide, kMode>(a, s_tab, dups, 1u, key, v);
+  probe_rows<kWide, kMode>(a, s_tab, L, 1u, key, v);
 }
 
 // Build step of one dim row j: enter its group key into the group table (slot gs), then
 // (pk -> gs) into the join table.  Returns false on TABLE_FULL.
+// In direct mode the row claims dslot[key - kmin] with one CAS; finding it taken means a
+// duplicate key (dup = true), which turns the direct array down for this dim.
 template <bool kWide>
 __device__ __forceinline__ bool dim_build_row(const int32_t* pk, const int32_t* pk_hi, const int32_t* grp,
                                               const int8_t* flag, int64_t j, const DimView& d,
-                                              unsigned long long glimit, bool& dup) {
+                                              unsigned long long glimit, bool& dup, bool direct = false,
+                                              int32_t kmin = 0) {
   const int64_t gk = group_key(grp[j], flag, j);
   const int64_t gs = group_find_or_insert(d.gkeys, d.gcap, gk, &d.dhdr->distinct, glimit);
   if (gs < 0) return false;
   if (kWide)
     return join_insert64((ulonglong2*)d.jslots, d.jcap, pack_key64(pk_hi[j], pk[j]), (uint32_t)gs, dup);
   const uint32_t key = (uint32_t)pk[j];
+  if (direct) {
+    if (atomicCAS(&d.dslot[key - (uint32_t)kmin], kEmpty32, (uint32_t)gs) != kEmpty32) dup = true;
+    return true;
+  }
   return join_insert32((uint64_t*)d.jslots, d.jcap, key, (uint64_t)key | ((uint64_t)(uint32_t)gs << 32), dup);
 }
 
+// Whether a dim's build takes the direct array: one-column keys whose range fits dcap.
+__device__ __forceinline__ bool direct_applies(const DimView& d, int64_t m) {
+  if (d.key_width != 4 || d.dcap <= 0 || m <= 0) return false;
+  const int64_t range = (int64_t)d.dhdr->key_max - (int64_t)d.dhdr->key_min + 1;
+  return range >= 1 && range <= d.dcap;
+}
+
 // ------------------------------------------------------------------ host phases
-DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor);
+DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor, bool allow_direct);
+DimLayout dim_layout_for(const sirius_pipeline_desc* q);
+DimLayout dim_layout_of_index(const sirius_dim_index* idx);
 RunLayout run_layout(int64_t gcap);
 DimView dim_view(const DimLayout& L, char* base);
 RunView run_view(const RunLayout& R, char* base);

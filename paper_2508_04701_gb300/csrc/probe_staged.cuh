@@ -78,7 +78,17 @@ __global__ void __launch_bounds__(kThreads, 1) probe_staged_kernel(ProbeArgs a, 
   int* timed_out = reinterpret_cast<int*>(bars + kColStages);
 
   if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
-  const bool dups = a.jhdr->has_dups != 0;
+  const Lookup L = read_lookup(a);
+  const bool dups = L.dups;
+  if (L.direct) {
+    // dense keys: the direct array needs no gathered buckets; probe the rows in place
+    const int64_t nq = a.n >> 2;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x)
+      probe_quad<kWide, kAggGlobal, true>(a, nullptr, L, q);
+    if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
+      probe_one<kWide, kAggGlobal>(a, nullptr, L, (nq << 2) + threadIdx.x);
+    return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nfull = (a.n >> 2) << 2;  // rows moved by TMA; the n % 4 tail goes scalar
   const int64_t ntiles = (nfull + kTile - 1) / kTile;
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) probe_staged_kernel(ProbeArgs a, 
   }
   cp_async_wait<0>();
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - nfull)
-    probe_one<kWide, kAggGlobal>(a, nullptr, dups, nfull + threadIdx.x);
+    probe_one<kWide, kAggGlobal>(a, nullptr, L, nfull + threadIdx.x);
   if (threadIdx.x == 0 && *timed_out) set_status(run_status, SIRIUS_ERR_TIMEOUT);
 }
 

@@ -1,0 +1,45 @@
+"""A small, fixed pipeline case for profiling one probe kernel under ncu.
+
+    python -m paper_2508_04701_gb300.profile_case [--n ROWS] [--m DIM_ROWS] [--variant direct|staged]
+                                                  [--load-factor LF] [--runs R]
+
+Builds the 600M-row query's distributions at a reduced fact size (default 100M rows, 1.6 GB of
+columns, above the L2 size) against the full 15M-row dim table, and runs the pipeline R times.
+"""
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--n", type=int, default=100_000_000)
+    p.add_argument("--m", type=int, default=15_000_000)
+    p.add_argument("--variant", default="direct", choices=["auto", "direct", "staged"])
+    p.add_argument("--load-factor", type=float, default=0.0)
+    p.add_argument("--runs", type=int, default=2)
+    p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed"])
+    a = p.parse_args()
+    import torch
+
+    from paper_2508_04701_gb300 import datagen as dg
+    from paper_2508_04701_gb300 import sirius as S
+    if a.workload == "skewed":
+        spec, hint = dg.skewed(n=a.n, m=a.m), a.m
+    else:
+        spec, hint = dg.plain_scale(n=a.n, m=a.m, composite=a.workload == "composite"), 100_000
+    dim = dg.gen_dim_device(spec)
+    fact = dg.gen_fact_device(spec, dim)
+    desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, hint, a.load_factor, probe_variant=a.variant)
+    outs = S.PipelineOutputs(hint + 1)
+    scratch = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device="cuda")
+    for _ in range(a.runs):
+        g = S.sirius_run_pipeline(desc, outs, scratch)
+    torch.cuda.synchronize()
+    print(f"profile case ok: n={a.n} m={a.m} variant={a.variant} groups={g}")
+
+
+if __name__ == "__main__":
+    main()

@@ -25,6 +25,7 @@ OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
 AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
 AGG_MODES = {"auto": 0, "smem": 1, "global": 2}
 PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2}
+JOIN_MODES = {"auto": 0, "hash": 1}
 
 
 class SiriusError(RuntimeError):
@@ -42,7 +43,8 @@ class PipelineDesc(ctypes.Structure):
                 ("op", ctypes.c_int32), ("literal", ctypes.c_int32), ("aggs", ctypes.c_uint32),
                 ("agg_mode", ctypes.c_int32), ("group_cap_hint", ctypes.c_int64),
                 ("load_factor", ctypes.c_float), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("probe_variant", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("probe_variant", ctypes.c_int32),
+                ("join_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -60,6 +62,7 @@ class JoinTable(ctypes.Structure):
 class DimIndex(ctypes.Structure):
     _fields_ = [("d_mem", ctypes.c_void_p), ("bytes", ctypes.c_size_t),
                 ("join_capacity", ctypes.c_int64), ("group_capacity", ctypes.c_int64),
+                ("direct_capacity", ctypes.c_int64),
                 ("key_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
@@ -326,7 +329,8 @@ def _host_ptr(t: Optional[torch.Tensor]) -> Optional[int]:
 def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="lt",
               literal: int = 50, aggs="sum,count,min,max", group_cap_hint: int = 0,
               load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
-              blocks_per_sm: int = 0, host: bool = False, probe_variant="auto") -> PipelineDesc:
+              blocks_per_sm: int = 0, host: bool = False, probe_variant="auto",
+              join_mode="auto") -> PipelineDesc:
     """A pipeline descriptor over device columns (host=True: over host columns, for
     sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?"""
     P = _host_ptr if host else _ptr
@@ -337,7 +341,8 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
         OPS[op] if isinstance(op, str) else int(op), int(literal), _agg_mask(aggs),
         AGG_MODES[agg_mode] if isinstance(agg_mode, str) else int(agg_mode), int(group_cap_hint),
         float(load_factor), int(block_threads), int(blocks_per_sm),
-        PROBE_VARIANTS[probe_variant] if isinstance(probe_variant, str) else int(probe_variant))
+        PROBE_VARIANTS[probe_variant] if isinstance(probe_variant, str) else int(probe_variant),
+        JOIN_MODES[join_mode] if isinstance(join_mode, str) else int(join_mode), 0)
     # the descriptor holds raw pointers: keep the tensors they point into alive with it
     d._columns = (dict(fact), dict(dim))
     return d
@@ -398,7 +403,7 @@ class DimIndexBuffer:
     def __init__(self, desc: PipelineDesc, device="cuda", stream=None):
         nbytes = int(lib().sirius_dim_index_bytes(ctypes.byref(desc)))
         self.mem = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
-        self.struct = DimIndex(self.mem.data_ptr(), self.mem.numel(), 0, 0, 0, 0)
+        self.struct = DimIndex(self.mem.data_ptr(), self.mem.numel(), 0, 0, 0, 0, 0)
         st = ctypes.c_int32(0)
         _check(lib().sirius_dim_index_build(ctypes.byref(desc), ctypes.byref(self.struct),
                                             ctypes.byref(st), _stream(stream)))
@@ -409,6 +414,12 @@ class DimIndexBuffer:
 
     def probe_scratch_bytes(self) -> int:
         return int(lib().sirius_probe_scratch_bytes(ctypes.byref(self.struct)))
+
+    def join_kind(self) -> str:
+        """'direct' when the build took the direct-address array, else 'hash' (reads the
+        index header: int32 status, uint32 direct at byte 4, uint32 direct_failed at byte 24)."""
+        h = self.mem[:32].cpu().numpy().view("uint32")
+        return "direct" if h[1] and not h[6] else "hash"
 
 
 def sirius_dim_index_build(desc: PipelineDesc, device="cuda", stream=None) -> DimIndexBuffer:

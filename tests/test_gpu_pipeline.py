@@ -173,6 +173,50 @@ def test_staged_probe_duplicates_composite_overflow(S, lf):
     check(S, fact, dim, "lt", spec.t, hint=100_000, load_factor=lf, probe_variant="staged")
 
 
+def _keys_case(case, rng, m):
+    if case == "offset":
+        return (rng.permutation(m) + 1_000_000_000).astype(np.int32), "direct"
+    if case == "negative":
+        return (rng.permutation(m) - 2**31).astype(np.int32), "direct"
+    if case == "gaps":        # range 1.9 m, unique
+        return rng.choice(int(1.9 * m), size=m, replace=False).astype(np.int32), "direct"
+    if case == "too_sparse":  # range 3 m
+        return rng.choice(3 * m, size=m, replace=False).astype(np.int32), "hash"
+    if case == "dups_dense":  # dense range with repeated keys: falls back to the hash table
+        return rng.integers(0, m // 2, size=m).astype(np.int32), "hash"
+    if case == "extremes":    # INT32_MIN .. INT32_MIN + m and INT32_MAX at the top: sparse
+        k = (np.arange(m) - 2**31).astype(np.int32)
+        k[-1] = 2**31 - 1
+        return k, "hash"
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["offset", "negative", "gaps", "too_sparse", "dups_dense", "extremes"])
+@pytest.mark.parametrize("join_mode", ["auto", "hash"])
+def test_direct_array_decision(S, case, join_mode):
+    rng = np.random.default_rng(31)
+    m = 50_000
+    pk, kind = _keys_case(case, rng, m)
+    dim = {"pk": pk, "grp": rng.integers(0, 700, size=m).astype(np.int32)}
+    lo, hi = int(pk.min()), int(pk.max())
+    fk = rng.integers(lo, hi + 1, size=400_003, dtype=np.int64)
+    fk[::5] = pk[rng.integers(0, m, size=fk[::5].size)]
+    fact = {"fk": fk.astype(np.int32), "pred": rng.integers(0, 100, size=fk.size).astype(np.int32),
+            "val": rng.integers(-10**9, 10**9, size=fk.size)}
+    dd, df = dev(dim), dev(fact)
+    desc = S.make_desc(df, dd, "lt", 55, group_cap_hint=700, join_mode=join_mode)
+    index = S.sirius_dim_index_build(desc)
+    assert index.join_kind() == (kind if join_mode == "auto" else "hash")
+    outs = S.PipelineOutputs(S.lib().sirius_groupby_capacity(700) + 1)
+    g = S.sirius_run_probe(desc, index, outs)
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in outs.trimmed(g).items()})
+    want = O.pipeline(fact, dim, "lt", 55)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
+    for mode in ("smem", "global"):   # the fused call takes the same decision
+        check(S, fact, dim, "lt", 55, hint=700, agg_mode=mode, join_mode=join_mode)
+
+
 def test_resident_dim_index_serves_many_probes(S):
     spec = dg.StarSpec("t", n=300_001, m=20_000, fk_domain=22_000, grp_bound=500, seed=9)
     dim = dg.gen_dim_host(spec)
