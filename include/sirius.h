@@ -92,6 +92,26 @@ sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t op, int32_t
                             uint32_t* d_row_ids, int64_t* d_count, int64_t* h_count,
                             void* d_scratch, size_t scratch_bytes, sirius_stream stream);
 
+/* sirius_filter_static: sirius_filter for callers that cannot allocate device memory at all.
+ * The paper has no counterpart; it exists for code that must not call cudaMalloc or
+ * cudaMallocAsync -- a host callback or another latency-critical path where an allocation
+ * could block the device or fail, or a process whose device memory is entirely owned by
+ * another allocator -- and so can pass neither scratch nor NULL.  The caller still passes the
+ * input column and the outputs (d_row_ids with room for n ids; d_count / h_count as in
+ * sirius_filter, same results).  The look-back scratch lives instead in one file-scope device
+ * array of the library, sized for at most sirius_filter_static_max_rows() = 2^28 rows (about
+ * 512 KB); every GPU that loads the library holds that array until the process exits.  Larger
+ * n is rejected with SIRIUS_ERR_INVALID and a message.  The call allocates nothing: it clears
+ * the part of the array it uses (stream-ordered) before its kernel.  The first call on each
+ * device looks up the array's device address (with that device current) and caches it; make
+ * that first call before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: two calls that may overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
+int64_t sirius_filter_static_max_rows(void);
+sirius_status sirius_filter_static(const int32_t* d_col, int64_t n, int32_t op, int32_t literal,
+                                   uint32_t* d_row_ids, int64_t* d_count, int64_t* h_count,
+                                   sirius_stream stream);
+
 /* ------------------------------------------------------------------ A1 / A3: hash join
  * An open-addressing hash table of the build side (Sec. 3.2.2 join operator; Sec. 4.2: joins
  * dominate).  Keys are one int32 column or a two-column (hi, lo) int32 key compared as one

@@ -7,6 +7,8 @@
 // (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA
 // technical report NVR-2016-002).  Tiles take tickets from an atomic counter, so every tile a
 // look-back waits on has already started; each wait is still bounded and reports TIMEOUT.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace sirius {
@@ -218,6 +220,85 @@ extern "C" sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t 
     *h_count = (int64_t)h.count;
     if (h.status != 0) {
       set_error("filter: device status %d", h.status);
+      return (sirius_status)h.status;
+    }
+  }
+  return SIRIUS_OK;
+}
+
+// ------------------------------------------------------------------ filter without allocation
+// sirius_filter_static: the same filter for callers that cannot allocate device memory at
+// all -- code running where cudaMalloc / cudaMallocAsync are unavailable or must not be called
+// (a host callback or another latency-critical path where an allocation could block the
+// device or fail, or a process whose device memory is entirely owned by another allocator and
+// that passes only its own inputs and outputs).  Its look-back scratch (the 256-byte header and
+// one status word per 4096-row tile) lives in the file-scope device array below, which every
+// GPU that loads this library holds until the process exits.
+namespace {
+constexpr int64_t kStaticFilterMaxRows = 1ll << 28;  // 268 435 456 rows
+constexpr int64_t kStaticFilterMaxTiles = (kStaticFilterMaxRows + kTileRows - 1) / kTileRows;
+static __device__ __align__(256) uint64_t g_filter_static_scratch[32 + kStaticFilterMaxTiles];
+
+std::mutex g_static_mu;
+void* g_static_addr[64] = {};  // device address of the array, per device ordinal
+
+// Host code cannot use the array's name as a device address; look the address up once per
+// device, with that device current.
+sirius_status static_scratch_addr(void** out) {
+  int dev = 0;
+  SIRIUS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("filter_static: device ordinal %d beyond 63", dev);
+    return SIRIUS_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> g(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_filter_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("filter_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return SIRIUS_ERR_CUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return SIRIUS_OK;
+}
+}  // namespace
+
+extern "C" int64_t sirius_filter_static_max_rows(void) { return kStaticFilterMaxRows; }
+
+extern "C" sirius_status sirius_filter_static(const int32_t* d_col, int64_t n, int32_t op, int32_t literal,
+                                              uint32_t* d_row_ids, int64_t* d_count, int64_t* h_count,
+                                              sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  SIRIUS_REQUIRE(n >= 0 && n <= kStaticFilterMaxRows,
+                 "filter_static: n=%lld exceeds the static scratch limit of %lld rows (use sirius_filter)",
+                 (long long)n, (long long)kStaticFilterMaxRows);
+  SIRIUS_REQUIRE(op >= SIRIUS_LT && op <= SIRIUS_NE, "filter_static: bad comparison %d", op);
+  SIRIUS_REQUIRE(n == 0 || (d_col && d_row_ids), "filter_static: NULL column or output");
+  if (n == 0) {
+    if (d_count) SIRIUS_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int64_t), s));
+    if (h_count) *h_count = 0;
+    return SIRIUS_OK;
+  }
+  void* base = nullptr;
+  sirius_status st = static_scratch_addr(&base);
+  if (st != SIRIUS_OK) return st;
+  DevHeader* hdr = (DevHeader*)base;
+  uint64_t* status = (uint64_t*)((char*)base + 256);
+  // filter_launch clears the header and the status words this call uses before its kernel
+  st = filter_launch(d_col, n, op, literal, d_row_ids, d_count, hdr, status, s);
+  if (st != SIRIUS_OK) return st;
+  if (h_count) {
+    DevHeader h;
+    SIRIUS_CUDA_TRY(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SIRIUS_CUDA_TRY(cudaStreamSynchronize(s));
+    *h_count = (int64_t)h.count;
+    if (h.status != 0) {
+      set_error("filter_static: device status %d", h.status);
       return (sirius_status)h.status;
     }
   }

@@ -79,6 +79,8 @@ SIGNATURES = {
     "sirius_profile_stop": (_I32, [_VP, _VP, _I32]),
     "sirius_filter_scratch_bytes": (_SZ, [_I64]),
     "sirius_filter": (_I32, [_VP, _I64, _I32, _I32, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "sirius_filter_static_max_rows": (_I64, []),
+    "sirius_filter_static": (_I32, [_VP, _I64, _I32, _I32, _VP, _VP, _VP, _VP]),
     "sirius_join_table_capacity": (_I64, [_I64, _F64]),
     "sirius_join_table_bytes": (_SZ, [_I64, _I32]),
     "sirius_hash_join_build": (_I32, [_VP, _VP, _I64, ctypes.POINTER(JoinTable), _VP, _VP]),
