@@ -74,7 +74,8 @@ enum { SIRIUS_PHASE_FILTER = 0, SIRIUS_PHASE_JOIN_BUILD = 1, SIRIUS_PHASE_JOIN_P
        SIRIUS_PHASE_GATHER = 3, SIRIUS_PHASE_GROUPBY = 4, SIRIUS_PHASE_PIPE_INIT = 5,
        SIRIUS_PHASE_PIPE_BUILD = 6, SIRIUS_PHASE_PIPE_PROBE = 7, SIRIUS_PHASE_PIPE_FINALIZE = 8,
        SIRIUS_PHASE_BATCH_GRAPH = 9, SIRIUS_PHASE_BATCH_BUILD = 10, SIRIUS_PHASE_BATCH_PROBE = 11,
-       SIRIUS_PHASE_BATCH_FINALIZE = 12, SIRIUS_PHASE_COPY = 13, SIRIUS_PHASES = 16 };
+       SIRIUS_PHASE_BATCH_FINALIZE = 12, SIRIUS_PHASE_COPY = 13, SIRIUS_PHASE_PIPE_AGGREGATE = 14,
+       SIRIUS_PHASES = 16 };
 void sirius_profile_start(void);
 sirius_status sirius_profile_stop(double* ms, int64_t* launches, int32_t nphases);
 
@@ -208,8 +209,14 @@ typedef struct {
   int32_t op;               /* sirius_cmp */
   int32_t literal;
   uint32_t aggs;            /* SIRIUS_AGG_* mask (COUNT is always computed) */
-  int32_t agg_mode;         /* 0 auto, 1 shared-memory table, 2 global atomics,
-                               3 global atomics behind a per-block hot-group cache */
+  int32_t agg_mode;         /* 0 auto; 1 per-block shared-memory table (group table of at most
+                               3072 slots); 2 global reductions; 3 partitioned: the probe pass
+                               writes (group slot, value) per joined row, grouped by 4096-slot
+                               partition within 4096-row tiles, and a second pass aggregates
+                               each partition in shared memory (group table of at most 2^20
+                               slots); 4 global reductions behind a per-block cache of 2048
+                               hot groups in shared memory (skewed keys).  Auto: 1 when it
+                               fits, else 4 from 1Mi fact rows, else 2 */
   int64_t group_cap_hint;   /* expected distinct group keys in the dim; 0 -> m */
   float load_factor;        /* join table load factor; 0 -> default 0.5 */
   int32_t block_threads;    /* probe kernel block size; 0 -> default */
@@ -266,9 +273,10 @@ size_t sirius_dim_index_bytes(const sirius_pipeline_desc* q);
 sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, sirius_dim_index* idx,
                                      int32_t* h_status, sirius_stream stream);
 /* The probe, aggregate and finalize phases against a built dim index: uses the fact and query
- * fields of `q`.  Scratch: sirius_probe_scratch_bytes(idx) (the aggregates).  The dim index is
- * only read, so any number of probes may use it at once, each with its own scratch. */
-size_t sirius_probe_scratch_bytes(const sirius_dim_index* idx);
+ * fields of `q`.  Scratch: sirius_probe_scratch_bytes(q, idx) (the aggregates, plus the tuple
+ * buffers of partitioned aggregation).  The dim index is only read, so any number of probes
+ * may use it at once, each with its own scratch. */
+size_t sirius_probe_scratch_bytes(const sirius_pipeline_desc* q, const sirius_dim_index* idx);
 sirius_status sirius_run_probe(const sirius_pipeline_desc* q, const sirius_dim_index* idx,
                                sirius_result* result, void* d_scratch, size_t scratch_bytes,
                                sirius_stream stream);

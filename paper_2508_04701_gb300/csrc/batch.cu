@@ -479,7 +479,9 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     const bool wide = pre ? indexes[i].key_width == 8 : (q->pk_hi != nullptr || q->fk_hi != nullptr);
     const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
                      (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
-    cls[i] = (wide ? 1 : 0) | (choose_mode(q->agg_mode, gcap + 1) == kAggSmem ? 2 : 0) | (vec ? 4 : 0);
+    // batches aggregate per probe unit in shared memory or with reductions (no partitioned mode)
+    const int am = (q->agg_mode == kAggPart || q->agg_mode == kAggHot) ? kAggGlobal : q->agg_mode;
+    cls[i] = (wide ? 1 : 0) | (choose_mode(am, gcap + 1, 0) == kAggSmem ? 2 : 0) | (vec ? 4 : 0);
     order[i] = i;
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cls[x] < cls[y]; });

@@ -6,7 +6,7 @@
 
 namespace sirius {
 
-enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2 };
+enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2, kAggPart = 3, kAggHot = 4 };
 constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up to 3072 slots
 
 // Build side ("dim index"): [DimHeader | JoinHeader + join slots | group keys[gcap + 1]].
@@ -43,9 +43,13 @@ struct DimLayout {
   size_t off_join = 256, off_gkeys = 0, off_direct = 0, total = 0;
 };
 
+// Run state: [PipeHeader | Agg[gslots] | (partitioned mode) tuple slots, tuple values, prefixes].
 struct RunLayout {
   int64_t gslots = 0;
-  size_t off_aggs = 256, total = 0;
+  int mode = kAggGlobal;  // aggregation mode chosen for this run
+  int parts = 0;          // partitioned mode: partitions and pass-1 tiles
+  int64_t ntiles = 0;
+  size_t off_aggs = 256, off_tgs = 0, off_tval = 0, off_prefix = 0, total = 0;
 };
 
 struct DimView {
@@ -63,6 +67,12 @@ struct DimView {
 struct RunView {
   PipeHeader* phdr;
   Agg* aggs;
+  uint32_t* tgs;
+  int64_t* tval;
+  int32_t* prefix;
+  int mode;
+  int parts;
+  int64_t ntiles;
 };
 
 struct PipeOut {
@@ -128,14 +138,35 @@ __device__ __forceinline__ void load_slot(const void* slots, uint32_t s, uint64_
   }
 }
 
+__device__ __forceinline__ void agg_update_smem(Agg* t, int64_t v, uint32_t aggs) {
+  if (aggs & SIRIUS_AGG_SUM) atomicAdd(&t->sum, (unsigned long long)v);
+  atomicAdd(&t->count, 1ull);
+  if ((aggs & SIRIUS_AGG_MIN) && v < t->min) atomicMin(&t->min, (long long)v);
+  if ((aggs & SIRIUS_AGG_MAX) && v > t->max) atomicMax(&t->max, (long long)v);
+}
+
+// Hot-group cache (kAggHot): kHotEntries direct-mapped entries per block, each claimed once by
+// the first group slot that maps to it (tags[e], kEmpty32 = free).  Under a skewed key
+// distribution the frequent groups claim entries early and then aggregate on chip; other
+// rows go to the global table.  Layout in dynamic shared memory: Agg[kHotEntries], then tags.
+constexpr int kHotBits = 11;
+constexpr int kHotEntries = 1 << kHotBits;
+constexpr size_t kHotSmemBytes = (size_t)kHotEntries * (sizeof(Agg) + 4);
+
 template <int kMode>
 __device__ __forceinline__ void aggregate(const ProbeArgs& a, Agg* s_tab, uint32_t gs, int64_t v) {
   if (kMode == kAggSmem) {
-    Agg* t = &s_tab[gs];
-    if (a.aggs & SIRIUS_AGG_SUM) atomicAdd(&t->sum, (unsigned long long)v);
-    atomicAdd(&t->count, 1ull);
-    if ((a.aggs & SIRIUS_AGG_MIN) && v < t->min) atomicMin(&t->min, (long long)v);
-    if ((a.aggs & SIRIUS_AGG_MAX) && v > t->max) atomicMax(&t->max, (long long)v);
+    agg_update_smem(&s_tab[gs], v, a.aggs);
+  } else if (kMode == kAggHot) {
+    uint32_t* tags = reinterpret_cast<uint32_t*>(s_tab + kHotEntries);
+    const uint32_t e = (gs * 2654435761u) >> (32 - kHotBits);
+    uint32_t t = *(volatile uint32_t*)&tags[e];
+    if (t == kEmpty32) {
+      t = atomicCAS(&tags[e], kEmpty32, gs);
+      if (t == kEmpty32) t = gs;
+    }
+    if (t == gs) agg_update_smem(&s_tab[e], v, a.aggs);
+    else agg_update_global(&a.tab[gs], v, a.aggs);
   } else {
     agg_update_global(&a.tab[gs], v, a.aggs);
   }
@@ -288,12 +319,13 @@ __device__ __forceinline__ bool direct_applies(const DimView& d, int64_t m) {
 DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor, bool allow_direct);
 DimLayout dim_layout_for(const sirius_pipeline_desc* q);
 DimLayout dim_layout_of_index(const sirius_dim_index* idx);
-RunLayout run_layout(int64_t gcap);
+// n: fact rows of the run (sizes the partitioned-mode buffers); agg_mode as in the descriptor.
+RunLayout run_layout(int64_t gcap, int64_t n = 0, int agg_mode = kAggGlobal);
 DimView dim_view(const DimLayout& L, char* base);
 RunView run_view(const RunLayout& R, char* base);
 sirius_status validate_dim(const sirius_pipeline_desc* q);
 sirius_status validate_fact(const sirius_pipeline_desc* q);
-int choose_mode(int agg_mode, int64_t gslots);
+int choose_mode(int agg_mode, int64_t gslots, int64_t n);
 sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char* base, cudaStream_t s);
 sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s);
 sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,

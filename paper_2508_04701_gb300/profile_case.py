@@ -22,6 +22,7 @@ def main():
     p.add_argument("--runs", type=int, default=2)
     p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed"])
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
+    p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot"])
     a = p.parse_args()
     import torch
 
@@ -33,8 +34,8 @@ def main():
         spec, hint = dg.plain_scale(n=a.n, m=a.m, composite=a.workload == "composite"), 100_000
     dim = dg.gen_dim_device(spec)
     fact = dg.gen_fact_device(spec, dim)
-    desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, hint, a.load_factor, probe_variant=a.variant,
-                       join_mode=a.join_mode)
+    desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, hint, a.load_factor, agg_mode=a.agg_mode,
+                       probe_variant=a.variant, join_mode=a.join_mode)
     outs = S.PipelineOutputs(hint + 1)
     scratch = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device="cuda")
     for _ in range(a.runs):

@@ -163,7 +163,7 @@ class Server:
         self.use_graph = use_graph
         dev = pool.device
         self.out_cap = S.lib().sirius_groupby_capacity(pool.hint) + 1
-        probe_bytes = pool.dim_index[0].probe_scratch_bytes()
+        probe_bytes = pool.dim_index[0].probe_scratch_bytes(S.PipelineDesc())  # aggregates only
         # processing-region bytes of one request: its aggregates and its result arrays
         self.req_bytes = probe_bytes + len(RESULT_COLS) * 8 * self.out_cap
         self.slots = [_Slot(max_batch, self.out_cap, max_batch * probe_bytes + 4096, dev) for _ in range(slots)]
@@ -248,7 +248,8 @@ def sequential_fifo(pool: ResidentPool, requests: List[Request], keep_results: b
     dev = pool.device
     out_cap = S.lib().sirius_groupby_capacity(pool.hint) + 1
     outs = S.PipelineOutputs(out_cap, dev)
-    scratch = torch.empty(pool.dim_index[0].probe_scratch_bytes() + 4096, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(pool.dim_index[0].probe_scratch_bytes(S.PipelineDesc()) + 4096, dtype=torch.uint8,
+                          device=dev)
     t0 = time.perf_counter()
     for r in sorted(requests, key=lambda r: r.arrival):
         now = time.perf_counter() - t0

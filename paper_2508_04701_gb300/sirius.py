@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CAPACITY", 4: "TABLE_FULL",
 LT, LE, GT, GE, EQ, NE = range(6)
 OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
 AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
-AGG_MODES = {"auto": 0, "smem": 1, "global": 2}
+AGG_MODES = {"auto": 0, "smem": 1, "global": 2, "part": 3, "hot": 4}
 PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2}
 JOIN_MODES = {"auto": 0, "hash": 1}
 
@@ -99,7 +99,7 @@ SIGNATURES = {
     "sirius_dim_index_bytes": (_SZ, [ctypes.POINTER(PipelineDesc)]),
     "sirius_dim_index_build": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(DimIndex), _VP,
                                       _VP]),
-    "sirius_probe_scratch_bytes": (_SZ, [ctypes.POINTER(DimIndex)]),
+    "sirius_probe_scratch_bytes": (_SZ, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(DimIndex)]),
     "sirius_run_probe": (_I32, [ctypes.POINTER(PipelineDesc), ctypes.POINTER(DimIndex),
                                 ctypes.POINTER(Result), _VP, _SZ, _VP]),
     "sirius_pipeline_host_scratch_bytes": (_SZ, [ctypes.POINTER(PipelineDesc), _I64, _I64]),
@@ -170,7 +170,7 @@ def launch_count() -> int:
 
 PHASES = ["filter", "join_build", "join_probe", "gather", "groupby", "pipe_init", "pipe_build",
           "pipe_probe", "pipe_finalize", "batch_graph", "batch_build", "batch_probe",
-          "batch_finalize", "copy", "reserved14", "reserved15"]
+          "batch_finalize", "copy", "pipe_aggregate", "reserved15"]
 
 
 def profile_start():
@@ -414,8 +414,10 @@ class DimIndexBuffer:
     def nbytes(self) -> int:
         return self.mem.numel()
 
-    def probe_scratch_bytes(self) -> int:
-        return int(lib().sirius_probe_scratch_bytes(ctypes.byref(self.struct)))
+    def probe_scratch_bytes(self, desc: PipelineDesc) -> int:
+        """Scratch of one probe pass of `desc` (its fact rows and aggregation mode) against
+        this index."""
+        return int(lib().sirius_probe_scratch_bytes(ctypes.byref(desc), ctypes.byref(self.struct)))
 
     def join_kind(self) -> str:
         """'direct' when the build took the direct-address array, else 'hash' (reads the
@@ -432,7 +434,7 @@ def sirius_run_probe(desc: PipelineDesc, index: DimIndexBuffer, outputs: Pipelin
                      scratch: Optional[torch.Tensor] = None, stream=None, sync: bool = True):
     r = outputs.result(sync)
     if scratch is None:
-        scratch = _scratch(index.probe_scratch_bytes(), outputs.d_groups.device)
+        scratch = _scratch(index.probe_scratch_bytes(desc), outputs.d_groups.device)
     st = lib().sirius_run_probe(ctypes.byref(desc), ctypes.byref(index.struct), ctypes.byref(r),
                                 _ptr(scratch), scratch.numel(), _stream(stream))
     _check(st, r.groups)

@@ -217,6 +217,52 @@ def test_direct_array_decision(S, case, join_mode):
         check(S, fact, dim, "lt", 55, hint=700, agg_mode=mode, join_mode=join_mode)
 
 
+@pytest.mark.parametrize("n", [1, 5, 4095, 4097, 1_000_003])
+@pytest.mark.parametrize("join_mode", ["auto", "hash"])
+def test_partitioned_aggregation(S, n, join_mode):
+    """100 000 groups (262 145 slots, 65 partitions): tuples per 4096-row tile, then
+    per-partition shared-memory aggregation."""
+    spec = dg.plain_scale(n=n, m=60_000, seed=n % 7)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=100_000, agg_mode="part", join_mode=join_mode)
+
+
+def test_partitioned_duplicates_composite_and_limits(S):
+    rng = np.random.default_rng(41)
+    m = 30_000
+    dim = {"pk": rng.integers(0, 12_000, size=m).astype(np.int32),          # duplicate keys
+           "grp": rng.integers(-500_000, 500_000, size=m).astype(np.int32)}  # ~30 000 groups
+    fact = {"fk": rng.integers(-100, 12_100, size=900_001).astype(np.int32),
+            "pred": rng.integers(0, 100, size=900_001).astype(np.int32),
+            "val": rng.integers(-10**12, 10**12, size=900_001)}
+    for jm in ("auto", "hash"):
+        check(S, fact, dim, "lt", 65, hint=m, agg_mode="part", join_mode=jm)
+    spec = dg.plain_scale(n=800_001, m=40_000, composite=True)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check(S, fact, dim, "lt", spec.t, hint=100_000, agg_mode="part")
+    # a group table at the partition limit (2^20 slots = 256 partitions) and one beyond it
+    # (reductions): both must give the same exact result
+    rng = np.random.default_rng(42)
+    dim = {"pk": rng.permutation(600_000).astype(np.int32),
+           "grp": rng.integers(0, 500_000, size=600_000).astype(np.int32)}
+    fact = {"fk": rng.integers(0, 600_000, size=2_000_003).astype(np.int32),
+            "pred": rng.integers(0, 100, size=2_000_003).astype(np.int32),
+            "val": rng.integers(0, 10**8, size=2_000_003)}
+    check(S, fact, dim, "lt", 50, hint=500_000, agg_mode="part")
+    check(S, fact, dim, "lt", 50, hint=600_000, agg_mode="part")
+
+
+@pytest.mark.parametrize("mode", ["hot", "global", "part"])
+def test_skewed_keys_all_large_table_modes(S, mode):
+    """Zipf(1.1) keys: the hot-group cache, plain reductions and partitioned aggregation give
+    the oracle's exact result."""
+    spec = dg.skewed(n=1_500_001, m=200_000)
+    dim = dg.gen_dim_host(spec)
+    fact = dg.gen_fact_host(spec, dim=dim)
+    check(S, fact, dim, "lt", spec.t, aggs="sum,count", hint=spec.m, agg_mode=mode)
+    check(S, fact, dim, "ge", 80, hint=spec.m, agg_mode=mode)
+
+
 def test_resident_dim_index_serves_many_probes(S):
     spec = dg.StarSpec("t", n=300_001, m=20_000, fk_domain=22_000, grp_bound=500, seed=9)
     dim = dg.gen_dim_host(spec)
