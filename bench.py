@@ -373,6 +373,10 @@ def run_batched(S, torch, args, dev, rank):
     plan = S.BatchPlan(nq)
     scr = torch.empty(S.batch_scratch_bytes(descs), dtype=torch.uint8, device=dev)
     t_batch = ev_time(lambda: plan.run(descs, outs_b, scratch=scr, sync=False), 3)
+    S.profile_start()
+    plan.run(descs, outs_b, scratch=scr, sync=False)
+    torch.cuda.synchronize()
+    batch_phases = {k: v[0] for k, v in S.profile_stop().items()}
     t_graph = ev_time(lambda: plan.run(descs, outs_b, scratch=scr, use_graph=True, sync=False), 5)
     tuned = autotune.tune_batch(plan, descs, outs_b, use_graph=True, use_cache=False,
                                 units=(16_384, 65_536, 262_144), load_factors=(0.35, 0.5, 0.7))
@@ -403,6 +407,7 @@ def run_batched(S, torch, args, dev, rank):
            "batched_graph_rows_per_s": rows / (t_graph / 1e3),
            "autotuned_rows_per_s": rows / (t_tuned / 1e3), "speedup_vs_plain": t_plain / min(t_graph, t_tuned),
            "autotuned": {k: tuned[k] for k in ("rows_per_unit", "load_factor")},
+           "batched_phase_ms": batch_phases,
            "hbm_gbs_effective": fact_bytes / (min(t_graph, t_tuned) / 1e3) / 1e9,
            "results_identical_to_plain": same}
     del tabs
@@ -439,37 +444,48 @@ def run_served(S, torch, args, dev, rank):
 
 def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
     """The same query through sirius_run_pipeline_host: fact and dim columns in pinned host
-    memory; every step copies them to the device inside the call (chunked, overlapped with
-    the probe pass) and copies the result rows back."""
+    memory; every step moves them to the device inside the call and copies the result rows
+    back.  Two ways are timed -- staged copies (chunks, one copy stream per column, overlapped
+    with the probe pass) and in-place reads of the pinned columns by the probe pass -- and the
+    faster one is reported."""
     hf = S.pinned_copy(fact)
     hd = S.pinned_copy(dim)
     desc = S.make_desc(hf, hd, "lt", spec.t, aggs, hint, args.load_factor, args.agg_mode,
                        args.block_threads, args.blocks_per_sm, host=True,
                        probe_variant=args.probe_variant)
     outs = S.HostOutputs(hint + 1)
-    scratch = torch.empty(S.pipeline_host_scratch_bytes(desc, 0, outs.cap), dtype=torch.uint8, device=dev)
-    g = S.sirius_run_pipeline_host(desc, outs, 0, scratch, stream, dev)   # warm-up
-    times = []
-    for _ in range(args.e2e_steps):
+    modes = {}
+    g = 0
+    for name, chunk in (("staged_copies", 0), ("in_place", -1)):
+        scratch = torch.empty(S.pipeline_host_scratch_bytes(desc, chunk, outs.cap), dtype=torch.uint8,
+                              device=dev)
+        g = S.sirius_run_pipeline_host(desc, outs, chunk, scratch, stream, dev)   # warm-up
+        times = []
+        for _ in range(args.e2e_steps):
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            t0 = time.perf_counter()
+            g = S.sirius_run_pipeline_host(desc, outs, chunk, scratch, stream, dev)
+            times.append(time.perf_counter() - t0)
+        t = sum(times) / len(times)
         if world > 1:
             import torch.distributed as dist
-            dist.barrier()
-        t0 = time.perf_counter()
-        g = S.sirius_run_pipeline_host(desc, outs, 0, scratch, stream, dev)
-        times.append(time.perf_counter() - t0)
-    t = max(times) if False else sum(times) / len(times)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+            tt = torch.tensor([t], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        modes[name] = t
+        del scratch
+    best = min(modes, key=modes.get)
+    t = modes[best]
     h2d = sum(v.numel() * v.element_size() for v in hf.values()) + \
         sum(v.numel() * v.element_size() for v in hd.values())
-    ncols = sum(1 for _ in ("key", "sum", "count", "min", "max"))
-    d2h = g * 8 * ncols + 256
+    d2h = g * 8 * 5 + 256
     return {"value": world * spec.n / t, "unit": "rows/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": t * 1e3, "steps": args.e2e_steps,
-            "h2d_gbs": h2d / t / 1e9, "call": "sirius_run_pipeline_host (pinned host columns)"}
+            "h2d_gbs": h2d / t / 1e9, "mode": best,
+            "ms_per_step_by_mode": {k: v * 1e3 for k, v in modes.items()},
+            "call": "sirius_run_pipeline_host (pinned host columns)"}
 
 
 if __name__ == "__main__":

@@ -285,9 +285,11 @@ sirius_status sirius_run_probe(const sirius_pipeline_desc* q, const sirius_dim_i
  * sirius_run_pipeline for columns in host memory (every column pointer of `q` is host memory,
  * pinned for full copy bandwidth; the result arrays are host memory too).  The dim columns are
  * copied and built first; the fact table then streams through the probe pass in chunks of
- * chunk_rows rows (0 = 16 Mi rows): the copy of chunk i+1 runs on a second stream while chunk
- * i is probed (batch execution over host data, Sec. 3.4).  The G result rows are copied back;
- * the call synchronises and fills result->groups / result->status.  Scratch:
+ * chunk_rows rows (0 = 16 Mi rows): each column of chunk i+1 is copied on a stream of its own
+ * while chunk i is probed (batch execution over host data, Sec. 3.4).  chunk_rows < 0: no
+ * staging at all -- the probe pass reads the fact columns in place through the host link
+ * (they must be pinned; INVALID otherwise).  The G result rows are copied back; the call
+ * synchronises and fills result->groups / result->status.  Scratch:
  * sirius_pipeline_host_scratch_bytes(q, chunk_rows, out_cap). */
 size_t sirius_pipeline_host_scratch_bytes(const sirius_pipeline_desc* q, int64_t chunk_rows,
                                           int64_t out_cap);

@@ -677,10 +677,14 @@ HostLayout host_layout(const sirius_pipeline_desc* q, int64_t chunk_rows, int64_
   HostLayout H;
   const bool wide = q->pk_hi != nullptr || q->fk_hi != nullptr;
   H.L = dim_layout(q->m, wide, q->group_cap_hint, q->load_factor, q->join_mode == 0);
-  H.R = run_layout(H.L.gcap, H.chunk, q->agg_mode);
-  H.chunk = chunk_rows > 0 ? chunk_rows : (16ll << 20);
-  if (H.chunk > q->n && q->n > 0) H.chunk = (q->n + 3) / 4 * 4;
-  H.chunk = (H.chunk + 3) / 4 * 4;
+  if (chunk_rows < 0) {
+    H.chunk = 0;  // columns read in place: no staging buffers
+  } else {
+    H.chunk = chunk_rows > 0 ? chunk_rows : (16ll << 20);
+    if (H.chunk > q->n && q->n > 0) H.chunk = (q->n + 3) / 4 * 4;
+    H.chunk = (H.chunk + 3) / 4 * 4;
+  }
+  H.R = run_layout(H.L.gcap, chunk_rows < 0 ? q->n : H.chunk, q->agg_mode);
   H.off_run = H.L.total;
   H.off_dimcols = H.off_run + H.R.total;
   const size_t m = (size_t)q->m;
@@ -708,7 +712,6 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
   if (st != SIRIUS_OK) return st;
   st = validate_result(result);
   if (st != SIRIUS_OK) return st;
-  SIRIUS_REQUIRE(chunk_rows >= 0, "pipeline_host: negative chunk_rows");
   const HostLayout H = host_layout(q, chunk_rows, result->out_cap);
   Scratch sc;
   st = sc.acquire(d_scratch, scratch_bytes, H.total, s);
@@ -745,17 +748,42 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
   if ((st = dim_build(&dq, H.L, base, s)) != SIRIUS_OK) return st;
   if ((st = run_init(H.R, base + H.off_run, s)) != SIRIUS_OK) return st;
 
-  // fact chunks: copies on a second stream, double-buffered against the probe pass
-  cudaStream_t c = nullptr;
-  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-  SIRIUS_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+  // fact chunks: each column copied on a stream of its own (several copy engines at once),
+  // double-buffered against the probe pass; or, with chunk_rows < 0, no staging at all: the
+  // probe pass reads the pinned host columns in place over the host link
+  constexpr int kCols = 4;  // fk, pred, fk_hi, val
+  cudaStream_t c[kCols] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_ready[2][kCols] = {}, ev_free[2] = {nullptr, nullptr};
   sirius_status fail = SIRIUS_OK;
-  for (int b = 0; b < 2 && fail == SIRIUS_OK; ++b) {
-    if (cudaEventCreateWithFlags(&ev_ready[b], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev_free[b], cudaEventDisableTiming) != cudaSuccess)
-      fail = SIRIUS_ERR_CUDA;
+  const bool zero_copy = chunk_rows < 0;
+  if (zero_copy) {
+    const void* cols[kCols] = {q->fk, q->pred, q->fk_hi, q->val};
+    for (int k = 0; k < kCols && fail == SIRIUS_OK; ++k) {
+      if (!cols[k] || q->n == 0) continue;
+      cudaPointerAttributes pa;
+      if (cudaPointerGetAttributes(&pa, cols[k]) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        set_error("pipeline_host: reading columns in place needs pinned (page-locked) host memory");
+        return SIRIUS_ERR_INVALID;
+      }
+    }
+    if (q->m > 0) {
+      sirius_pipeline_desc cq = dq;
+      cq.fk = q->fk;
+      cq.pred = q->pred;
+      cq.fk_hi = q->fk_hi;
+      cq.val = q->val;
+      if ((st = run_probe(&cq, d, r, H.R.gslots, s)) != SIRIUS_OK) fail = st;
+    }
   }
-  const int64_t nchunks = q->m > 0 ? (q->n + H.chunk - 1) / H.chunk : 0;
+  for (int k = 0; k < kCols && fail == SIRIUS_OK && !zero_copy; ++k)
+    if (cudaStreamCreateWithFlags(&c[k], cudaStreamNonBlocking) != cudaSuccess) fail = SIRIUS_ERR_CUDA;
+  for (int b = 0; b < 2 && fail == SIRIUS_OK && !zero_copy; ++b) {
+    if (cudaEventCreateWithFlags(&ev_free[b], cudaEventDisableTiming) != cudaSuccess) fail = SIRIUS_ERR_CUDA;
+    for (int k = 0; k < kCols && fail == SIRIUS_OK; ++k)
+      if (cudaEventCreateWithFlags(&ev_ready[b][k], cudaEventDisableTiming) != cudaSuccess) fail = SIRIUS_ERR_CUDA;
+  }
+  const int64_t nchunks = (q->m > 0 && !zero_copy) ? (q->n + H.chunk - 1) / H.chunk : 0;
   for (int64_t i = 0; i < nchunks && fail == SIRIUS_OK; ++i) {
     const int b = (int)(i & 1);
     const int64_t r0 = i * H.chunk;
@@ -768,15 +796,17 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
     cq.fk_hi = wide ? (const int32_t*)(buf + 2 * a4) : nullptr;
     cq.val = (const int64_t*)(buf + (wide ? 3 : 2) * a4);
     cq.n = rows;
-    if (i >= 2 && cudaStreamWaitEvent(c, ev_free[b], 0) != cudaSuccess) { fail = SIRIUS_ERR_CUDA; break; }
-    if (cudaMemcpyAsync((void*)cq.fk, q->fk + r0, rows * 4, cudaMemcpyHostToDevice, c) != cudaSuccess ||
-        cudaMemcpyAsync((void*)cq.pred, q->pred + r0, rows * 4, cudaMemcpyHostToDevice, c) != cudaSuccess ||
-        (wide && cudaMemcpyAsync((void*)cq.fk_hi, q->fk_hi + r0, rows * 4, cudaMemcpyHostToDevice, c) != cudaSuccess) ||
-        cudaMemcpyAsync((void*)cq.val, q->val + r0, rows * 8, cudaMemcpyHostToDevice, c) != cudaSuccess ||
-        cudaEventRecord(ev_ready[b], c) != cudaSuccess || cudaStreamWaitEvent(s, ev_ready[b], 0) != cudaSuccess) {
-      fail = SIRIUS_ERR_CUDA;
-      break;
+    void* dst[kCols] = {(void*)cq.fk, (void*)cq.pred, (void*)cq.fk_hi, (void*)cq.val};
+    const void* src[kCols] = {q->fk + r0, q->pred + r0, wide ? (const void*)(q->fk_hi + r0) : nullptr, q->val + r0};
+    const size_t bytes[kCols] = {(size_t)rows * 4, (size_t)rows * 4, (size_t)rows * 4, (size_t)rows * 8};
+    for (int k = 0; k < kCols && fail == SIRIUS_OK; ++k) {
+      if (!src[k]) continue;
+      if ((i >= 2 && cudaStreamWaitEvent(c[k], ev_free[b], 0) != cudaSuccess) ||
+          cudaMemcpyAsync(dst[k], src[k], bytes[k], cudaMemcpyHostToDevice, c[k]) != cudaSuccess ||
+          cudaEventRecord(ev_ready[b][k], c[k]) != cudaSuccess || cudaStreamWaitEvent(s, ev_ready[b][k], 0) != cudaSuccess)
+        fail = SIRIUS_ERR_CUDA;
     }
+    if (fail != SIRIUS_OK) break;
     if ((st = run_probe(&cq, d, r, H.R.gslots, s)) != SIRIUS_OK) { fail = st; break; }
     if (cudaEventRecord(ev_free[b], s) != cudaSuccess) { fail = SIRIUS_ERR_CUDA; break; }
   }
@@ -800,11 +830,14 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
       if (fail == SIRIUS_ERR_CUDA) set_error("pipeline_host: result copy failed");
     }
   }
-  cudaStreamSynchronize(c);
+  for (int k = 0; k < kCols; ++k)
+    if (c[k]) cudaStreamSynchronize(c[k]);
   for (int b = 0; b < 2; ++b) {
-    if (ev_ready[b]) cudaEventDestroy(ev_ready[b]);
+    for (int k = 0; k < kCols; ++k)
+      if (ev_ready[b][k]) cudaEventDestroy(ev_ready[b][k]);
     if (ev_free[b]) cudaEventDestroy(ev_free[b]);
   }
-  cudaStreamDestroy(c);
+  for (int k = 0; k < kCols; ++k)
+    if (c[k]) cudaStreamDestroy(c[k]);
   return fail;
 }

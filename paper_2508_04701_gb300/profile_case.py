@@ -23,11 +23,30 @@ def main():
     p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed"])
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
     p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot"])
+    p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
     a = p.parse_args()
     import torch
 
     from paper_2508_04701_gb300 import datagen as dg
     from paper_2508_04701_gb300 import sirius as S
+    if a.batch > 0:
+        specs = [dg.batch_query(q) for q in range(a.batch)]
+        keep, descs = [], []
+        for sp in specs:
+            dim = dg.gen_dim_device(sp)
+            fact = dg.gen_fact_device(sp, dim)
+            keep.append((dim, fact))
+            descs.append(S.make_desc(fact, dim, "lt", sp.t, group_cap_hint=1000))
+        cap = S.lib().sirius_groupby_capacity(1000) + 1
+        outs = [S.PipelineOutputs(cap) for _ in specs]
+        plan = S.BatchPlan(a.batch)
+        scratch = torch.empty(S.batch_scratch_bytes(descs), dtype=torch.uint8, device="cuda")
+        for _ in range(a.runs):
+            g = plan.run(descs, outs, scratch=scratch)
+        torch.cuda.synchronize()
+        print(f"profile case ok: batch of {a.batch} queries, {sum(s.n for s in specs)} fact rows, "
+              f"{sum(g)} groups")
+        return
     if a.workload == "skewed":
         spec, hint = dg.skewed(n=a.n, m=a.m), a.m
     else:

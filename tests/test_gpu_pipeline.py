@@ -282,7 +282,18 @@ def test_resident_dim_index_serves_many_probes(S):
             assert np.array_equal(got[c], want[c]), (seed, c)
 
 
-@pytest.mark.parametrize("chunk", [0, 4096, 10_000, 77_777])
+def test_host_columns_in_place_need_pinned_memory(S):
+    spec = dg.StarSpec("t", n=10_000, m=500, fk_domain=500, grp_bound=30, seed=14)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    hf = {k: torch.from_numpy(v) for k, v in fact.items()}          # pageable
+    hd = {k: torch.from_numpy(v) for k, v in dim.items()}
+    desc = S.make_desc(hf, hd, "lt", spec.t, group_cap_hint=30, host=True)
+    with pytest.raises(S.SiriusError) as e:
+        S.sirius_run_pipeline_host(desc, S.HostOutputs(64), -1)
+    assert e.value.status == S.ERR_INVALID and "pinned" in str(e.value)
+
+
+@pytest.mark.parametrize("chunk", [0, 4096, 10_000, 77_777, -1])
 def test_host_columns_streamed_in_chunks(S, chunk):
     spec = dg.StarSpec("t", n=250_003, m=9000, fk_domain=9500, grp_bound=300, t=45, seed=12)
     dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
