@@ -11,6 +11,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import shlex
 import shutil
 import subprocess
 
@@ -47,7 +48,8 @@ def _newer(target: str, deps) -> bool:
 
 
 def _compile(nvcc: str, src: str, obj: str, verbose: bool):
-    cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    # SIRIUS_NVCC_FLAGS: extra nvcc flags, e.g. -D overrides of the kernels' build-time tunables
+    cmd = [nvcc, *ARCH, *FLAGS, *shlex.split(os.environ.get("SIRIUS_NVCC_FLAGS", "")), "-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

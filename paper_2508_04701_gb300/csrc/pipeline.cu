@@ -8,11 +8,14 @@
 // aggregates straight into slot gs, so no row ids, gathered columns or second hash lookup
 // exist between the operators.  The probe pass streams pred / fk / val with 16-byte
 // evict-first loads (each column byte is read once), probes four rows per thread with their
-// first slot loads in flight together, and aggregates
+// first slot loads in flight together, and aggregates (agg_mode)
 //   - into a per-block copy of the aggregates in shared memory when the group table is small
 //     (few groups contend on chip, not in L2), merged into the global table at block exit;
-//   - with global atomics otherwise (SUM and COUNT as reductions; MIN/MAX only when the value
-//     beats the one already stored).
+//   - through a per-block cache of hot groups in shared memory, the rest with global
+//     reductions, when it is large (the default for large tables);
+//   - with global reductions only (SUM, COUNT, MIN, MAX: four fire-and-forget REDs);
+//   - or partitioned: tuples (slot, value) scattered by slot range per tile, then one
+//     shared-memory pass per partition (csrc/partagg.cuh).
 // Finalize compacts the slots with COUNT > 0 into the caller's output arrays.
 //
 // The build side ("dim index") and the per-query run state live in separate memory, so a dim

@@ -240,15 +240,16 @@ def test_partitioned_duplicates_composite_and_limits(S):
     spec = dg.plain_scale(n=800_001, m=40_000, composite=True)
     dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
     check(S, fact, dim, "lt", spec.t, hint=100_000, agg_mode="part")
-    # a group table at the partition limit (2^20 slots = 256 partitions) and one beyond it
-    # (reductions): both must give the same exact result
+    # the largest group table the partitioned mode takes (hint 250 000: 2^19 + 1 slots, 129
+    # partitions of 4096; 2^20 + 1 slots would be one over 256 x 4096) and one beyond it
+    # (hint 600 000: plain reductions): both must give the same exact result
     rng = np.random.default_rng(42)
     dim = {"pk": rng.permutation(600_000).astype(np.int32),
            "grp": rng.integers(0, 500_000, size=600_000).astype(np.int32)}
     fact = {"fk": rng.integers(0, 600_000, size=2_000_003).astype(np.int32),
             "pred": rng.integers(0, 100, size=2_000_003).astype(np.int32),
             "val": rng.integers(0, 10**8, size=2_000_003)}
-    check(S, fact, dim, "lt", 50, hint=500_000, agg_mode="part")
+    check(S, fact, dim, "lt", 50, hint=250_000, agg_mode="part")
     check(S, fact, dim, "lt", 50, hint=600_000, agg_mode="part")
 
 
