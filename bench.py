@@ -481,10 +481,29 @@ def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
     h2d = sum(v.numel() * v.element_size() for v in hf.values()) + \
         sum(v.numel() * v.element_size() for v in hd.values())
     d2h = g * 8 * 5 + 256
+    # the link's ceiling on this machine: plain copies of the same pinned columns to the device
+    # (one cudaMemcpyAsync per column, back to back on one stream), timed with CUDA events
+    dst = {k: torch.empty_like(v, device=dev) for k, v in list(hf.items()) + [("d_" + k, v) for k, v in hd.items()]}
+    src = dict(list(hf.items()) + [("d_" + k, v) for k, v in hd.items()])
+
+    def copy_all():
+        for k, v in src.items():
+            dst[k].copy_(v, non_blocking=True)
+    copy_all()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        copy_all()
+    e1.record()
+    torch.cuda.synchronize()
+    copy_gbs = h2d / (e0.elapsed_time(e1) / 3 / 1e3) / 1e9
+    del dst
     return {"value": world * spec.n / t, "unit": "rows/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": t * 1e3, "steps": args.e2e_steps,
             "h2d_gbs": h2d / t / 1e9, "mode": best,
             "ms_per_step_by_mode": {k: v * 1e3 for k, v in modes.items()},
+            "link_copy_gbs": copy_gbs, "link_frac": (h2d / t / 1e9) / copy_gbs,
             "call": "sirius_run_pipeline_host (pinned host columns)"}
 
 

@@ -26,6 +26,8 @@ constexpr int kBatchThreads = 256;
 constexpr int kProbeThreads = 256;
 
 enum : uint32_t { kQWide = 1, kQSmem = 2, kQVec = 4, kQBuild = 8 };
+// Bits 0-7 of a plan's class mask: probe classes with work; this bit: some dim builds two-column keys.
+constexpr uint32_t kBuildWideBit = 1u << 8;
 
 struct BatchQuery {
   ProbeArgs a;
@@ -158,6 +160,9 @@ batch_clear_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
   }
 }
 
+// One instantiation per key width (each skips the other width's queries), so that neither
+// carries the registers of both insert paths.
+template <bool kWide>
 __global__ void __launch_bounds__(kBatchThreads)
 batch_build_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
   const int nq = H->nq;
@@ -166,15 +171,14 @@ batch_build_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
     const int64_t local = u - b.u0[1];
     const int64_t r0 = local * kBuildUnit;
     const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
+    if (((b.flags & kQWide) != 0) != kWide) continue;  // block-uniform
     const DimView d = b.d;
-    const bool wide = (b.flags & kQWide) != 0;
-    const bool direct = !wide && direct_applies(d, b.m);
+    const bool direct = !kWide && direct_applies(d, b.m);
     const int32_t kmin = d.dhdr->key_min;
     if (local == 0 && threadIdx.x == 0) d.dhdr->direct = direct ? 1u : 0u;
     bool dup = false;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-      const bool ok = wide ? dim_build_row<true>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup)
-                           : dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup, direct, kmin);
+      const bool ok = dim_build_row<kWide>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup, direct, kmin);
       if (!ok) set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     }
     if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
@@ -307,6 +311,7 @@ struct sirius_batch_plan_s {
   size_t graph_smem = 0;
   uint32_t graph_classes = 0;  // probe classes launched by the captured graph
   int grid_small = 0;
+  int grid_build = 0;          // build-phase kernels: one block per resident slot, no second wave
   int grid_probe[8] = {};
   size_t smem_for_grid = (size_t)-1;
 };
@@ -401,11 +406,15 @@ static sirius_status enqueue_batch(sirius_batch_plan p, size_t smem, uint32_t cl
     SIRIUS_LAUNCH_CHECK();
     batch_clear_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ, 0);
     SIRIUS_LAUNCH_CHECK();
-    batch_build_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    batch_build_kernel<false><<<p->grid_build, kBatchThreads, 0, s>>>(dH, dQ);
     SIRIUS_LAUNCH_CHECK();
+    if (classes & kBuildWideBit) {
+      batch_build_kernel<true><<<p->grid_build, kBatchThreads, 0, s>>>(dH, dQ);
+      SIRIUS_LAUNCH_CHECK();
+    }
     batch_clear_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ, 1);
     SIRIUS_LAUNCH_CHECK();
-    batch_fallback_kernel<<<p->grid_small, kBatchThreads, 0, s>>>(dH, dQ);
+    batch_fallback_kernel<<<p->grid_build, kBatchThreads, 0, s>>>(dH, dQ);
     SIRIUS_LAUNCH_CHECK();
   }
   {
@@ -561,6 +570,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     H->cls_q1[c] = k + 1;
     H->cls_u1[c] = H->total[2];
     if (b.nu[2] > 0) classes |= 1u << c;
+    if ((c & 1) && b.nu[1] > 0) classes |= kBuildWideBit;
   }
   const size_t smem = (size_t)max_smem_slots * sizeof(Agg);
   if (p->smem_for_grid != smem) {
@@ -574,6 +584,9 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
       p->grid_probe[c] = sm_count() * (per > 0 ? per : 1);
     }
     p->grid_small = sm_count() * 8;
+    int per_build = 0;
+    SIRIUS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_build, batch_build_kernel<false>, kBatchThreads, 0));
+    p->grid_build = sm_count() * (per_build > 0 ? per_build : 1);
     p->smem_for_grid = smem;
   }
 

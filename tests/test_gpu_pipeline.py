@@ -245,7 +245,7 @@ def test_partitioned_duplicates_composite_and_limits(S):
     # (hint 600 000: plain reductions): both must give the same exact result
     rng = np.random.default_rng(42)
     dim = {"pk": rng.permutation(600_000).astype(np.int32),
-           "grp": rng.integers(0, 500_000, size=600_000).astype(np.int32)}
+           "grp": rng.integers(0, 200_000, size=600_000).astype(np.int32)}  # ~190 000 groups
     fact = {"fk": rng.integers(0, 600_000, size=2_000_003).astype(np.int32),
             "pred": rng.integers(0, 100, size=2_000_003).astype(np.int32),
             "val": rng.integers(0, 10**8, size=2_000_003)}
