@@ -208,46 +208,61 @@ batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __res
 
 // The probe phase runs one kernel per query class (key width, aggregation mode, vector
 // loads), each specialised at compile time; the host orders the task table by class, so a
-// class's queries -- and their probe units -- are contiguous.
+// class's queries -- and their probe units -- are contiguous.  Each block takes one
+// contiguous range of the class's units, so consecutive units mostly belong to the same
+// query: in shared-memory mode the block keeps that query's aggregates on chip across them
+// and merges them into the global table only when its query changes (and at the end).
 template <bool kWide, int kMode, bool kVec>
 __global__ void __launch_bounds__(kProbeThreads, 3)
 batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int cls) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  Agg* s_tab = reinterpret_cast<Agg*>(smem_raw);
   const int qlo = H->cls_q0[cls], qhi = H->cls_q1[cls];
   const int64_t qpu = H->quads_per_unit;
-  for (int64_t u = H->cls_u0[cls] + blockIdx.x; u < H->cls_u1[cls]; u += gridDim.x) {
-    int lo = qlo, hi = qhi - 1;
+  const int64_t U0 = H->cls_u0[cls], U1 = H->cls_u1[cls];
+  const int64_t per = (U1 - U0 + gridDim.x - 1) / gridDim.x;
+  const int64_t ub = U0 + (int64_t)blockIdx.x * per;
+  const int64_t ue = ub + per < U1 ? ub + per : U1;
+  int held = -1;  // the query whose aggregates the block's shared-memory table holds
+  for (int64_t u = ub; u < ue; ++u) {  // block-uniform
+    int lo = held >= 0 ? held : qlo, hi = qhi - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (Q[mid].u0[2] <= u) lo = mid;
       else hi = mid - 1;
     }
     const BatchQuery& b = Q[lo];
+    if (kMode == kAggSmem && lo != held) {
+      if (held >= 0) {
+        __syncthreads();
+        const ProbeArgs& h = Q[held].a;
+        const SmemAggs Th = smem_aggs(smem_raw, h.gslots);
+        for (uint32_t i = threadIdx.x; i < h.gslots; i += blockDim.x) smem_merge(Th, i, &h.tab[i], h.aggs);
+        __syncthreads();
+      }
+      const SmemAggs Tn = smem_aggs(smem_raw, b.a.gslots);
+      for (uint32_t i = threadIdx.x; i < b.a.gslots; i += blockDim.x) smem_identity(Tn, i);
+      __syncthreads();
+      held = lo;
+    }
     if (b.d.dhdr->status != 0) continue;  // the build failed: nothing to aggregate
     const ProbeArgs a = b.a;
+    const SmemAggs T = kMode == kAggSmem ? smem_aggs(smem_raw, a.gslots) : SmemAggs{};
     const Lookup L = read_lookup(a);
     const int64_t local = u - b.u0[2];
     const int64_t nq4 = a.n >> 2;
     const int64_t q0 = local * qpu;
     const int64_t q1 = q0 + qpu < nq4 ? q0 + qpu : nq4;
-    if (kMode == kAggSmem) {
-      for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) agg_identity(&s_tab[i]);
-      __syncthreads();
-    }
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec>(a, s_tab, L, q);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec>(a, T, L, q);
     if (local == b.nu[2] - 1) {
       const int64_t t0 = nq4 << 2;
-      if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, s_tab, L, t0 + threadIdx.x);
+      if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, T, L, t0 + threadIdx.x);
     }
-    if (kMode == kAggSmem) {
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) {
-        const Agg t = s_tab[i];
-        if (t.count) agg_merge_global(&a.tab[i], t.sum, t.count, t.min, t.max, a.aggs);
-      }
-      __syncthreads();
-    }
+  }
+  if (kMode == kAggSmem && held >= 0) {
+    __syncthreads();
+    const ProbeArgs& h = Q[held].a;
+    const SmemAggs Th = smem_aggs(smem_raw, h.gslots);
+    for (uint32_t i = threadIdx.x; i < h.gslots; i += blockDim.x) smem_merge(Th, i, &h.tab[i], h.aggs);
   }
 }
 
@@ -572,7 +587,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     if (b.nu[2] > 0) classes |= 1u << c;
     if ((c & 1) && b.nu[1] > 0) classes |= kBuildWideBit;
   }
-  const size_t smem = (size_t)max_smem_slots * sizeof(Agg);
+  const size_t smem = smem_aggs_bytes((uint32_t)max_smem_slots, false);
   if (p->smem_for_grid != smem) {
     for (int c = 0; c < 8; ++c) {
       const size_t sm = (c & 2) ? smem : 0;

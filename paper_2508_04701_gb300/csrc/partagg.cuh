@@ -181,7 +181,7 @@ part_scatter_kernel(ProbeArgs a, PartArgs pa) {
   }
   // ragged tail (n % 4 rows): aggregated directly
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-    probe_one<kWide, kAggGlobal>(a, nullptr, L, (nq << 2) + threadIdx.x);
+    probe_one<kWide, kAggGlobal>(a, SmemAggs{}, L, (nq << 2) + threadIdx.x);
 }
 
 // Pass 2: block (k, p) aggregates partition p over tiles [k * per, (k + 1) * per).

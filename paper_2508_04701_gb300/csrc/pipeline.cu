@@ -122,39 +122,29 @@ template <bool kWide, int kMode, bool kVec>
 __global__ void __launch_bounds__(512)
 probe_kernel(ProbeArgs a) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  Agg* s_tab = reinterpret_cast<Agg*>(smem_raw);
   if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
   const Lookup L = read_lookup(a);
-  if (kMode == kAggSmem) {
-    for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) agg_identity(&s_tab[i]);
-    __syncthreads();
-  } else if (kMode == kAggHot) {
-    uint32_t* tags = reinterpret_cast<uint32_t*>(s_tab + kHotEntries);
-    for (int i = threadIdx.x; i < kHotEntries; i += blockDim.x) {
-      agg_identity(&s_tab[i]);
-      tags[i] = kEmpty32;
+  const uint32_t slots = kMode == kAggSmem ? a.gslots : (kMode == kAggHot ? (uint32_t)kHotEntries : 0u);
+  const SmemAggs T = smem_aggs(smem_raw, slots);
+  if (kMode == kAggSmem || kMode == kAggHot) {
+    for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+      smem_identity(T, i);
+      if (kMode == kAggHot) T.tag[i] = kEmpty32;
     }
     __syncthreads();
   }
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
-    probe_quad<kWide, kMode, kVec>(a, s_tab, L, q);
+    probe_quad<kWide, kMode, kVec>(a, T, L, q);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-    probe_one<kWide, kMode>(a, s_tab, L, (nq << 2) + threadIdx.x);
-  if (kMode == kAggSmem) {
+    probe_one<kWide, kMode>(a, T, L, (nq << 2) + threadIdx.x);
+  if (kMode == kAggSmem || kMode == kAggHot) {
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < a.gslots; i += blockDim.x) {
-      const Agg t = s_tab[i];
-      if (t.count) agg_merge_global(&a.tab[i], t.sum, t.count, t.min, t.max, a.aggs);
-    }
-  } else if (kMode == kAggHot) {
-    __syncthreads();
-    const uint32_t* tags = reinterpret_cast<const uint32_t*>(s_tab + kHotEntries);
-    for (int i = threadIdx.x; i < kHotEntries; i += blockDim.x) {
-      const Agg t = s_tab[i];
-      if (tags[i] != kEmpty32 && t.count) agg_merge_global(&a.tab[tags[i]], t.sum, t.count, t.min, t.max, a.aggs);
+    for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+      if (kMode == kAggSmem) smem_merge(T, i, &a.tab[i], a.aggs);
+      else if (T.tag[i] != kEmpty32) smem_merge(T, i, &a.tab[T.tag[i]], a.aggs);
     }
   }
 }
@@ -421,7 +411,7 @@ static sirius_status validate_pair(const sirius_pipeline_desc* q) {
 // Shared-memory table when the group table fits a block; otherwise partitioned aggregation
 // for large inputs whose group table has at most kMaxParts partitions; otherwise reductions.
 int choose_mode(int agg_mode, int64_t gslots, int64_t n) {
-  const bool fits = gslots * (int64_t)sizeof(Agg) <= kSmemAggMaxBytes;
+  const bool fits = (int64_t)smem_aggs_bytes((uint32_t)(gslots < (1 << 30) ? gslots : (1 << 30)), false) <= kSmemAggMaxBytes;
   const bool part_ok = gslots <= (int64_t)part::kMaxParts * part::kPartSlots && n > 0;
   if (agg_mode == kAggSmem && fits) return kAggSmem;
   if (agg_mode == kAggGlobal) return kAggGlobal;
@@ -521,7 +511,7 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
     return d.key_width == 8 ? launch_staged<true>(a, r.phdr, s) : launch_staged<false>(a, r.phdr, s);
   }
   const int threads = q->block_threads > 0 ? q->block_threads : (mode == kAggSmem || mode == kAggHot ? 512 : 256);
-  const size_t smem = mode == kAggSmem ? (size_t)gslots * sizeof(Agg) : 0;  // hot cache: fixed size
+  const size_t smem = mode == kAggSmem ? smem_aggs_bytes((uint32_t)gslots, false) : 0;  // hot cache: fixed size
   PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
   return d.key_width == 8 ? dispatch_probe<true>(a, mode, vec, threads, q->blocks_per_sm, smem, s)
                           : dispatch_probe<false>(a, mode, vec, threads, q->blocks_per_sm, smem, s);

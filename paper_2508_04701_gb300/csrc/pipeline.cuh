@@ -7,7 +7,7 @@
 namespace sirius {
 
 enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2, kAggPart = 3, kAggHot = 4 };
-constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up to 3072 slots
+constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up to 3510 slots
 
 // Build side ("dim index"): [DimHeader | JoinHeader + join slots | group keys[gcap + 1]].
 // It depends on the dim table only, so it can stay resident and serve many probes.
@@ -138,34 +138,69 @@ __device__ __forceinline__ void load_slot(const void* slots, uint32_t s, uint64_
   }
 }
 
-__device__ __forceinline__ void agg_update_smem(Agg* t, int64_t v, uint32_t aggs) {
-  if (aggs & SIRIUS_AGG_SUM) atomicAdd(&t->sum, (unsigned long long)v);
-  atomicAdd(&t->count, 1ull);
-  if ((aggs & SIRIUS_AGG_MIN) && v < t->min) atomicMin(&t->min, (long long)v);
-  if ((aggs & SIRIUS_AGG_MAX) && v > t->max) atomicMax(&t->max, (long long)v);
+// Per-block aggregates in shared memory (the shared-memory and hot-group modes), stored as
+// arrays -- SUM, MIN, MAX (64-bit), COUNT (32-bit) and, for the hot-group cache, a tag per
+// entry -- rather than as 32-byte records: a warp's updates of random slots then spread over
+// the 32 banks, where the record layout puts every record's SUM on the same four banks.
+// COUNT is 32-bit because a block counts at most the rows it processes between two merges,
+// fewer than 2^32 (the library's row-count limit).
+struct SmemAggs {
+  unsigned long long* sum = nullptr;
+  long long* mn = nullptr;
+  long long* mx = nullptr;
+  uint32_t* cnt = nullptr;
+  uint32_t* tag = nullptr;  // hot-group cache only
+};
+__host__ __device__ constexpr size_t smem_aggs_bytes(uint32_t slots, bool tags) {
+  return (size_t)slots * (tags ? 32 : 28);
+}
+__device__ __forceinline__ SmemAggs smem_aggs(unsigned char* base, uint32_t slots) {
+  SmemAggs t;
+  t.sum = reinterpret_cast<unsigned long long*>(base);
+  t.mn = reinterpret_cast<long long*>(base + (size_t)slots * 8);
+  t.mx = reinterpret_cast<long long*>(base + (size_t)slots * 16);
+  t.cnt = reinterpret_cast<uint32_t*>(base + (size_t)slots * 24);
+  t.tag = reinterpret_cast<uint32_t*>(base + (size_t)slots * 28);
+  return t;
+}
+__device__ __forceinline__ void smem_identity(const SmemAggs& t, uint32_t i) {
+  t.sum[i] = 0;
+  t.mn[i] = INT64_MAX;
+  t.mx[i] = INT64_MIN;
+  t.cnt[i] = 0;
+}
+__device__ __forceinline__ void agg_update_smem(const SmemAggs& t, uint32_t i, int64_t v, uint32_t aggs) {
+  if (aggs & SIRIUS_AGG_SUM) atomicAdd(&t.sum[i], (unsigned long long)v);
+  atomicAdd(&t.cnt[i], 1u);
+  if ((aggs & SIRIUS_AGG_MIN) && v < t.mn[i]) atomicMin(&t.mn[i], (long long)v);
+  if ((aggs & SIRIUS_AGG_MAX) && v > t.mx[i]) atomicMax(&t.mx[i], (long long)v);
+}
+// Merge entry i into a global aggregate (nothing when it counted no row).
+__device__ __forceinline__ void smem_merge(const SmemAggs& t, uint32_t i, Agg* dst, uint32_t aggs) {
+  const uint32_t c = t.cnt[i];
+  if (c) agg_merge_global(dst, t.sum[i], c, t.mn[i], t.mx[i], aggs);
 }
 
 // Hot-group cache (kAggHot): kHotEntries direct-mapped entries per block, each claimed once by
-// the first group slot that maps to it (tags[e], kEmpty32 = free).  Under a skewed key
+// the first group slot that maps to it (tag[e], kEmpty32 = free).  Under a skewed key
 // distribution the frequent groups claim entries early and then aggregate on chip; other
-// rows go to the global table.  Layout in dynamic shared memory: Agg[kHotEntries], then tags.
+// rows go to the global table.
 constexpr int kHotBits = 11;
 constexpr int kHotEntries = 1 << kHotBits;
-constexpr size_t kHotSmemBytes = (size_t)kHotEntries * (sizeof(Agg) + 4);
+constexpr size_t kHotSmemBytes = smem_aggs_bytes(kHotEntries, true);
 
 template <int kMode>
-__device__ __forceinline__ void aggregate(const ProbeArgs& a, Agg* s_tab, uint32_t gs, int64_t v) {
+__device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T, uint32_t gs, int64_t v) {
   if (kMode == kAggSmem) {
-    agg_update_smem(&s_tab[gs], v, a.aggs);
+    agg_update_smem(T, gs, v, a.aggs);
   } else if (kMode == kAggHot) {
-    uint32_t* tags = reinterpret_cast<uint32_t*>(s_tab + kHotEntries);
     const uint32_t e = (gs * 2654435761u) >> (32 - kHotBits);
-    uint32_t t = *(volatile uint32_t*)&tags[e];
+    uint32_t t = *(volatile uint32_t*)&T.tag[e];
     if (t == kEmpty32) {
-      t = atomicCAS(&tags[e], kEmpty32, gs);
+      t = atomicCAS(&T.tag[e], kEmpty32, gs);
       if (t == kEmpty32) t = gs;
     }
-    if (t == gs) agg_update_smem(&s_tab[e], v, a.aggs);
+    if (t == gs) agg_update_smem(T, e, v, a.aggs);
     else agg_update_global(&a.tab[gs], v, a.aggs);
   } else {
     agg_update_global(&a.tab[gs], v, a.aggs);
@@ -183,7 +218,7 @@ __device__ __forceinline__ void load_bucket(const void* slots, uint32_t s, uint6
 // selected row is loaded before any row is examined, so four sector misses are in flight
 // together; a walk continues bucket by bucket only past full buckets.
 template <bool kWide, int kMode>
-__device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, const Lookup& L, uint32_t bits,
+__device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, uint32_t bits,
                                            const uint64_t (&key)[4], const int64_t (&v)[4]) {
   if (!kWide && L.direct) {
     // dense keys: one 4-byte read of the direct array per selected row, all four in flight
@@ -195,7 +230,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, const
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (gs[r] != kEmpty32) aggregate<kMode>(a, s_tab, gs[r], v[r]);
+      if (gs[r] != kEmpty32) aggregate<kMode>(a, T, gs[r], v[r]);
     return;
   }
   const bool dups = L.dups;
@@ -223,7 +258,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, const
           if (p == kEmpty32) {
             stop = true;
           } else if (k == key[r]) {
-            aggregate<kMode>(a, s_tab, p, v[r]);
+            aggregate<kMode>(a, T, p, v[r]);
             stop = !dups;
           }
         }
@@ -238,7 +273,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, Agg* s_tab, const
 
 // Filter, probe and aggregate the four rows of quad q (rows 4q .. 4q+3, all < n).
 template <bool kWide, int kMode, bool kVec>
-__device__ __forceinline__ void probe_quad(const ProbeArgs& a, Agg* s_tab, const Lookup& L, int64_t q) {
+__device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t q) {
   const int64_t row0 = q << 2;
   uint32_t bits = 0;
   uint64_t key[4];
@@ -272,18 +307,18 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, Agg* s_tab, const
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-  probe_rows<kWide, kMode>(a, s_tab, L, bits, key, v);
+  probe_rows<kWide, kMode>(a, T, L, bits, key, v);
 }
 
 // Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
 template <bool kWide, int kMode>
-__device__ __forceinline__ void probe_one(const ProbeArgs& a, Agg* s_tab, const Lookup& L, int64_t r) {
+__device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t r) {
   if (!cmp_op(a.pred[r], a.lit, a.op)) return;
   uint64_t key[4] = {0, 0, 0, 0};
   int64_t v[4] = {0, 0, 0, 0};
   key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
   v[0] = a.val[r];
-  probe_rows<kWide, kMode>(a, s_tab, L, 1u, key, v);
+  probe_rows<kWide, kMode>(a, T, L, 1u, key, v);
 }
 
 // Build step of one dim row j: enter its group key into the group table (slot gs), then

@@ -84,9 +84,9 @@ __global__ void __launch_bounds__(kThreads, 1) probe_staged_kernel(ProbeArgs a, 
     // dense keys: the direct array needs no gathered buckets; probe the rows in place
     const int64_t nq = a.n >> 2;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x)
-      probe_quad<kWide, kAggGlobal, true>(a, nullptr, L, q);
+      probe_quad<kWide, kAggGlobal, true>(a, SmemAggs{}, L, q);
     if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-      probe_one<kWide, kAggGlobal>(a, nullptr, L, (nq << 2) + threadIdx.x);
+      probe_one<kWide, kAggGlobal>(a, SmemAggs{}, L, (nq << 2) + threadIdx.x);
     return;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) probe_staged_kernel(ProbeArgs a, 
   }
   cp_async_wait<0>();
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - nfull)
-    probe_one<kWide, kAggGlobal>(a, nullptr, L, nfull + threadIdx.x);
+    probe_one<kWide, kAggGlobal>(a, SmemAggs{}, L, nfull + threadIdx.x);
   if (threadIdx.x == 0 && *timed_out) set_status(run_status, SIRIUS_ERR_TIMEOUT);
 }
 
