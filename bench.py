@@ -4,7 +4,11 @@
 Default workload: the 600M-row fact / 15M-row dim star query (fk uniform over the dim keys,
 pred < 30, group by grp with 100 000 values; SUM, COUNT, MIN, MAX), seeded synthetic data
 generated on the device.  One step = one sirius_run_pipeline call: build over the dim, one
-fused filter/probe/aggregate pass over the fact table, finalize.  Prints one JSON line.
+fused filter/probe/aggregate pass over the fact table, finalize.  Prints one JSON line; besides
+the main line's keys it carries the end-to-end run through host columns (`e2e`), the 512-query
+batch (`batched`), the Poisson-served workload (`served`), the 1M-row query's latency and the
+300M-row Zipf query with its TABLE_FULL retry (`configs`), and the oracle on the host cores
+(`cpu_baseline`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
@@ -51,6 +55,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-served", action="store_true")
+    p.add_argument("--no-configs", action="store_true")
     p.add_argument("--batch-queries", type=int, default=512)
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--serve-seconds", type=float, default=10.0)
@@ -307,6 +312,11 @@ def main():
         served = run_served(S, torch, args, dev, rank)
         torch.cuda.empty_cache()
 
+    configs = None
+    if not args.no_configs:
+        configs = run_configs(S, torch, dev, rank)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, args.cpu_sample_rows)
@@ -323,7 +333,7 @@ def main():
                        "load_factor": args.load_factor or 0.5, "agg_mode": args.agg_mode},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "phase_ms": phase_ms, "device_status": status,
-            "batched": batched, "served": served,
+            "batched": batched, "served": served, "configs": configs,
             "hbm_gbs_effective_step": alg_bytes / (ms_step / 1e3) / 1e9,
         }
         print(json.dumps(line), flush=True)
@@ -440,6 +450,94 @@ def run_served(S, torch, args, dev, rank):
     fst = serve.latency_stats(fifo_reqs)
     return {"rate_qps": args.serve_rate, "seconds": args.serve_seconds, "served": st,
             "plain_fifo": fst, "fifo_seconds": args.fifo_seconds}
+
+
+def run_configs(S, torch, dev, rank):
+    """The metric's two other single-GPU configurations, measured beside the main line.
+    1M-row query: latency per query, median of 100 timed runs after 10 warm-ups, as a plain
+    sirius_run_pipeline call and as a one-query batch plan replayed from its CUDA graph (both
+    must give the same groups).  300M-row Zipf(1.1) query with (grp, flag) group keys: rows/s
+    and G, then the same query with group_cap_hint a quarter of the dim's 10M group keys, which
+    must fail with TABLE_FULL, and its retry with the full hint."""
+    from paper_2508_04701_gb300 import datagen as dg
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def median_us(fn, warm=10, reps=100):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        return statistics.median(ts)
+
+    # ---- 1M-row query
+    spec = dg.plain_small(seed=rank)
+    dim = dg.gen_dim_device(spec, dev)
+    fact = dg.gen_fact_device(spec, dim, dev)
+    desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, 1000)
+    o1, o2 = S.PipelineOutputs(1001, dev), S.PipelineOutputs(1001, dev)
+    scr = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
+    g1 = S.sirius_run_pipeline(desc, o1, scr, stream, sync=True)
+    us_plain = median_us(lambda: S.sirius_run_pipeline(desc, o1, scr, stream, sync=False))
+    plan = S.BatchPlan(1)
+    bscr = torch.empty(S.batch_scratch_bytes([desc]), dtype=torch.uint8, device=dev)
+    g2 = plan.run([desc], [o2], scratch=bscr, use_graph=True, stream=stream)[0]
+    us_graph = median_us(lambda: plan.run([desc], [o2], scratch=bscr, use_graph=True, stream=stream, sync=False))
+    torch.cuda.synchronize()
+    same = g1 == g2
+    if same:
+        a, b = o1.trimmed(g1), o2.trimmed(g2)
+        ia, ib = torch.sort(a["key"]).indices, torch.sort(b["key"]).indices
+        same = all(torch.equal(a[c][ia], b[c][ib]) for c in a)
+    plan.close()
+    out["plain_1M"] = {"rows": spec.n, "groups": g1, "us_per_query_median": us_plain,
+                       "rows_per_s": spec.n / (us_plain / 1e6), "us_per_query_graph_median": us_graph,
+                       "rows_per_s_graph": spec.n / (us_graph / 1e6), "graph_results_identical": bool(same),
+                       "timing": "CUDA events per query, median of 100 after 10 warm-ups"}
+    del fact, dim, desc, scr, bscr, o1, o2
+
+    # ---- 300M-row Zipf query, 10M group keys
+    spec = dg.skewed(seed=rank)
+    dim = dg.gen_dim_device(spec, dev)
+    fact = dg.gen_fact_device(spec, dim, dev)
+    need = spec.m
+    desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, need)
+    o = S.PipelineOutputs(need + 1, dev)
+    scr = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
+    g = S.sirius_run_pipeline(desc, o, scr, stream, sync=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        S.sirius_run_pipeline(desc, o, scr, stream, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    small = need // 4
+    desc_s = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, small)
+    scr_s = torch.empty(S.pipeline_scratch_bytes(desc_s), dtype=torch.uint8, device=dev)
+    o_s = S.PipelineOutputs(small + 1, dev)
+    t0 = time.perf_counter()
+    try:
+        S.sirius_run_pipeline(desc_s, o_s, scr_s, stream, sync=True)
+        first = "OK"
+    except S.SiriusError as e:
+        first = S.STATUS_NAMES.get(e.status, str(e.status))
+    g_retry = S.sirius_run_pipeline(desc, o, scr, stream, sync=True)
+    t_retry = time.perf_counter() - t0
+    out["skewed_300M"] = {"rows": spec.n, "groups": g, "ms_per_query": ms, "rows_per_s": spec.n / (ms / 1e3),
+                          "aggregates": spec.aggs, "group_keys_in_dim": need,
+                          "undersized_hint": {"group_cap_hint": small, "first_status": first, "retries": 1,
+                                              "groups_after_retry": g_retry,
+                                              "ms_failed_run_plus_retry": t_retry * 1e3}}
+    del fact, dim, desc, desc_s, scr, scr_s, o, o_s
+    return out
 
 
 def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
