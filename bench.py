@@ -486,22 +486,42 @@ def run_configs(S, torch, dev, rank):
     scr = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
     g1 = S.sirius_run_pipeline(desc, o1, scr, stream, sync=True)
     us_plain = median_us(lambda: S.sirius_run_pipeline(desc, o1, scr, stream, sync=False))
-    plan = S.BatchPlan(1)
-    bscr = torch.empty(S.batch_scratch_bytes([desc]), dtype=torch.uint8, device=dev)
-    g2 = plan.run([desc], [o2], scratch=bscr, use_graph=True, stream=stream)[0]
-    us_graph = median_us(lambda: plan.run([desc], [o2], scratch=bscr, use_graph=True, stream=stream, sync=False))
+    # the same call captured once into a CUDA graph and replayed
+    scr2 = torch.empty_like(scr)
+    us_graph, graph_error = None, None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        S.sirius_run_pipeline(desc, o2, scr2, cs, sync=False)
+        cs.synchronize()
+        with torch.cuda.graph(graph, stream=cs):
+            S.sirius_run_pipeline(desc, o2, scr2, cs, sync=False)
+        us_graph = median_us(lambda: graph.replay())
+    except Exception as e:  # capture refused: report why instead of a number
+        graph_error = str(e).splitlines()[0][:200]
     torch.cuda.synchronize()
+    g2 = int(o2.d_groups.item())
     same = g1 == g2
     if same:
         a, b = o1.trimmed(g1), o2.trimmed(g2)
         ia, ib = torch.sort(a["key"]).indices, torch.sort(b["key"]).indices
         same = all(torch.equal(a[c][ia], b[c][ib]) for c in a)
+    # a one-query batch plan replaying its own graph; its time includes the plan's host work
+    # per call (task table, copy in, status copy out)
+    plan = S.BatchPlan(1)
+    o3 = S.PipelineOutputs(1001, dev)
+    bscr = torch.empty(S.batch_scratch_bytes([desc]), dtype=torch.uint8, device=dev)
+    plan.run([desc], [o3], scratch=bscr, use_graph=True, stream=stream)
+    us_plan = median_us(lambda: plan.run([desc], [o3], scratch=bscr, use_graph=True, stream=stream, sync=False))
     plan.close()
     out["plain_1M"] = {"rows": spec.n, "groups": g1, "us_per_query_median": us_plain,
                        "rows_per_s": spec.n / (us_plain / 1e6), "us_per_query_graph_median": us_graph,
-                       "rows_per_s_graph": spec.n / (us_graph / 1e6), "graph_results_identical": bool(same),
+                       "rows_per_s_graph": spec.n / (us_graph / 1e6) if us_graph else None,
+                       "graph_error": graph_error, "graph_results_identical": bool(same),
+                       "us_per_query_one_query_plan_median": us_plan,
                        "timing": "CUDA events per query, median of 100 after 10 warm-ups"}
-    del fact, dim, desc, scr, bscr, o1, o2
+    del fact, dim, desc, scr, scr2, bscr, o1, o2, o3
 
     # ---- 300M-row Zipf query, 10M group keys
     spec = dg.skewed(seed=rank)

@@ -59,6 +59,11 @@ __device__ __forceinline__ int64_t group_find_or_insert(int64_t* keys, uint32_t 
   if (key == kEmptyKey) return cap;
   uint32_t s = home_slot64((uint64_t)key, cap);
   for (uint32_t step = 0; step < cap; ++step) {
+    // A walk this long only happens near or past the limit.  Past it the call fails
+    // (TABLE_FULL) and its output is unspecified, so the walk stops: otherwise inserts would
+    // go on claiming slots until none is left and every further new key would walk the whole
+    // table.
+    if ((step & 63) == 63 && ld_relaxed_u64((const uint64_t*)distinct) >= limit) return -1;
     int64_t cur = (int64_t)ld_relaxed_u64((const uint64_t*)&keys[s]);
     if (cur == key) return s;
     if (cur == kEmptyKey) {
@@ -94,9 +99,11 @@ struct __align__(32) Agg {
 };
 
 // Global aggregation: four fire-and-forget reductions (no result is read back, so they
-// compile to RED operations executed at L2).  Reading MIN/MAX first to skip the atomic would
-// put an L2 round trip, ordered behind the reductions just issued to the same line, on every
-// row's critical path.
+// compile to RED operations executed at L2).  Reading the {MIN, MAX} pair first and reducing
+// MIN / MAX only when the value can change them (exact, since a stale extreme is never tighter
+// than the current one) saves a request per row once extremes settle, but measured slower in
+// the fused probe pass: the read is a round trip on the row's path and its registers cost the
+// kernel half its resident warps.
 __device__ __forceinline__ void agg_update_global(Agg* a, int64_t v, uint32_t aggs) {
   if (aggs & SIRIUS_AGG_SUM) atomicAdd(&a->sum, (unsigned long long)v);
   atomicAdd(&a->count, 1ull);
