@@ -141,6 +141,26 @@ def test_group_table_full_then_retry(S):
     check(S, fact, dim, "lt", 50, aggs="sum,count", hint=spec.m)
 
 
+def test_group_table_full_fails_promptly(S):
+    """2M dim rows with 2M distinct group keys against a table sized for a quarter of them:
+    past the limit, further keys must stop walking (a walk over the full 2^20-slot table for
+    each of ~1M keys would take hours)."""
+    import time
+    m = 2_000_000
+    rng = np.random.default_rng(17)
+    dim = {"pk": rng.permutation(m).astype(np.int32), "grp": rng.permutation(m).astype(np.int32)}
+    fact = {"fk": rng.integers(0, m, size=1_000_000).astype(np.int32),
+            "pred": rng.integers(0, 100, size=1_000_000).astype(np.int32),
+            "val": rng.integers(0, 10**8, size=1_000_000)}
+    d, f = dev(dim), dev(fact)
+    t0 = time.perf_counter()
+    with pytest.raises(S.SiriusError) as e:
+        S.run_pipeline(f, d, "lt", 50, "sum,count", group_cap_hint=m // 4)
+    assert e.value.status == S.ERR_TABLE_FULL
+    assert time.perf_counter() - t0 < 30.0
+    check(S, fact, dim, "lt", 50, aggs="sum,count", hint=m)
+
+
 def test_output_capacity(S):
     spec = dg.StarSpec("t", n=100_000, m=1000, fk_domain=1000, grp_bound=200, seed=8)
     dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
