@@ -101,9 +101,10 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-def probe_traffic(workload: str):
-    """Per-launch DRAM bytes of the probe kernel from the committed ncu summary, or None when
-    the kernel source changed since that capture."""
+def probe_record(workload: str):
+    """The committed ncu record of the probe kernel for this workload (DRAM bytes and L2 tag
+    requests per launch, the L2's request peak), or None when the kernel's sources changed
+    since that capture."""
     path = os.path.join(ROOT, "profiles", "pipe_probe_traffic.json")
     try:
         with open(path) as f:
@@ -113,7 +114,7 @@ def probe_traffic(workload: str):
     ent = rec.get(workload)
     if not ent or ent.get("source_hash") != source_hash(PROBE_SOURCES):
         return None
-    return ent.get("bytes_per_launch")
+    return ent
 
 
 class ClockSampler:
@@ -287,12 +288,23 @@ def main():
     alg_bytes = spec.n * spec.fact_bytes_per_row
     achieved = alg_bytes / (probe_avg_ms / 1e3) / 1e9 if probe_avg_ms > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = probe_traffic(args.workload)
+    rec = probe_record(args.workload)
+    traffic = rec.get("bytes_per_launch") if rec else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "pipe_probe_kernel",
                 "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": probe_avg_ms}
+    if rec and rec.get("l2_tag_requests_per_launch") and probe_avg_ms > 0:
+        # the unit that actually bounds this kernel: L2 tag lookups (each joined row's
+        # reductions and direct-array read); requests per launch and the peak rate from the
+        # ncu record, the time live
+        l2_ach = rec["l2_tag_requests_per_launch"] / (probe_avg_ms / 1e3) / 1e9
+        l2_peak = rec["l2_tag_requests_peak_per_s"] / 1e9
+        roofline["l2"] = {"unit": "G tag requests/s", "achieved": l2_ach, "peak": l2_peak,
+                          "frac": l2_ach / l2_peak,
+                          "requests_per_launch": rec["l2_tag_requests_per_launch"],
+                          "source": "ncu lts__t_tag_requests (profiles/pipe_probe_traffic.json)"}
     phase_ms = {k: v[0] / max(v[1], 1) for k, v in phases.items()}
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
