@@ -465,10 +465,11 @@ def run_served(S, torch, args, dev, rank):
 
 
 def run_configs(S, torch, dev, rank):
-    """The metric's two other single-GPU configurations, measured beside the main line.
+    """The metric's other single-GPU configurations, measured beside the main line.
     1M-row query: latency per query, median of 100 timed runs after 10 warm-ups, as a plain
-    sirius_run_pipeline call and as a one-query batch plan replayed from its CUDA graph (both
-    must give the same groups).  300M-row Zipf(1.1) query with (grp, flag) group keys: rows/s
+    sirius_run_pipeline call, as the same call captured once in a CUDA graph and replayed (both
+    must give the same groups), and as a one-query batch plan.  The 600M-row query on two-column join keys (hash-table join):
+    rows/s and phases.  300M-row Zipf(1.1) query with (grp, flag) group keys: rows/s
     and G, then the same query with group_cap_hint a quarter of the dim's 10M group keys, which
     must fail with TABLE_FULL, and its retry with the full hint."""
     from paper_2508_04701_gb300 import datagen as dg
@@ -534,6 +535,29 @@ def run_configs(S, torch, dev, rank):
                        "us_per_query_one_query_plan_median": us_plan,
                        "timing": "CUDA events per query, median of 100 after 10 warm-ups"}
     del fact, dim, desc, scr, scr2, bscr, o1, o2, o3
+
+    # ---- 600M-row query on two-column join keys: the hash-table join at full size
+    spec = dg.plain_scale(composite=True, seed=rank)
+    dim = dg.gen_dim_device(spec, dev)
+    fact = dg.gen_fact_device(spec, dim, dev)
+    desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, 100_000)
+    o = S.PipelineOutputs(100_001, dev)
+    scr = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
+    g = S.sirius_run_pipeline(desc, o, scr, stream, sync=True)
+    S.profile_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        S.sirius_run_pipeline(desc, o, scr, stream, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ph = {k: v[0] / max(v[1], 1) for k, v in S.profile_stop().items()}
+    ms = e0.elapsed_time(e1) / 3
+    out["plain_600M_composite"] = {"rows": spec.n, "groups": g, "ms_per_query": ms,
+                                   "rows_per_s": spec.n / (ms / 1e3), "phase_ms": ph,
+                                   "join": "hash table (two-column keys), 20 B/row of fact columns"}
+    del fact, dim, desc, scr, o
+    torch.cuda.empty_cache()
 
     # ---- 300M-row Zipf query, 10M group keys
     spec = dg.skewed(seed=rank)
