@@ -177,14 +177,21 @@ def groupby_loop(keys, vals) -> Dict[str, np.ndarray]:
 
 # ------------------------------------------------------------------------------- pipeline
 def pipeline(fact: Dict[str, np.ndarray], dim: Dict[str, np.ndarray], op: str = "lt",
-             literal: int = 50, join: str = "sorted") -> Dict[str, np.ndarray]:
+             literal: int = 50, join: str = "sorted", dim_op: Optional[str] = None,
+             dim_literal: int = 0) -> Dict[str, np.ndarray]:
     """One pipeline of the push-based executor (Sec. 3.2.2): filter the fact rows, join the
     survivors to the dim on fk = pk, materialise the value and group key of each joined pair
     by row id (late materialisation), then group-by aggregate.
 
     fact: fk (int32, low word), fk_hi (optional high word), pred int32, val int64.
-    dim:  pk (int32, low word), pk_hi (optional), grp int32, flag (optional int8).
+    dim:  pk (int32, low word), pk_hi (optional), grp int32, flag (optional int8), and dattr
+          (int32) when dim_op is given: the dim-side predicate dattr <dim_op> dim_literal keeps
+          the dim rows that take part in the join (a filter on the build side; moving it there
+          from above the join is the predicate transfer of Sec. 3.4).
     Group key: grp, or (grp, flag) packed by pack_group."""
+    if dim_op is not None:
+        keep = filter_rows(dim["dattr"], dim_op, dim_literal).astype(np.int64)
+        dim = {k: (np.asarray(v)[keep] if v is not None else None) for k, v in dim.items()}
     sel = filter_rows(fact["pred"], op, literal).astype(np.int64)
     fk = join_key(fact, "fk", "fk_hi")[sel]
     pk = join_key(dim, "pk", "pk_hi")

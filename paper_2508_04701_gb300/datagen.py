@@ -39,7 +39,7 @@ BATCH_TABLE0 = 0x100  # query q of a batch: fact 0x100 + 2q, dim 0x101 + 2q
 # fact columns
 C_FK, C_PRED, C_VAL, C_FK_ROW = 0, 1, 2, 3
 # dim columns
-C_PK_TAG, C_GRP, C_FLAG_TAG, C_KEY_SALT = 0, 1, 2, 3
+C_PK_TAG, C_GRP, C_FLAG_TAG, C_KEY_SALT, C_DATTR = 0, 1, 2, 3, 4
 
 
 # ----------------------------------------------------------------------------- scalar streams
@@ -141,6 +141,8 @@ class StarSpec:
     zipf_s: float = 0.0         # > 0: fk = pk[Zipf rank]
     composite: bool = False     # 64-bit join keys as (hi, lo) int32 pairs
     group_flag: bool = False    # group key (grp, flag) = bijection of dim row onto [0, m/2) x {0,1}
+    dim_attr_bound: int = 0     # > 0: dim column dattr uniform in [0, dim_attr_bound)
+    dt: int = 0                 # with dattr: the dim-side predicate dattr < dt
     aggs: str = "sum,count,min,max"
     seed: int = 0
     fact_table: int = FACT
@@ -158,10 +160,13 @@ def plain_small(seed: int = 0) -> StarSpec:
 
 
 def plain_scale(n: int = 600_000_000, m: int = 15_000_000, composite: bool = False,
-                seed: int = 0) -> StarSpec:
-    """600M-row fact, 15M-row dim, grp in [0, 100 000), pred < 30 (30 % selectivity)."""
-    return StarSpec("plain_600M" + ("_composite" if composite else ""), n=n, m=m, fk_domain=m,
-                    grp_bound=100_000, t=30, composite=composite, seed=seed)
+                seed: int = 0, dt: int = 0) -> StarSpec:
+    """600M-row fact, 15M-row dim, grp in [0, 100 000), pred < 30 (30 % selectivity).
+    dt > 0: the dim also has dattr uniform in [0, 100) and the query the dim-side predicate
+    dattr < dt (dt % of the dim rows, and so of the fact rows, take part in the join)."""
+    name = "plain_600M" + ("_composite" if composite else "") + (f"_dim{dt}" if dt else "")
+    return StarSpec(name, n=n, m=m, fk_domain=m, grp_bound=100_000, t=30, composite=composite,
+                    seed=seed, dim_attr_bound=100 if dt else 0, dt=dt)
 
 
 def skewed(n: int = 300_000_000, m: int = 10_000_000, seed: int = 0) -> StarSpec:
@@ -199,6 +204,8 @@ def gen_dim_host(spec: StarSpec) -> Dict[str, np.ndarray]:
         out["flag"] = (v & 1).astype(np.int8)
     else:
         out["grp"] = bounded(stream(s, T, C_GRP, 0, m), spec.grp_bound).astype(np.int32)
+    if spec.dim_attr_bound > 0:
+        out["dattr"] = bounded(stream(s, T, C_DATTR, 0, m), spec.dim_attr_bound).astype(np.int32)
     return out
 
 
@@ -311,6 +318,9 @@ def gen_dim_device(spec: StarSpec, device="cuda"):
     else:
         out["grp"] = _dbounded(stream_base(s, T, C_GRP), 0, m, spec.grp_bound, device,
                                torch.int32)
+    if spec.dim_attr_bound > 0:
+        out["dattr"] = _dbounded(stream_base(s, T, C_DATTR), 0, m, spec.dim_attr_bound, device,
+                                 torch.int32)
     return out
 
 

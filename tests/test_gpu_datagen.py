@@ -18,6 +18,7 @@ def built():
     dg.plain_small(),
     dg.plain_scale(n=300_001, m=70_001),
     dg.plain_scale(n=300_001, m=70_001, composite=True),
+    dg.plain_scale(n=300_001, m=70_001, dt=10),
     dg.skewed(n=200_003, m=50_000),
     dg.batch_query(17),
 ], ids=lambda s: s.name)

@@ -197,6 +197,44 @@ def check_composite_and_group_keys(o, seed):
         assert acc[g] == [int(s), int(c), int(mn), int(mx)], g
 
 
+def check_dim_predicate_brute(o, seed):
+    """The dim-side predicate (predicate transfer): a Python triple loop over tiny tables with
+    duplicate keys, misses and every comparison operator on both sides."""
+    rng = np.random.default_rng(seed)
+    n, m = int(rng.integers(0, 300)), int(rng.integers(0, 60))
+    fact = {"fk": rng.integers(0, 50, size=n).astype(np.int32),
+            "pred": rng.integers(0, 10, size=n).astype(np.int32),
+            "val": rng.integers(-10**6, 10**6, size=n).astype(np.int64)}
+    dim = {"pk": rng.integers(0, 40, size=m).astype(np.int32),
+           "grp": rng.integers(0, 6, size=m).astype(np.int32),
+           "dattr": rng.integers(0, 10, size=m).astype(np.int32)}
+    cmp = {"lt": lambda a, b: a < b, "le": lambda a, b: a <= b, "gt": lambda a, b: a > b,
+           "ge": lambda a, b: a >= b, "eq": lambda a, b: a == b, "ne": lambda a, b: a != b}
+    for dop in O.OPS:
+        op, t, dt = O.OPS[int(rng.integers(0, 6))], int(rng.integers(0, 11)), int(rng.integers(0, 11))
+        acc = {}
+        for i in range(n):
+            if not cmp[op](int(fact["pred"][i]), t):
+                continue
+            for j in range(m):
+                if int(dim["pk"][j]) != int(fact["fk"][i]) or not cmp[dop](int(dim["dattr"][j]), dt):
+                    continue
+                g, v = int(dim["grp"][j]), int(fact["val"][i])
+                a = acc.setdefault(g, [0, 0, v, v])
+                a[0] += v; a[1] += 1; a[2] = min(a[2], v); a[3] = max(a[3], v)
+        r = o.pipeline(fact, dim, op, t, dim_op=dop, dim_literal=dt)
+        assert r["key"].tolist() == sorted(acc), (dop, dt)
+        for k, s_, c, mn, mx in zip(r["key"], r["sum"], r["count"], r["min"], r["max"]):
+            assert acc[int(k)] == [int(s_), int(c), int(mn), int(mx)], (dop, dt, int(k))
+    # a predicate every dim row passes changes nothing; one none passes empties the result
+    whole = o.pipeline(fact, dim, "lt", 5)
+    same = o.pipeline(fact, dim, "lt", 5, dim_op="lt", dim_literal=10)
+    none = o.pipeline(fact, dim, "lt", 5, dim_op="lt", dim_literal=0)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(whole[c], same[c])
+    assert none["key"].size == 0
+
+
 # ----------------------------------------------------------------------------- the pins
 @pytest.mark.parametrize("seed", range(60))
 def test_filter_brute(seed):
@@ -248,6 +286,11 @@ def test_composite_and_group_keys(seed):
     check_composite_and_group_keys(O, seed)
 
 
+@pytest.mark.parametrize("seed", range(40))
+def test_dim_predicate_brute(seed):
+    check_dim_predicate_brute(O, seed)
+
+
 def test_merge_partials_equals_whole():
     rng = np.random.default_rng(3)
     keys = rng.integers(0, 50, size=5000)
@@ -281,7 +324,10 @@ def _mutant(**over):
     for k, v in over.items():
         setattr(m, k, v)
     # pipeline must call the mutant's pieces, so rebuild it over the namespace
-    def pipeline(fact, dim, op="lt", literal=50, join="sorted"):
+    def pipeline(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0):
+        if dim_op is not None:
+            keep = m.filter_rows(dim["dattr"], dim_op, dim_literal).astype(np.int64)
+            dim = {k: v[keep] for k, v in dim.items()}
         sel = m.filter_rows(fact["pred"], op, literal).astype(np.int64)
         fk = O.join_key(fact, "fk", "fk_hi")[sel]
         pk = O.join_key(dim, "pk", "pk_hi")
@@ -332,7 +378,15 @@ def _flag_signed_shift(grp, flag=None):
     return g * 256 + np.asarray(flag, dtype=np.int64)   # sign-extended byte: (g, -1) == (g-1, 255)
 
 
+def _ignores_dim_predicate(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0):
+    return O.pipeline(fact, dim, op, literal, join)
+
+
 MUTANTS = [
+    ("dim predicate ignored", dict(pipeline=_ignores_dim_predicate),
+     lambda m: [check_dim_predicate_brute(m, s) for s in range(10)]),
+    ("filter le for lt (dim predicate)", dict(filter_rows=_le_instead_of_lt),
+     lambda m: [check_dim_predicate_brute(m, s) for s in range(10)]),
     ("filter le for lt", dict(filter_rows=_le_instead_of_lt),
      lambda m: check_filter_closed_form(m)),
     ("filter le for lt (pipeline)", dict(filter_rows=_le_instead_of_lt),
