@@ -228,6 +228,19 @@ typedef struct {
                                of at most 2m values are joined through a direct-address array
                                (decided on the device during the build); 1 hash table always */
   int32_t reserved;
+  /* dim-side predicate (predicate transfer, Sec. 3.4): NULL, or a dim column of m values; only
+     the dim rows with dpred[j] <dop> dliteral take part in the join (a filter on the build
+     side, so the probe pass finds no partner for the other rows' keys) */
+  const int32_t* dpred;
+  int32_t dop;              /* sirius_cmp */
+  int32_t dliteral;
+  int32_t bloom;            /* Bloom pre-filter of the probe keys: 0 auto (on when dpred is set),
+                               1 off, 2 on.  Built from the keys of the dim rows that take part
+                               (16 bits per dim row, three bits in one 64-bit word per key) and
+                               tested before each hash-table probe, so most probes of absent keys
+                               skip their random bucket read; the direct-address join, itself an
+                               exact filter, does not use it */
+  int32_t reserved2;
 } sirius_pipeline_desc;
 
 typedef struct {
@@ -255,9 +268,9 @@ sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, sirius_result* 
  * The build phase of sirius_run_pipeline as a call of its own, so that a dim table's join and
  * group tables stay resident in device memory and serve many probe passes (the pre-allocated
  * data caching region, Sec. 3.2.3).  The dim index depends only on the dim fields of `q`
- * (pk, pk_hi, grp, flag, m, group_cap_hint, load_factor).  d_mem: caller device memory of
+ * (pk, pk_hi, grp, flag, m, dpred / dop / dliteral, bloom, group_cap_hint, load_factor, join_mode).  d_mem: caller device memory of
  * sirius_dim_index_bytes(q) bytes, 256-byte aligned, passed in `bytes`.  The build fills
- * join_capacity, group_capacity and key_width.  h_status (nullable) synchronises and receives
+ * join_capacity, group_capacity, direct_capacity, key_width and bloom_log2.  h_status (nullable) synchronises and receives
  * the device status (TABLE_FULL: more distinct group keys than the hint allows). */
 typedef struct {
   void* d_mem;
@@ -266,7 +279,7 @@ typedef struct {
   int64_t group_capacity;
   int64_t direct_capacity;   /* entries of the direct-address array (0: hash table only) */
   int32_t key_width;
-  int32_t reserved;
+  int32_t bloom_log2;        /* log2 of the Bloom filter's 64-bit words (0: no filter) */
 } sirius_dim_index;
 
 size_t sirius_dim_index_bytes(const sirius_pipeline_desc* q);

@@ -38,6 +38,7 @@ struct BatchQuery {
   const int32_t* pk_hi;
   const int32_t* grp;
   const int8_t* flag;
+  DimPred dpred;   // dim-side predicate of the build
   int64_t m;
   int64_t jpairs;  // 16-byte words of join slots (0 when the dim index is prebuilt)
   int64_t dpairs;  // 16-byte words of the direct array (0 when prebuilt or hash only)
@@ -178,7 +179,7 @@ batch_build_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
     if (local == 0 && threadIdx.x == 0) d.dhdr->direct = direct ? 1u : 0u;
     bool dup = false;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-      const bool ok = dim_build_row<kWide>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup, direct, kmin);
+      const bool ok = dim_build_row<kWide>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup, b.dpred, direct, kmin);
       if (!ok) set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     }
     if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
@@ -200,7 +201,7 @@ batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __res
     const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
     bool dup = false;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x)
-      if (!dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup))
+      if (!dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup, b.dpred))
         set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
   }
@@ -307,6 +308,12 @@ __global__ void batch_publish_kernel(const BatchHeader* __restrict__ H, const Ba
 }
 
 DimLayout layout_of_index(const sirius_dim_index* idx) { return dim_layout_of_index(idx); }
+// A batch builds its dims without a Bloom filter: its dims are small enough (a join table in L2)
+// that a filter would not save DRAM reads.  Prebuilt dim indexes keep theirs.
+DimLayout batch_dim_layout(const sirius_pipeline_desc* q) {
+  return dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint, q->load_factor,
+                    q->join_mode == 0, false);
+}
 
 bool prebuilt(const sirius_dim_index* indexes, int i) { return indexes && indexes[i].d_mem; }
 
@@ -363,7 +370,7 @@ extern "C" size_t sirius_pipeline_batch_scratch_bytes(const sirius_pipeline_desc
     if (prebuilt(indexes, i)) {
       gcap = indexes[i].group_capacity;
     } else {
-      const DimLayout L = dim_layout_for(q);
+      const DimLayout L = batch_dim_layout(q);
       off += L.total;
       gcap = L.gcap;
     }
@@ -499,7 +506,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
   for (int i = 0; i < nq; ++i) {
     const sirius_pipeline_desc* q = &qs[i];
     const bool pre = prebuilt(indexes, i);
-    const int64_t gcap = pre ? indexes[i].group_capacity : dim_layout_for(q).gcap;
+    const int64_t gcap = pre ? indexes[i].group_capacity : batch_dim_layout(q).gcap;
     const bool wide = pre ? indexes[i].key_width == 8 : (q->pk_hi != nullptr || q->fk_hi != nullptr);
     const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
                      (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
@@ -526,7 +533,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
       L = layout_of_index(&indexes[i]);
       dbase = (char*)indexes[i].d_mem;
     } else {
-      L = dim_layout_for(q);
+      L = batch_dim_layout(q);
       dbase = sc.base + off;
       off += L.total;
     }
@@ -551,12 +558,15 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     b.a.jhdr = b.d.jhdr;
     b.a.dhdr = b.d.dhdr;
     b.a.dslot = b.d.dslot;
+    b.a.bloom = b.d.bloom;
+    b.a.bloom_mask = b.d.bloom_mask;
     b.a.tab = r.aggs;
     b.a.gslots = (uint32_t)R.gslots;
     b.pk = q->pk;
     b.pk_hi = q->pk_hi;
     b.grp = q->grp;
     b.flag = q->flag;
+    b.dpred = DimPred{pre ? nullptr : q->dpred, q->dop, q->dliteral};
     b.m = pre ? 0 : q->m;
     b.gslots = R.gslots;
     b.jpairs = pre ? 0 : (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16;

@@ -31,10 +31,12 @@ namespace sirius {
 namespace {
 
 // Clears the dim index: headers (key range to its empty value), join slots (kEmpty), direct
-// array (kEmpty32, as 16-byte words) and group keys.  The join slots are only cleared when
-// the hash table may be needed (`jpairs` is 0 when the direct array is certain to be used).
+// array (kEmpty32, as 16-byte words), group keys and the Bloom filter's words.  The join slots
+// are only cleared when the hash table may be needed (`jpairs` is 0 when the direct array is
+// certain to be used).
 __global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* jwords2, int64_t jpairs,
-                                ulonglong2* dwords2, int64_t dpairs, int64_t* gkeys, int64_t gslots) {
+                                ulonglong2* dwords2, int64_t dpairs, int64_t* gkeys, int64_t gslots,
+                                uint64_t* bloom, int64_t bwords) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (tid < 32) {
@@ -46,6 +48,7 @@ __global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* j
   for (int64_t i = tid; i < jpairs; i += stride) jwords2[i] = ones;
   for (int64_t i = tid; i < dpairs; i += stride) dwords2[i] = ones;
   for (int64_t i = tid; i < gslots; i += stride) gkeys[i] = kEmptyKey;
+  for (int64_t i = tid; i < bwords; i += stride) bloom[i] = 0;
 }
 
 // Range of the one-column build keys (for the direct-array decision).
@@ -69,14 +72,17 @@ __global__ void dim_minmax_kernel(const int32_t* __restrict__ pk, int64_t m, Dim
 template <bool kWide>
 __global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
                                  const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
-                                 int64_t m, DimView d, unsigned long long glimit) {
+                                 int64_t m, DimView d, unsigned long long glimit, DimPred P) {
   const bool direct = !kWide && direct_applies(d, m);
   const int32_t kmin = d.dhdr->key_min;
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.dhdr->direct = direct ? 1u : 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.dhdr->direct = direct ? 1u : 0u;
+    if (!direct && d.bloom) d.dhdr->bloom = 1;
+  }
   bool dup = false;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
        j += (int64_t)gridDim.x * blockDim.x) {
-    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup, direct, kmin))
+    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup, P, direct, kmin))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
@@ -101,12 +107,13 @@ __global__ void dim_clear_join_kernel(DimView d, int64_t m, int phase, int64_t j
 // (the group keys are already in their table; finding them again returns the same slots).
 __global__ void dim_fallback_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
                                     const int8_t* __restrict__ flag, int64_t m, DimView d,
-                                    unsigned long long glimit) {
+                                    unsigned long long glimit, DimPred P) {
   if (!(d.dhdr->direct && d.dhdr->direct_failed)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && d.bloom) d.dhdr->bloom = 1;
   bool dup = false;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
        j += (int64_t)gridDim.x * blockDim.x) {
-    if (!dim_build_row<false>(pk, nullptr, grp, flag, j, d, glimit, dup))
+    if (!dim_build_row<false>(pk, nullptr, grp, flag, j, d, glimit, dup, P))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
@@ -292,7 +299,7 @@ sirius_status dispatch_probe(const ProbeArgs& a, int mode, bool vec, int threads
 }  // namespace
 
 // ------------------------------------------------------------------ layouts and validation
-DimLayout dim_layout(int64_t m, bool wide, int64_t hint, float lf, bool allow_direct) {
+DimLayout dim_layout(int64_t m, bool wide, int64_t hint, float lf, bool allow_direct, bool bloom) {
   DimLayout L;
   L.key_width = wide ? 8 : 4;
   L.jcap = sirius_join_table_capacity(m, lf > 0 ? lf : 0.5);
@@ -302,13 +309,25 @@ DimLayout dim_layout(int64_t m, bool wide, int64_t hint, float lf, bool allow_di
   L.off_join = 256;
   L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (wide ? 16 : 8), 256);
   L.off_direct = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
-  L.total = align_up(L.off_direct + (size_t)L.dcap * 4, 256);
+  L.off_bloom = align_up(L.off_direct + (size_t)L.dcap * 4, 256);
+  // Bloom filter: 16 bits per dim row (a 64-bit word per four rows), at least 64 words
+  if (bloom && m > 0) {
+    L.bloom_log2 = 6;
+    while ((1ll << L.bloom_log2) < (m + 3) / 4) ++L.bloom_log2;
+  }
+  L.total = align_up(L.off_bloom + (L.bloom_log2 > 0 ? (size_t)8 << L.bloom_log2 : 0), 256);
   return L;
+}
+
+// The Bloom filter is built when asked for (bloom = 2), or by default when a dim-side
+// predicate leaves dim rows out of the join, so that probe keys often find no partner.
+static bool bloom_wanted(const sirius_pipeline_desc* q) {
+  return q->bloom == 2 || (q->bloom == 0 && q->dpred != nullptr);
 }
 
 DimLayout dim_layout_for(const sirius_pipeline_desc* q) {
   return dim_layout(q->m, q->pk_hi != nullptr || q->fk_hi != nullptr, q->group_cap_hint, q->load_factor,
-                    q->join_mode == 0);
+                    q->join_mode == 0, bloom_wanted(q));
 }
 
 // The layout of a built dim index, from the capacities its build recorded.
@@ -321,7 +340,9 @@ DimLayout dim_layout_of_index(const sirius_dim_index* idx) {
   L.off_join = 256;
   L.off_gkeys = align_up(L.off_join + 256 + (size_t)L.jcap * (L.key_width == 8 ? 16 : 8), 256);
   L.off_direct = align_up(L.off_gkeys + (size_t)(L.gcap + 1) * 8, 256);
-  L.total = align_up(L.off_direct + (size_t)L.dcap * 4, 256);
+  L.off_bloom = align_up(L.off_direct + (size_t)L.dcap * 4, 256);
+  L.bloom_log2 = idx->bloom_log2;
+  L.total = align_up(L.off_bloom + (L.bloom_log2 > 0 ? (size_t)8 << L.bloom_log2 : 0), 256);
   return L;
 }
 
@@ -351,6 +372,8 @@ DimView dim_view(const DimLayout& L, char* base) {
   d.jslots = base + L.off_join + 256;
   d.gkeys = (int64_t*)(base + L.off_gkeys);
   d.dslot = (uint32_t*)(base + L.off_direct);
+  d.bloom = L.bloom_log2 > 0 ? (uint64_t*)(base + L.off_bloom) : nullptr;
+  d.bloom_mask = L.bloom_log2 > 0 ? (uint32_t)((1ull << L.bloom_log2) - 1) : 0u;
   d.jcap = (uint32_t)L.jcap;
   d.gcap = (uint32_t)L.gcap;
   d.dcap = L.dcap;
@@ -379,6 +402,8 @@ sirius_status validate_dim(const sirius_pipeline_desc* q) {
   const int64_t hint = q->group_cap_hint > 0 ? q->group_cap_hint : q->m;
   SIRIUS_REQUIRE(hint < (1ll << 30), "pipeline: group_cap_hint too large");
   SIRIUS_REQUIRE(q->join_mode == 0 || q->join_mode == 1, "pipeline: bad join_mode %d", q->join_mode);
+  SIRIUS_REQUIRE(!q->dpred || (q->dop >= 0 && q->dop <= 5), "pipeline: bad dim comparison %d", q->dop);
+  SIRIUS_REQUIRE(q->bloom >= 0 && q->bloom <= 2, "pipeline: bad bloom %d", q->bloom);
   return SIRIUS_OK;
 }
 
@@ -436,16 +461,20 @@ sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char*
     const int64_t init_jpairs = lazy_join ? 0 : jpairs;
     int64_t work = init_jpairs > gslots ? init_jpairs : gslots;
     work = dpairs > work ? dpairs : work;
+    const int64_t bwords = L.bloom_log2 > 0 ? (1ll << L.bloom_log2) : 0;
+    work = bwords > work ? bwords : work;
     dim_init_kernel<<<grid_for(work, 256), 256, 0, s>>>(d.dhdr, d.jhdr, (ulonglong2*)d.jslots, init_jpairs,
-                                                       (ulonglong2*)d.dslot, dpairs, d.gkeys, gslots);
+                                                       (ulonglong2*)d.dslot, dpairs, d.gkeys, gslots, d.bloom,
+                                                       bwords);
     SIRIUS_LAUNCH_CHECK();
   }
   if (q->m > 0) {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_BUILD);
     const int g = grid_for(q->m, 256);
     const unsigned long long lim = group_limit_for(L.gcap);
+    const DimPred P{q->dpred, q->dop, q->dliteral};
     if (L.key_width == 8) {
-      dim_build_kernel<true><<<g, 256, 0, s>>>(q->pk, q->pk_hi, q->grp, q->flag, q->m, d, lim);
+      dim_build_kernel<true><<<g, 256, 0, s>>>(q->pk, q->pk_hi, q->grp, q->flag, q->m, d, lim, P);
       SIRIUS_LAUNCH_CHECK();
     } else {
       if (L.dcap > 0) {
@@ -456,14 +485,14 @@ sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char*
           SIRIUS_LAUNCH_CHECK();
         }
       }
-      dim_build_kernel<false><<<g, 256, 0, s>>>(q->pk, nullptr, q->grp, q->flag, q->m, d, lim);
+      dim_build_kernel<false><<<g, 256, 0, s>>>(q->pk, nullptr, q->grp, q->flag, q->m, d, lim, P);
       SIRIUS_LAUNCH_CHECK();
       if (L.dcap > 0) {
         if (lazy_join) {
           dim_clear_join_kernel<<<grid_for(jpairs, 256), 256, 0, s>>>(d, q->m, 1, jpairs);
           SIRIUS_LAUNCH_CHECK();
         }
-        dim_fallback_kernel<<<g, 256, 0, s>>>(q->pk, q->grp, q->flag, q->m, d, lim);
+        dim_fallback_kernel<<<g, 256, 0, s>>>(q->pk, q->grp, q->flag, q->m, d, lim, P);
         SIRIUS_LAUNCH_CHECK();
       }
     }
@@ -496,6 +525,8 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   a.jhdr = d.jhdr;
   a.dhdr = d.dhdr;
   a.dslot = d.dslot;
+  a.bloom = d.bloom;
+  a.bloom_mask = d.bloom_mask;
   a.tab = r.aggs;
   a.gslots = (uint32_t)gslots;
   const int mode = r.mode;
@@ -610,6 +641,7 @@ extern "C" sirius_status sirius_dim_index_build(const sirius_pipeline_desc* q, s
   idx->group_capacity = L.gcap;
   idx->direct_capacity = L.dcap;
   idx->key_width = L.key_width;
+  idx->bloom_log2 = L.bloom_log2;
   if ((st = dim_build(q, L, (char*)idx->d_mem, s)) != SIRIUS_OK) return st;
   if (h_status) {
     DimHeader h;
@@ -669,7 +701,7 @@ struct HostLayout {
 HostLayout host_layout(const sirius_pipeline_desc* q, int64_t chunk_rows, int64_t out_cap) {
   HostLayout H;
   const bool wide = q->pk_hi != nullptr || q->fk_hi != nullptr;
-  H.L = dim_layout(q->m, wide, q->group_cap_hint, q->load_factor, q->join_mode == 0);
+  H.L = dim_layout_for(q);
   if (chunk_rows < 0) {
     H.chunk = 0;  // columns read in place: no staging buffers
   } else {
@@ -681,7 +713,8 @@ HostLayout host_layout(const sirius_pipeline_desc* q, int64_t chunk_rows, int64_
   H.off_run = H.L.total;
   H.off_dimcols = H.off_run + H.R.total;
   const size_t m = (size_t)q->m;
-  const size_t dimcols = align_up(m * 4, 256) * (wide ? 3 : 2) + align_up(q->flag ? m : 0, 256);
+  const size_t dimcols =
+      align_up(m * 4, 256) * ((wide ? 3 : 2) + (q->dpred ? 1 : 0)) + align_up(q->flag ? m : 0, 256);
   H.off_chunks = H.off_dimcols + dimcols;
   H.chunk_bytes = align_up((size_t)H.chunk * 4, 256) * (wide ? 3 : 2) + align_up((size_t)H.chunk * 8, 256);
   H.off_out = H.off_chunks + 2 * H.chunk_bytes;
@@ -727,14 +760,17 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
     void* d_pk_hi = nullptr;
     void* d_grp = nullptr;
     void* d_flag = nullptr;
+    void* d_dpred = nullptr;
     SIRIUS_CUDA_TRY(put(q->pk, m * 4, &d_pk));
     if (wide) SIRIUS_CUDA_TRY(put(q->pk_hi, m * 4, &d_pk_hi));
     SIRIUS_CUDA_TRY(put(q->grp, m * 4, &d_grp));
     if (q->flag) SIRIUS_CUDA_TRY(put(q->flag, m, &d_flag));
+    if (q->dpred) SIRIUS_CUDA_TRY(put(q->dpred, m * 4, &d_dpred));
     dq.pk = (const int32_t*)d_pk;
     dq.pk_hi = (const int32_t*)d_pk_hi;
     dq.grp = (const int32_t*)d_grp;
     dq.flag = (const int8_t*)d_flag;
+    dq.dpred = (const int32_t*)d_dpred;
   }
   const DimView d = dim_view(H.L, base);
   const RunView r = run_view(H.R, base + H.off_run);

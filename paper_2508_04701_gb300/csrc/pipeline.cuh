@@ -17,7 +17,7 @@ struct DimHeader {
   unsigned long long distinct;   // group slots claimed
   int32_t key_min, key_max;      // range of the one-column build keys
   uint32_t direct_failed;        // a duplicate key turned the direct array down: hash table used
-  uint32_t pad1;
+  uint32_t bloom;                // 1: the hash table is in use and the Bloom filter holds its keys
   unsigned long long pad[28];
 };
 static_assert(sizeof(DimHeader) == 256, "dim header is 256 bytes");
@@ -39,8 +39,9 @@ static_assert(sizeof(PipeHeader) == 256, "pipeline header is 256 bytes");
 struct DimLayout {
   int key_width = 4;
   int64_t jcap = 0, gcap = 0;
-  int64_t dcap = 0;  // direct-array entries (0: hash table only)
-  size_t off_join = 256, off_gkeys = 0, off_direct = 0, total = 0;
+  int64_t dcap = 0;    // direct-array entries (0: hash table only)
+  int bloom_log2 = 0;  // Bloom filter of 2^bloom_log2 64-bit words after the direct array (0: none)
+  size_t off_join = 256, off_gkeys = 0, off_direct = 0, off_bloom = 0, total = 0;
 };
 
 // Run state: [PipeHeader | Agg[gslots] | (partitioned mode) tuple slots, tuple values, prefixes].
@@ -58,6 +59,8 @@ struct DimView {
   void* jslots;
   int64_t* gkeys;
   uint32_t* dslot;
+  uint64_t* bloom;      // nullptr: no Bloom filter
+  uint32_t bloom_mask;  // words - 1
   uint32_t jcap;
   uint32_t gcap;
   int64_t dcap;
@@ -103,12 +106,15 @@ struct ProbeArgs {
   const uint32_t* dslot;
   Agg* tab;
   uint32_t gslots;
+  const uint64_t* bloom;  // nullptr: no Bloom filter
+  uint32_t bloom_mask;
 };
 
 // How the probe pass finds a key's group slot, read once from the dim header.
 struct Lookup {
   bool direct;     // direct array in use
   bool dups;       // hash table holds duplicate keys (walks go past the first match)
+  bool bloom;      // hash table in use and a Bloom filter of its keys to test first
   int32_t kmin;
   uint32_t range;  // key_max - key_min + 1 (direct mode)
 };
@@ -117,6 +123,7 @@ __device__ __forceinline__ Lookup read_lookup(const ProbeArgs& a) {
   Lookup L;
   L.direct = a.dhdr->direct != 0 && a.dhdr->direct_failed == 0;
   L.dups = a.jhdr->has_dups != 0;
+  L.bloom = a.bloom != nullptr && !L.direct && a.dhdr->bloom != 0;
   L.kmin = a.dhdr->key_min;
   L.range = (uint32_t)((int64_t)a.dhdr->key_max - (int64_t)a.dhdr->key_min + 1);
   return L;
@@ -233,6 +240,13 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
       if (gs[r] != kEmpty32) aggregate<kMode>(a, T, gs[r], v[r]);
     return;
   }
+  if (L.bloom) {
+    // keys the filter rules out skip their bucket read (all four tests in flight together)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (((bits >> r) & 1u) && !bloom_test(a.bloom, a.bloom_mask, key[r])) bits &= ~(1u << r);
+    if (!bits) return;
+  }
   const bool dups = L.dups;
   constexpr int kPer = kWide ? 2 : 4;  // slots per bucket
   uint32_t s[4];
@@ -321,25 +335,38 @@ __device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T,
   probe_rows<kWide, kMode>(a, T, L, 1u, key, v);
 }
 
-// Build step of one dim row j: enter its group key into the group table (slot gs), then
-// (pk -> gs) into the join table.  Returns false on TABLE_FULL.
+// The dim-side predicate of a build (col == nullptr: every dim row takes part).
+struct DimPred {
+  const int32_t* col;
+  int32_t op;
+  int32_t lit;
+};
+
+// Build step of one dim row j: unless the dim-side predicate leaves it out, enter its group
+// key into the group table (slot gs), then (pk -> gs) into the join table -- and the key into
+// the Bloom filter when there is one.  Returns false on TABLE_FULL.
 // In direct mode the row claims dslot[key - kmin] with one CAS; finding it taken means a
 // duplicate key (dup = true), which turns the direct array down for this dim.
 template <bool kWide>
 __device__ __forceinline__ bool dim_build_row(const int32_t* pk, const int32_t* pk_hi, const int32_t* grp,
                                               const int8_t* flag, int64_t j, const DimView& d,
-                                              unsigned long long glimit, bool& dup, bool direct = false,
-                                              int32_t kmin = 0) {
+                                              unsigned long long glimit, bool& dup, const DimPred& P,
+                                              bool direct = false, int32_t kmin = 0) {
+  if (P.col && !cmp_op(P.col[j], P.lit, P.op)) return true;
   const int64_t gk = group_key(grp[j], flag, j);
   const int64_t gs = group_find_or_insert(d.gkeys, d.gcap, gk, &d.dhdr->distinct, glimit);
   if (gs < 0) return false;
-  if (kWide)
-    return join_insert64((ulonglong2*)d.jslots, d.jcap, pack_key64(pk_hi[j], pk[j]), (uint32_t)gs, dup);
+  if (kWide) {
+    const uint64_t key = pack_key64(pk_hi[j], pk[j]);
+    if (d.bloom) bloom_insert(d.bloom, d.bloom_mask, key);
+    return join_insert64((ulonglong2*)d.jslots, d.jcap, key, (uint32_t)gs, dup);
+  }
   const uint32_t key = (uint32_t)pk[j];
   if (direct) {
     if (atomicCAS(&d.dslot[key - (uint32_t)kmin], kEmpty32, (uint32_t)gs) != kEmpty32) dup = true;
     return true;
   }
+  if (d.bloom) bloom_insert(d.bloom, d.bloom_mask, (uint64_t)key);
   return join_insert32((uint64_t*)d.jslots, d.jcap, key, (uint64_t)key | ((uint64_t)(uint32_t)gs << 32), dup);
 }
 
@@ -351,7 +378,8 @@ __device__ __forceinline__ bool direct_applies(const DimView& d, int64_t m) {
 }
 
 // ------------------------------------------------------------------ host phases
-DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor, bool allow_direct);
+DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor, bool allow_direct,
+                     bool bloom = false);
 DimLayout dim_layout_for(const sirius_pipeline_desc* q);
 DimLayout dim_layout_of_index(const sirius_dim_index* idx);
 // n: fact rows of the run (sizes the partitioned-mode buffers); agg_mode as in the descriptor.

@@ -80,6 +80,29 @@ __device__ __forceinline__ int64_t group_find_or_insert(int64_t* keys, uint32_t 
   return -1;
 }
 
+// Blocked Bloom filter over join keys: one 64-bit word per key (index from the high half of a
+// 64-bit hash, masked to the power-of-two word count) with three bits set in it (from the low
+// bits of the same hash), so a test is one 8-byte read and an insert one atomic OR.  No false
+// negatives: every inserted key tests true.
+__device__ __forceinline__ void bloom_word(uint64_t key, uint32_t mask, uint32_t& w, uint64_t& bits) {
+  const uint64_t h = fmix64(key ^ 0x9E3779B97F4A7C15ull);
+  w = (uint32_t)(h >> 32) & mask;
+  bits = (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)) | (1ull << ((h >> 12) & 63));
+}
+__device__ __forceinline__ void bloom_insert(uint64_t* f, uint32_t mask, uint64_t key) {
+  uint32_t w;
+  uint64_t bits;
+  bloom_word(key, mask, w, bits);
+  atomicOr(reinterpret_cast<unsigned long long*>(&f[w]), (unsigned long long)bits);
+}
+// Read-only during the probe pass: through the non-coherent path.
+__device__ __forceinline__ bool bloom_test(const uint64_t* f, uint32_t mask, uint64_t key) {
+  uint32_t w;
+  uint64_t bits;
+  bloom_word(key, mask, w, bits);
+  return (__ldg(reinterpret_cast<const unsigned long long*>(f) + w) & bits) == bits;
+}
+
 // Capacity of a group table for an expected number of distinct keys: a power of two with
 // load at most one half; `limit` = the most distinct keys accepted (7/8 of the slots).
 inline int64_t group_capacity_for(int64_t hint) {

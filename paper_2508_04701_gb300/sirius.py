@@ -25,6 +25,7 @@ OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
 AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
 AGG_MODES = {"auto": 0, "smem": 1, "global": 2, "part": 3, "hot": 4}
 PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2}
+BLOOM_MODES = {"auto": 0, "off": 1, "on": 2}
 JOIN_MODES = {"auto": 0, "hash": 1}
 
 
@@ -44,7 +45,9 @@ class PipelineDesc(ctypes.Structure):
                 ("agg_mode", ctypes.c_int32), ("group_cap_hint", ctypes.c_int64),
                 ("load_factor", ctypes.c_float), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("probe_variant", ctypes.c_int32),
-                ("join_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("join_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dpred", ctypes.c_void_p), ("dop", ctypes.c_int32), ("dliteral", ctypes.c_int32),
+                ("bloom", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -63,7 +66,7 @@ class DimIndex(ctypes.Structure):
     _fields_ = [("d_mem", ctypes.c_void_p), ("bytes", ctypes.c_size_t),
                 ("join_capacity", ctypes.c_int64), ("group_capacity", ctypes.c_int64),
                 ("direct_capacity", ctypes.c_int64),
-                ("key_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("key_width", ctypes.c_int32), ("bloom_log2", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) of every exported function
@@ -332,9 +335,10 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
               literal: int = 50, aggs="sum,count,min,max", group_cap_hint: int = 0,
               load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
               blocks_per_sm: int = 0, host: bool = False, probe_variant="auto",
-              join_mode="auto") -> PipelineDesc:
+              join_mode="auto", dim_op=None, dim_literal: int = 0, bloom="auto") -> PipelineDesc:
     """A pipeline descriptor over device columns (host=True: over host columns, for
-    sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?"""
+    sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?, and
+    dattr when dim_op is given (the dim-side predicate dattr <dim_op> dim_literal)."""
     P = _host_ptr if host else _ptr
     g = lambda d, k: P(d.get(k)) if d.get(k) is not None else None  # noqa: E731
     d = PipelineDesc(
@@ -344,7 +348,10 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
         AGG_MODES[agg_mode] if isinstance(agg_mode, str) else int(agg_mode), int(group_cap_hint),
         float(load_factor), int(block_threads), int(blocks_per_sm),
         PROBE_VARIANTS[probe_variant] if isinstance(probe_variant, str) else int(probe_variant),
-        JOIN_MODES[join_mode] if isinstance(join_mode, str) else int(join_mode), 0)
+        JOIN_MODES[join_mode] if isinstance(join_mode, str) else int(join_mode), 0,
+        g(dim, "dattr") if dim_op is not None else None,
+        (OPS[dim_op] if isinstance(dim_op, str) else int(dim_op)) if dim_op is not None else 0,
+        int(dim_literal), BLOOM_MODES[bloom] if isinstance(bloom, str) else int(bloom), 0)
     # the descriptor holds raw pointers: keep the tensors they point into alive with it
     d._columns = (dict(fact), dict(dim))
     return d

@@ -90,3 +90,36 @@ def test_scratch_size_query_grows_with_inputs(lib):
     assert big > small > 0
     d.group_cap_hint = 100
     assert lib.sirius_pipeline_scratch_bytes(ctypes.byref(d)) < big
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every struct the binding passes through the C ABI has the header's size and field offsets
+    (a small C program built against include/sirius.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2508_04701_gb300 import sirius as S
+    structs = {"sirius_pipeline_desc": S.PipelineDesc, "sirius_result": S.Result,
+               "sirius_dim_index": S.DimIndex, "sirius_join_table": S.JoinTable}
+    lines = ['#include "sirius.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, v = line.split()
+        got[(cname, field)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

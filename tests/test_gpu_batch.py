@@ -1,5 +1,7 @@
 """Batched pipelines (one set of persistent launches, optionally one CUDA graph): every
 query's result equals the CPU oracle and the same query run alone, bit-exact (GPU)."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -143,4 +145,30 @@ def test_batch_per_query_status(S):
     assert e.value.status == S.ERR_TABLE_FULL
     assert plan.last_status[2] == S.ERR_TABLE_FULL
     assert all(s == 0 for i, s in enumerate(plan.last_status) if i != 2)
+    plan.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_with_dim_predicates(S, use_graph):
+    """Queries with dim-side predicates (one- and two-column keys, different thresholds) in one
+    batch with queries without."""
+    tabs, descs, outs = [], [], []
+    for q in range(10):
+        spec = dg.plain_scale(n=50_000 + 7919 * q, m=3000 + 101 * q, composite=(q % 3 == 2),
+                              dt=(10 * q if q % 4 else 0), seed=q)
+        spec = dataclasses.replace(spec, grp_bound=300, fact_table=dg.BATCH_TABLE0 + 2 * q,
+                                   dim_table=dg.BATCH_TABLE0 + 2 * q + 1)
+        dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+        dop = "lt" if spec.dt else None
+        descs.append(S.make_desc(dev(fact), dev(dim), "lt", spec.t, group_cap_hint=300, dim_op=dop,
+                                 dim_literal=spec.dt))
+        outs.append(S.PipelineOutputs(S.lib().sirius_groupby_capacity(300) + 1))
+        tabs.append((fact, dim, spec.t, dop, spec.dt))
+    plan = S.BatchPlan(16)
+    g = plan.run(descs, outs, use_graph=use_graph)
+    for (fact, dim, t, dop, dt), o, gq in zip(tabs, outs, g):
+        got = O.sort_groups({k: v.cpu().numpy() for k, v in o.trimmed(gq).items()})
+        want = O.pipeline(fact, dim, "lt", t, dim_op=dop, dim_literal=dt)
+        for c in COLS:
+            assert np.array_equal(got[c], want[c]), c
     plan.close()

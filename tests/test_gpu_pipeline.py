@@ -352,3 +352,74 @@ def test_repeatable_across_block_shapes(S):
         got = run(S, fact, dim, "lt", 30, hint=100_000, block_threads=bt, blocks_per_sm=bps)
         for c in COLS:
             assert np.array_equal(got[c], ref[c])
+
+
+# ----------------------------------------------------------------------------- dim-side predicate
+def check_dim_pred(S, fact, dim, op, t, dop, dt, hint, **kw):
+    got = run(S, fact, dim, op, t, hint=hint, dim_op=dop, dim_literal=dt, **kw)
+    want = O.pipeline(fact, dim, op, t, dim_op=dop, dim_literal=dt)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), (dop, dt, kw, c)
+    return want["key"].size
+
+
+@pytest.mark.parametrize("join_mode", ["auto", "hash"])
+@pytest.mark.parametrize("bloom", ["auto", "off", "on"])
+def test_dim_predicate(S, join_mode, bloom):
+    """Predicate transfer: only dim rows with dattr < 10 take part (direct array and hash
+    table, Bloom filter on and off); every operator once, and the edges none / all."""
+    spec = dg.plain_scale(n=1_000_003, m=60_000, dt=10)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    assert check_dim_pred(S, fact, dim, "lt", 30, "lt", 10, 100_000, join_mode=join_mode, bloom=bloom) > 0
+    for dop, dt in (("le", 3), ("gt", 90), ("ge", 50), ("eq", 7), ("ne", 7)):
+        check_dim_pred(S, fact, dim, "lt", 30, dop, dt, 100_000, join_mode=join_mode, bloom=bloom)
+    assert check_dim_pred(S, fact, dim, "lt", 30, "lt", 0, 100_000, join_mode=join_mode, bloom=bloom) == 0
+    check_dim_pred(S, fact, dim, "lt", 30, "lt", 100, 100_000, join_mode=join_mode, bloom=bloom)
+
+
+@pytest.mark.parametrize("bloom", ["off", "on"])
+def test_dim_predicate_composite_duplicates_and_misses(S, bloom):
+    """Two-column keys (hash table + filter), then duplicate keys and fact keys absent from the
+    dim, both with a dim-side predicate."""
+    spec = dg.plain_scale(n=700_001, m=30_000, composite=True, dt=25)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    check_dim_pred(S, fact, dim, "lt", 30, "lt", 25, 100_000, bloom=bloom)
+    rng = np.random.default_rng(31)
+    m = 20_000
+    dim = {"pk": rng.integers(0, 12_000, size=m).astype(np.int32),        # duplicate keys
+           "grp": rng.integers(0, 700, size=m).astype(np.int32),
+           "dattr": rng.integers(0, 100, size=m).astype(np.int32)}
+    fact = {"fk": rng.integers(-500, 15_000, size=900_001).astype(np.int32),  # many misses
+            "pred": rng.integers(0, 100, size=900_001).astype(np.int32),
+            "val": rng.integers(-10**12, 10**12, size=900_001)}
+    for am in ("smem", "global", "hot"):
+        check_dim_pred(S, fact, dim, "lt", 60, "ge", 40, 1000, bloom=bloom, agg_mode=am)
+
+
+def test_dim_predicate_resident_index_and_host_columns(S):
+    """A dim index built with a dim-side predicate (and its Bloom filter) serves several probe
+    passes; the same query through pinned host columns."""
+    spec = dg.plain_scale(n=400_003, m=25_000, composite=True, dt=15)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    ddim = dev(dim)
+    desc0 = S.make_desc(dev(fact), ddim, "lt", 30, group_cap_hint=100_000, dim_op="lt", dim_literal=15)
+    index = S.sirius_dim_index_build(desc0)
+    assert index.struct.bloom_log2 > 0
+    for op, t in (("lt", 30), ("ge", 80)):
+        dfact = dev(fact)
+        desc = S.make_desc(dfact, ddim, op, t, group_cap_hint=100_000, dim_op="lt", dim_literal=15)
+        outs = S.PipelineOutputs(100_001)
+        g = S.sirius_run_probe(desc, index, outs)
+        got = O.sort_groups({k: v.cpu().numpy() for k, v in outs.trimmed(g).items()})
+        want = O.pipeline(fact, dim, op, t, dim_op="lt", dim_literal=15)
+        for c in COLS:
+            assert np.array_equal(got[c], want[c]), (op, c)
+    hf = {k: torch.from_numpy(v).pin_memory() for k, v in fact.items()}
+    hd = {k: torch.from_numpy(v).pin_memory() for k, v in dim.items()}
+    desc = S.make_desc(hf, hd, "lt", 30, group_cap_hint=100_000, host=True, dim_op="lt", dim_literal=15)
+    outs = S.HostOutputs(100_001)
+    g = S.sirius_run_pipeline_host(desc, outs, 100_000)
+    got = O.sort_groups({k: v.numpy() for k, v in outs.trimmed(g).items()})
+    want = O.pipeline(fact, dim, "lt", 30, dim_op="lt", dim_literal=15)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
