@@ -210,7 +210,7 @@ typedef struct {
   int32_t literal;
   uint32_t aggs;            /* SIRIUS_AGG_* mask (COUNT is always computed) */
   int32_t agg_mode;         /* 0 auto; 1 per-block shared-memory table (group table of at most
-                               3072 slots); 2 global reductions; 3 partitioned: the probe pass
+                               3510 slots); 2 global reductions; 3 partitioned: the probe pass
                                writes (group slot, value) per joined row, grouped by 4096-slot
                                partition within 4096-row tiles, and a second pass aggregates
                                each partition in shared memory (group table of at most 2^20
