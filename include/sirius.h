@@ -192,6 +192,23 @@ sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_width, const in
  * pass over the fact table evaluates the predicate, probes the join table and aggregates into
  * the group slot directly -- no intermediate row ids are materialised.  Finalize compacts the
  * groups with at least one row.  All columns are caller device memory. */
+/* A further dim joined as a filter (a semi-join, for star queries with several dims): a fact
+ * row takes part only if its key (fk, fk_hi) equals the key (pk, pk_hi) of some row of this
+ * dim that passes attr <op> literal (attr NULL: every row passes).  The dim contributes no
+ * column to the result. */
+typedef struct {
+  const int32_t* fk;        /* fact column, n values: the key into this dim, or its low word */
+  const int32_t* fk_hi;     /* NULL, or the high word of a two-column key */
+  const int32_t* pk;        /* dim keys, m values, or their low words */
+  const int32_t* pk_hi;     /* NULL, or the high words (must match fk_hi being NULL or not) */
+  const int32_t* attr;      /* NULL, or the dim column the predicate tests */
+  int64_t m;
+  int32_t op;               /* sirius_cmp of attr against literal */
+  int32_t literal;
+} sirius_semijoin;
+
+#define SIRIUS_MAX_SEMIJOINS 3
+
 typedef struct {
   /* fact (probe side), n rows */
   const int32_t* fk;        /* join key, or its low word */
@@ -240,7 +257,10 @@ typedef struct {
                                tested before each hash-table probe, so most probes of absent keys
                                skip their random bucket read; the direct-address join, itself an
                                exact filter, does not use it */
-  int32_t reserved2;
+  int32_t nsemi;            /* further dims joined as filters, 0..SIRIUS_MAX_SEMIJOINS (star query;
+                               sirius_run_pipeline only: the batched, resident-index and
+                               host-column calls reject them) */
+  sirius_semijoin semi[SIRIUS_MAX_SEMIJOINS];
 } sirius_pipeline_desc;
 
 typedef struct {

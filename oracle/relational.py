@@ -176,9 +176,19 @@ def groupby_loop(keys, vals) -> Dict[str, np.ndarray]:
 
 
 # ------------------------------------------------------------------------------- pipeline
+def semi_keep(fact_keys: np.ndarray, dim: Dict[str, np.ndarray], op: Optional[str],
+              literal: int) -> np.ndarray:
+    """Semi-join: which fact keys equal the key of some dim row that passes attr <op> literal
+    (every dim row when op is None)."""
+    pk = join_key(dim, "pk", "pk_hi")
+    if op is not None:
+        pk = pk[filter_rows(dim["attr"], op, literal).astype(np.int64)]
+    return np.isin(fact_keys, pk)
+
+
 def pipeline(fact: Dict[str, np.ndarray], dim: Dict[str, np.ndarray], op: str = "lt",
              literal: int = 50, join: str = "sorted", dim_op: Optional[str] = None,
-             dim_literal: int = 0) -> Dict[str, np.ndarray]:
+             dim_literal: int = 0, semi=None) -> Dict[str, np.ndarray]:
     """One pipeline of the push-based executor (Sec. 3.2.2): filter the fact rows, join the
     survivors to the dim on fk = pk, materialise the value and group key of each joined pair
     by row id (late materialisation), then group-by aggregate.
@@ -188,11 +198,18 @@ def pipeline(fact: Dict[str, np.ndarray], dim: Dict[str, np.ndarray], op: str = 
           (int32) when dim_op is given: the dim-side predicate dattr <dim_op> dim_literal keeps
           the dim rows that take part in the join (a filter on the build side; moving it there
           from above the join is the predicate transfer of Sec. 3.4).
+    semi: further dims joined as filters (a star query): a list of dicts {"fk": the fact's key
+          column into the dim, "fk_hi"?, "dim": {"pk", "pk_hi"?, "attr"?}, "op", "literal"};
+          a fact row takes part only if each of these keys has a partner (semi_keep).
     Group key: grp, or (grp, flag) packed by pack_group."""
     if dim_op is not None:
         keep = filter_rows(dim["dattr"], dim_op, dim_literal).astype(np.int64)
         dim = {k: (np.asarray(v)[keep] if v is not None else None) for k, v in dim.items()}
     sel = filter_rows(fact["pred"], op, literal).astype(np.int64)
+    for sj in semi or []:
+        keys = join_key({"fk": sj["fk"], "fk_hi": sj.get("fk_hi")}, "fk", "fk_hi")[sel]
+        sel = sel[semi_keep(keys, sj["dim"], sj.get("op") if sj["dim"].get("attr") is not None else None,
+                            sj.get("literal", 0))]
     fk = join_key(fact, "fk", "fk_hi")[sel]
     pk = join_key(dim, "pk", "pk_hi")
     jf = join_loop if join == "loop" else join_sorted
@@ -250,6 +267,6 @@ def sort_groups(res: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
     return {k: np.asarray(v)[o] for k, v in res.items()}
 
 
-__all__ = ["OPS", "filter_rows", "filter_rows_loop", "pack_composite", "pack_group",
+__all__ = ["OPS", "filter_rows", "filter_rows_loop", "pack_composite", "pack_group", "semi_keep",
            "join_key", "join_sorted", "join_loop", "groupby_agg", "groupby_loop", "pipeline",
            "merge_partials", "restrict_dim", "sort_pairs", "sort_groups"]

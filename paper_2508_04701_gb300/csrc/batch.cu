@@ -471,6 +471,10 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
   for (int i = 0; i < nq; ++i) {
     sirius_status st = validate_fact(&qs[i]);
     if (st == SIRIUS_OK && !prebuilt(indexes, i)) st = validate_dim(&qs[i]);
+    if (st == SIRIUS_OK && qs[i].nsemi != 0) {
+      set_error("batch: query %d: semi-join dims are taken by sirius_run_pipeline only", i);
+      st = SIRIUS_ERR_INVALID;
+    }
     if (st == SIRIUS_OK && !prebuilt(indexes, i) && qs[i].n > 0 && qs[i].m > 0 &&
         (qs[i].fk_hi == nullptr) != (qs[i].pk_hi == nullptr)) {
       set_error("batch: query %d mixes one- and two-column keys", i);

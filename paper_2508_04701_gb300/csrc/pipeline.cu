@@ -125,12 +125,83 @@ __global__ void run_init_kernel(PipeHeader* phdr, Agg* aggs, int64_t gslots) {
   for (int64_t i = tid; i < gslots; i += (int64_t)gridDim.x * blockDim.x) agg_identity(&aggs[i]);
 }
 
-template <bool kWide, int kMode, bool kVec>
+// ------------------------------------------------------------------ semi-join dims (star query)
+struct SemiInput {
+  const int32_t* pk;
+  const int32_t* pk_hi;
+  const int32_t* attr;
+  int64_t m;
+  int32_t op;
+  int32_t lit;
+};
+
+__device__ __forceinline__ bool semi_row_qualifies(const SemiInput& in, int64_t j) {
+  return !in.attr || cmp_op(in.attr[j], in.lit, in.op);
+}
+
+// Clears a semi-join dim's region: header (empty key range), bitmap and hash-set slots.
+__global__ void semi_init_kernel(SemiView v, int64_t jpairs) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (tid < 32) {
+    // word 0 of the header holds (key_min, key_max): start at (INT32_MAX, INT32_MIN)
+    reinterpret_cast<uint64_t*>(v.hdr)[tid] = tid == 0 ? 0x800000007FFFFFFFull : 0ull;
+    reinterpret_cast<uint64_t*>(v.jhdr)[tid] = 0;
+  }
+  for (int64_t i = tid; i < v.words; i += stride) v.bits[i] = 0;
+  const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
+  for (int64_t i = tid; i < jpairs; i += stride) reinterpret_cast<ulonglong2*>(v.jslots)[i] = ones;
+}
+
+// Range of the qualifying rows' one-column keys.
+__global__ void semi_minmax_kernel(SemiInput in, SemiHeader* h) {
+  int32_t lo = INT32_MAX, hi = INT32_MIN;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < in.m; j += (int64_t)gridDim.x * blockDim.x) {
+    if (!semi_row_qualifies(in, j)) continue;
+    const int32_t k = in.pk[j];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&h->key_min, lo);
+    atomicMax(&h->key_max, hi);
+  }
+}
+
+// Enters the qualifying rows' keys: into the bitmap when they are one column and their range
+// spans at most 32 bits per dim row (also when no row qualifies: an empty range), else into
+// the hash set (payload 0).
+template <bool kWide>
+__global__ void semi_build_kernel(SemiInput in, SemiView v) {
+  const int64_t range = (int64_t)v.hdr->key_max - (int64_t)v.hdr->key_min + 1;
+  const bool bitmap = !kWide && range <= 32 * (v.words - 2);
+  const int32_t kmin = v.hdr->key_min;
+  if (blockIdx.x == 0 && threadIdx.x == 0) v.hdr->bitmap = bitmap ? 1u : 0u;
+  bool dup = false;  // duplicate keys change nothing in a membership test
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < in.m; j += (int64_t)gridDim.x * blockDim.x) {
+    if (!semi_row_qualifies(in, j)) continue;
+    if (kWide) {
+      join_insert64((ulonglong2*)v.jslots, v.jcap, pack_key64(in.pk_hi[j], in.pk[j]), 0u, dup);
+    } else if (bitmap) {
+      const uint32_t k = (uint32_t)in.pk[j] - (uint32_t)kmin;
+      atomicOr(&v.bits[k >> 5], 1u << (k & 31));
+    } else {
+      const uint32_t key = (uint32_t)in.pk[j];
+      join_insert32((uint64_t*)v.jslots, v.jcap, key, (uint64_t)key, dup);
+    }
+  }
+}
+
+template <bool kWide, int kMode, bool kVec, bool kSemi>
 __global__ void __launch_bounds__(512)
-probe_kernel(ProbeArgs a) {
+probe_kernel(ProbeArgs a, SemiArgs sa) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
   const Lookup L = read_lookup(a);
+  SemiLookups SL;
+  if (kSemi) read_semi_lookup(sa, SL);
   const uint32_t slots = kMode == kAggSmem ? a.gslots : (kMode == kAggHot ? (uint32_t)kHotEntries : 0u);
   const SmemAggs T = smem_aggs(smem_raw, slots);
   if (kMode == kAggSmem || kMode == kAggHot) {
@@ -143,10 +214,10 @@ probe_kernel(ProbeArgs a) {
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
-    probe_quad<kWide, kMode, kVec>(a, T, L, q);
+    probe_quad<kWide, kMode, kVec, kSemi>(a, T, L, q, kSemi ? &SL : nullptr);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-    probe_one<kWide, kMode>(a, T, L, (nq << 2) + threadIdx.x);
+    probe_one<kWide, kMode, kSemi>(a, T, L, (nq << 2) + threadIdx.x, kSemi ? &SL : nullptr);
   if (kMode == kAggSmem || kMode == kAggHot) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
@@ -201,9 +272,10 @@ int occupancy_blocks(K kernel, int threads, size_t smem) {
   return b > 0 ? b : 1;
 }
 
-template <bool kWide, int kMode, bool kVec>
-sirius_status launch_probe(const ProbeArgs& a, int threads, int blocks_per_sm, size_t smem, cudaStream_t s) {
-  auto k = probe_kernel<kWide, kMode, kVec>;
+template <bool kWide, int kMode, bool kVec, bool kSemi>
+sirius_status launch_probe(const ProbeArgs& a, const SemiArgs& sa, int threads, int blocks_per_sm, size_t smem,
+                           cudaStream_t s) {
+  auto k = probe_kernel<kWide, kMode, kVec, kSemi>;
   if (kMode == kAggSmem || kMode == kAggHot) {
     static bool attr = false;
     if (!attr) {
@@ -227,7 +299,7 @@ sirius_status launch_probe(const ProbeArgs& a, int threads, int blocks_per_sm, s
   if (want < 1) want = 1;
   int64_t g = (int64_t)sm_count() * per_sm;
   if (g > want) g = want;
-  k<<<(unsigned)g, threads, smem, s>>>(a);
+  k<<<(unsigned)g, threads, smem, s>>>(a, sa);
   SIRIUS_LAUNCH_CHECK();
   return SIRIUS_OK;
 }
@@ -283,17 +355,17 @@ sirius_status launch_staged(const ProbeArgs& a, PipeHeader* phdr, cudaStream_t s
   return SIRIUS_OK;
 }
 
-template <bool kWide>
-sirius_status dispatch_probe(const ProbeArgs& a, int mode, bool vec, int threads, int bps, size_t smem,
-                             cudaStream_t s) {
+template <bool kWide, bool kSemi>
+sirius_status dispatch_probe(const ProbeArgs& a, const SemiArgs& sa, int mode, bool vec, int threads, int bps,
+                             size_t smem, cudaStream_t s) {
   if (mode == kAggSmem)
-    return vec ? launch_probe<kWide, kAggSmem, true>(a, threads, bps, smem, s)
-               : launch_probe<kWide, kAggSmem, false>(a, threads, bps, smem, s);
+    return vec ? launch_probe<kWide, kAggSmem, true, kSemi>(a, sa, threads, bps, smem, s)
+               : launch_probe<kWide, kAggSmem, false, kSemi>(a, sa, threads, bps, smem, s);
   if (mode == kAggHot)
-    return vec ? launch_probe<kWide, kAggHot, true>(a, threads, bps, kHotSmemBytes, s)
-               : launch_probe<kWide, kAggHot, false>(a, threads, bps, kHotSmemBytes, s);
-  return vec ? launch_probe<kWide, kAggGlobal, true>(a, threads, bps, 0, s)
-             : launch_probe<kWide, kAggGlobal, false>(a, threads, bps, 0, s);
+    return vec ? launch_probe<kWide, kAggHot, true, kSemi>(a, sa, threads, bps, kHotSmemBytes, s)
+               : launch_probe<kWide, kAggHot, false, kSemi>(a, sa, threads, bps, kHotSmemBytes, s);
+  return vec ? launch_probe<kWide, kAggGlobal, true, kSemi>(a, sa, threads, bps, 0, s)
+             : launch_probe<kWide, kAggGlobal, false, kSemi>(a, sa, threads, bps, 0, s);
 }
 
 }  // namespace
@@ -509,7 +581,7 @@ sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s) {
 }
 
 sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
-                        cudaStream_t s) {
+                        cudaStream_t s, const SemiView* semi, int nsemi) {
   if (q->n == 0) return SIRIUS_OK;
   ProbeArgs a;
   a.fk = q->fk;
@@ -527,25 +599,33 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   a.dslot = d.dslot;
   a.bloom = d.bloom;
   a.bloom_mask = d.bloom_mask;
+  SemiArgs sa;
+  sa.nsemi = nsemi;
+  for (int i = 0; i < kMaxSemi; ++i) sa.semi[i] = i < nsemi ? semi[i] : SemiView{};
   a.tab = r.aggs;
   a.gslots = (uint32_t)gslots;
   const int mode = r.mode;
-  const bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
-                   (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+  bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
+             (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+  for (int i = 0; i < nsemi; ++i)  // a star query's key columns take the vector loads too
+    vec = vec && ((uintptr_t)semi[i].fk & 15) == 0 && (!semi[i].fk_hi || ((uintptr_t)semi[i].fk_hi & 15) == 0);
   if (mode == kAggPart) {
     part::PartArgs pa{r.tgs, r.tval, r.prefix, r.ntiles, r.parts, 0};
     return d.key_width == 8 ? launch_part<true>(a, pa, vec, s) : launch_part<false>(a, pa, vec, s);
   }
   const bool staged_ok = mode == kAggGlobal && vec && ((uintptr_t)q->val & 15) == 0;
-  if (staged_ok && q->probe_variant == 2) {
+  if (staged_ok && q->probe_variant == 2 && nsemi == 0) {
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
     return d.key_width == 8 ? launch_staged<true>(a, r.phdr, s) : launch_staged<false>(a, r.phdr, s);
   }
   const int threads = q->block_threads > 0 ? q->block_threads : (mode == kAggSmem || mode == kAggHot ? 512 : 256);
   const size_t smem = mode == kAggSmem ? smem_aggs_bytes((uint32_t)gslots, false) : 0;  // hot cache: fixed size
   PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
-  return d.key_width == 8 ? dispatch_probe<true>(a, mode, vec, threads, q->blocks_per_sm, smem, s)
-                          : dispatch_probe<false>(a, mode, vec, threads, q->blocks_per_sm, smem, s);
+  if (nsemi > 0)
+    return d.key_width == 8 ? dispatch_probe<true, true>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s)
+                            : dispatch_probe<false, true>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s);
+  return d.key_width == 8 ? dispatch_probe<true, false>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s)
+                          : dispatch_probe<false, false>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s);
 }
 
 sirius_status run_finalize(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
@@ -589,10 +669,87 @@ static sirius_status validate_result(const sirius_result* r) {
 using namespace sirius;
 
 // ------------------------------------------------------------------ single query
+// ------------------------------------------------------------------ semi-join dims, host side
+SemiLayout semi_layout(const sirius_semijoin& sj) {
+  SemiLayout S;
+  S.key_width = (sj.pk_hi || sj.fk_hi) ? 8 : 4;
+  S.words = sj.m + 2;
+  S.jcap = sirius_join_table_capacity(sj.m > 0 ? sj.m : 1, 0.5);
+  S.off_bits = 256;
+  S.off_join = align_up(S.off_bits + (size_t)S.words * 4, 256);
+  S.total = align_up(S.off_join + 256 + (size_t)S.jcap * (S.key_width == 8 ? 16 : 8), 256);
+  return S;
+}
+
+static size_t semi_bytes(const sirius_pipeline_desc* q) {
+  size_t b = 0;
+  for (int i = 0; i < q->nsemi && i < kMaxSemi; ++i) b += semi_layout(q->semi[i]).total;
+  return b;
+}
+
+static SemiView semi_view(const SemiLayout& S, char* base, const sirius_semijoin& sj) {
+  SemiView v;
+  v.fk = sj.fk;
+  v.fk_hi = sj.fk_hi;
+  v.hdr = (SemiHeader*)base;
+  v.bits = (uint32_t*)(base + S.off_bits);
+  v.jhdr = (JoinHeader*)(base + S.off_join);
+  v.jslots = base + S.off_join + 256;
+  v.jcap = (uint32_t)S.jcap;
+  v.words = S.words;
+  v.key_width = S.key_width;
+  return v;
+}
+
+sirius_status validate_semi(const sirius_pipeline_desc* q) {
+  SIRIUS_REQUIRE(q->nsemi >= 0 && q->nsemi <= kMaxSemi, "pipeline: nsemi=%d out of [0, %d]", q->nsemi, kMaxSemi);
+  for (int i = 0; i < q->nsemi; ++i) {
+    const sirius_semijoin& sj = q->semi[i];
+    SIRIUS_REQUIRE(sj.m >= 0 && sj.m <= kMaxRows, "pipeline: semi-join %d: m=%lld out of range", i, (long long)sj.m);
+    SIRIUS_REQUIRE(sj.m == 0 || sj.pk, "pipeline: semi-join %d: NULL dim key column", i);
+    SIRIUS_REQUIRE(q->n == 0 || sj.fk, "pipeline: semi-join %d: NULL fact key column", i);
+    SIRIUS_REQUIRE((sj.pk_hi == nullptr) == (sj.fk_hi == nullptr) || sj.m == 0 || q->n == 0,
+                   "pipeline: semi-join %d: key widths of the two sides differ", i);
+    SIRIUS_REQUIRE(!sj.attr || (sj.op >= 0 && sj.op <= 5), "pipeline: semi-join %d: bad comparison %d", i, sj.op);
+  }
+  return SIRIUS_OK;
+}
+
+// Builds the semi-join dims into `base` (one region after another); fills views[0 .. nsemi).
+static sirius_status semi_build(const sirius_pipeline_desc* q, char* base, SemiView* views, cudaStream_t s) {
+  for (int i = 0; i < q->nsemi; ++i) {
+    const sirius_semijoin& sj = q->semi[i];
+    const SemiLayout S = semi_layout(sj);
+    views[i] = semi_view(S, base, sj);
+    base += S.total;
+    const int64_t jpairs = (S.jcap * (S.key_width == 8 ? 16 : 8) + 15) / 16;
+    const int64_t work = jpairs > S.words ? jpairs : S.words;
+    semi_init_kernel<<<grid_for(work, 256), 256, 0, s>>>(views[i], jpairs);
+    SIRIUS_LAUNCH_CHECK();
+    if (sj.m == 0) continue;
+    const SemiInput in{sj.pk, sj.pk_hi, sj.attr, sj.m, sj.op, sj.literal};
+    const int g = grid_for(sj.m, 256);
+    if (S.key_width == 8) {
+      semi_build_kernel<true><<<g, 256, 0, s>>>(in, views[i]);
+    } else {
+      semi_minmax_kernel<<<g, 256, 0, s>>>(in, views[i].hdr);
+      SIRIUS_LAUNCH_CHECK();
+      semi_build_kernel<false><<<g, 256, 0, s>>>(in, views[i]);
+    }
+    SIRIUS_LAUNCH_CHECK();
+  }
+  return SIRIUS_OK;
+}
+
+// A star query takes no partitioned aggregation (its probe pass is the fused one).
+static int star_agg_mode(const sirius_pipeline_desc* q) {
+  return (q->nsemi > 0 && q->agg_mode == kAggPart) ? kAggGlobal : q->agg_mode;
+}
+
 extern "C" size_t sirius_pipeline_scratch_bytes(const sirius_pipeline_desc* q) {
   if (!q) return 0;
   const DimLayout L = dim_layout_for(q);
-  return L.total + run_layout(L.gcap, q->n, q->agg_mode).total;
+  return L.total + run_layout(L.gcap, q->n, star_agg_mode(q)).total + semi_bytes(q);
 }
 
 extern "C" sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, sirius_result* result,
@@ -603,16 +760,22 @@ extern "C" sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, siri
   if (st != SIRIUS_OK) return st;
   st = validate_result(result);
   if (st != SIRIUS_OK) return st;
+  if ((st = validate_semi(q)) != SIRIUS_OK) return st;
   const DimLayout L = dim_layout_for(q);
-  const RunLayout R = run_layout(L.gcap, q->n, q->agg_mode);
+  const RunLayout R = run_layout(L.gcap, q->n, star_agg_mode(q));
   Scratch sc;
-  st = sc.acquire(d_scratch, scratch_bytes, L.total + R.total, s);
+  st = sc.acquire(d_scratch, scratch_bytes, L.total + R.total + semi_bytes(q), s);
   if (st != SIRIUS_OK) return st;
   const DimView d = dim_view(L, sc.base);
   const RunView r = run_view(R, sc.base + L.total);
   if ((st = dim_build(q, L, sc.base, s)) != SIRIUS_OK) return st;
+  SemiView semi[kMaxSemi];
+  if (q->nsemi > 0) {
+    PhaseTimer pt(s, SIRIUS_PHASE_PIPE_BUILD);
+    if ((st = semi_build(q, sc.base + L.total + R.total, semi, s)) != SIRIUS_OK) return st;
+  }
   if ((st = run_init(R, sc.base + L.total, s)) != SIRIUS_OK) return st;
-  if (q->m > 0 && (st = run_probe(q, d, r, R.gslots, s)) != SIRIUS_OK) return st;
+  if (q->m > 0 && (st = run_probe(q, d, r, R.gslots, s, semi, q->nsemi)) != SIRIUS_OK) return st;
   if ((st = run_finalize(q, d, r, R.gslots, pipe_out(result), s)) != SIRIUS_OK) return st;
   if (result->sync) return read_run_status(r, result, s);
   return SIRIUS_OK;
@@ -670,6 +833,7 @@ extern "C" sirius_status sirius_run_probe(const sirius_pipeline_desc* q, const s
   cudaStream_t s = (cudaStream_t)stream;
   sirius_status st = validate_fact(q);
   if (st != SIRIUS_OK) return st;
+  SIRIUS_REQUIRE(q->nsemi == 0, "probe: semi-join dims are taken by sirius_run_pipeline only");
   st = validate_result(result);
   if (st != SIRIUS_OK) return st;
   SIRIUS_REQUIRE(idx && idx->d_mem && idx->join_capacity > 0 && idx->group_capacity > 0,
@@ -736,6 +900,7 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
   cudaStream_t s = (cudaStream_t)stream;
   sirius_status st = validate_pair(q);
   if (st != SIRIUS_OK) return st;
+  SIRIUS_REQUIRE(q->nsemi == 0, "host columns: semi-join dims are taken by sirius_run_pipeline only");
   st = validate_result(result);
   if (st != SIRIUS_OK) return st;
   const HostLayout H = host_layout(q, chunk_rows, result->out_cap);

@@ -89,6 +89,41 @@ struct PipeOut {
   int32_t* d_status;
 };
 
+// Semi-join dims of a star query (further dims joined as filters).  Each has its own region:
+// [SemiHeader | bitmap words | JoinHeader + hash-set slots].  After a pass over the keys of its
+// qualifying rows, the build takes the bitmap over [key_min, key_max] when the keys are one
+// column and span at most 32 bits per dim row (membership = one bit), else the hash set (the
+// join table's layout with payload 0; membership = a bucket walk).
+constexpr int kMaxSemi = SIRIUS_MAX_SEMIJOINS;
+
+struct SemiHeader {
+  int32_t key_min, key_max;  // range of the qualifying one-column keys
+  uint32_t bitmap;           // 1: membership by the bitmap
+  int32_t pad0;
+  unsigned long long pad[30];
+};
+static_assert(sizeof(SemiHeader) == 256, "semi-join header is 256 bytes");
+
+struct SemiLayout {
+  int key_width = 4;
+  int64_t words = 0;  // bitmap words (32 bits each): m + 2
+  int64_t jcap = 0;   // hash-set slots
+  size_t off_bits = 256, off_join = 0, total = 0;
+};
+
+// One semi-join dim as the probe pass and its build see it.
+struct SemiView {
+  const int32_t* fk;     // fact key column, or its low word
+  const int32_t* fk_hi;  // nullptr, or the high word
+  SemiHeader* hdr;
+  uint32_t* bits;
+  JoinHeader* jhdr;
+  void* jslots;
+  uint32_t jcap;
+  int64_t words;
+  int key_width;
+};
+
 // Everything the probe pass reads for one query.
 struct ProbeArgs {
   const int32_t* fk;
@@ -109,6 +144,52 @@ struct ProbeArgs {
   const uint64_t* bloom;  // nullptr: no Bloom filter
   uint32_t bloom_mask;
 };
+
+// The semi-join dims of a star query: a kernel parameter of its own, read only by the kSemi
+// instantiations of the probe pass (so the others carry no trace of it).
+struct SemiArgs {
+  int32_t nsemi;
+  SemiView semi[kMaxSemi];
+};
+
+// How the probe pass tests one semi-join dim: its columns and structures, and the outcome of
+// the build read once from its header.
+struct SemiLookup {
+  bool bitmap;
+  bool wide;
+  int32_t kmin;
+  uint32_t range;  // key_max - key_min + 1, 0 when no dim row qualifies
+  uint32_t jcap;
+  const int32_t* fk;
+  const int32_t* fk_hi;
+  const uint32_t* bits;
+  const void* jslots;
+};
+struct SemiLookups {
+  int n;
+  SemiLookup s[kMaxSemi];
+};
+
+__device__ __forceinline__ void read_semi_lookup(const SemiArgs& sa, SemiLookups& SL) {
+  SL.n = sa.nsemi;
+#pragma unroll
+  for (int i = 0; i < kMaxSemi; ++i) {
+    SL.s[i] = SemiLookup{false, false, 0, 0u, 0u, nullptr, nullptr, nullptr, nullptr};
+    if (i < sa.nsemi) {
+      const SemiView& v = sa.semi[i];
+      const int64_t range = (int64_t)v.hdr->key_max - (int64_t)v.hdr->key_min + 1;
+      SL.s[i].bitmap = v.hdr->bitmap != 0;
+      SL.s[i].wide = v.key_width == 8;
+      SL.s[i].kmin = v.hdr->key_min;
+      SL.s[i].range = range > 0 ? (uint32_t)range : 0u;
+      SL.s[i].jcap = v.jcap;
+      SL.s[i].fk = v.fk;
+      SL.s[i].fk_hi = v.fk_hi;
+      SL.s[i].bits = v.bits;
+      SL.s[i].jslots = v.jslots;
+    }
+  }
+}
 
 // How the probe pass finds a key's group slot, read once from the dim header.
 struct Lookup {
@@ -286,8 +367,71 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
 }
 
 // Filter, probe and aggregate the four rows of quad q (rows 4q .. 4q+3, all < n).
-template <bool kWide, int kMode, bool kVec>
-__device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t q) {
+// Membership of a key in a semi-join dim: one bit of the bitmap, or a bucket walk of the hash
+// set (read-only during the probe pass: non-coherent loads).
+template <bool kWide>
+__device__ __forceinline__ bool semi_contains(const SemiLookup& SL, uint64_t key) {
+  if (!kWide && SL.bitmap) {
+    const uint32_t k = (uint32_t)key - (uint32_t)SL.kmin;
+    return k < SL.range && ((__ldg(SL.bits + (k >> 5)) >> (k & 31)) & 1u);
+  }
+  constexpr int kPer = kWide ? 2 : 4;
+  uint32_t slot = kWide ? home_slot64(key, SL.jcap) : home_slot32((uint32_t)key, SL.jcap);
+  for (uint32_t step = 0; step < SL.jcap; step += kPer) {
+    uint64_t w[4];
+    load_bucket<kWide>(SL.jslots, slot, w);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const uint64_t k = kWide ? w[2 * j] : (uint64_t)(uint32_t)w[j];
+      const uint32_t p = kWide ? (uint32_t)w[2 * j + 1] : (uint32_t)(w[j] >> 32);
+      if (p == kEmpty32) return false;
+      if (k == key) return true;
+    }
+    slot += kPer;
+    if (slot >= SL.jcap) slot = 0;
+  }
+  return false;
+}
+
+// Star query: drop the selected rows among row0 .. row0+3 (bit r of `bits`; rows below n)
+// whose key into some semi-join dim has no qualifying partner there.  kVec: the four rows'
+// keys come as one 16-byte load per key column (row0 a multiple of 4, columns 16-byte aligned).
+template <bool kVec>
+__device__ __forceinline__ uint32_t semi_filter(const SemiLookups& SL, int64_t row0, uint32_t bits) {
+#pragma unroll
+  for (int i = 0; i < kMaxSemi; ++i) {
+    if (i >= SL.n || !bits) break;
+    const SemiLookup& sl = SL.s[i];
+    uint64_t key[4];
+    if (kVec) {
+      const int4 k4 = __ldcs(reinterpret_cast<const int4*>(sl.fk + row0));
+      int4 h4 = make_int4(0, 0, 0, 0);
+      if (sl.wide) h4 = __ldcs(reinterpret_cast<const int4*>(sl.fk_hi + row0));
+      key[0] = sl.wide ? pack_key64(h4.x, k4.x) : (uint64_t)(uint32_t)k4.x;
+      key[1] = sl.wide ? pack_key64(h4.y, k4.y) : (uint64_t)(uint32_t)k4.y;
+      key[2] = sl.wide ? pack_key64(h4.z, k4.z) : (uint64_t)(uint32_t)k4.z;
+      key[3] = sl.wide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        key[r] = 0;
+        if ((bits >> r) & 1u)
+          key[r] = sl.wide ? pack_key64(sl.fk_hi[row0 + r], sl.fk[row0 + r]) : (uint64_t)(uint32_t)sl.fk[row0 + r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (!((bits >> r) & 1u)) continue;
+      const bool in = sl.wide ? semi_contains<true>(sl, key[r]) : semi_contains<false>(sl, key[r]);
+      if (!in) bits &= ~(1u << r);
+    }
+  }
+  return bits;
+}
+
+template <bool kWide, int kMode, bool kVec, bool kSemi = false>
+__device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t q,
+                                           const SemiLookups* SLp = nullptr) {
   const int64_t row0 = q << 2;
   uint32_t bits = 0;
   uint64_t key[4];
@@ -296,6 +440,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
     const int4 p4 = __ldcs(reinterpret_cast<const int4*>(a.pred) + q);
     bits = (uint32_t)cmp_op(p4.x, a.lit, a.op) | ((uint32_t)cmp_op(p4.y, a.lit, a.op) << 1) |
            ((uint32_t)cmp_op(p4.z, a.lit, a.op) << 2) | ((uint32_t)cmp_op(p4.w, a.lit, a.op) << 3);
+    if (kSemi && bits) bits = semi_filter<true>(*SLp, row0, bits);
     if (!bits) return;
     const int4 k4 = __ldcs(reinterpret_cast<const int4*>(a.fk) + q);
     if (kWide) {
@@ -314,6 +459,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
 #pragma unroll
     for (int r = 0; r < 4; ++r)
       if (cmp_op(a.pred[row0 + r], a.lit, a.op)) bits |= 1u << r;
+    if (kSemi && bits) bits = semi_filter<false>(*SLp, row0, bits);
     if (!bits) return;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -325,9 +471,11 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
 }
 
 // Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
-template <bool kWide, int kMode>
-__device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t r) {
+template <bool kWide, int kMode, bool kSemi = false>
+__device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t r,
+                                          const SemiLookups* SLp = nullptr) {
   if (!cmp_op(a.pred[r], a.lit, a.op)) return;
+  if (kSemi && !semi_filter<false>(*SLp, r, 1u)) return;
   uint64_t key[4] = {0, 0, 0, 0};
   int64_t v[4] = {0, 0, 0, 0};
   key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
@@ -392,7 +540,7 @@ int choose_mode(int agg_mode, int64_t gslots, int64_t n);
 sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char* base, cudaStream_t s);
 sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s);
 sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
-                        cudaStream_t s);
+                        cudaStream_t s, const SemiView* semi = nullptr, int nsemi = 0);
 sirius_status run_finalize(const sirius_pipeline_desc* q, const DimView& d, const RunView& r,
                            int64_t gslots, const PipeOut& out, cudaStream_t s);
 sirius_status read_run_status(const RunView& r, sirius_result* res, cudaStream_t s);

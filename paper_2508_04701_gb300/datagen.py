@@ -38,6 +38,8 @@ BATCH_TABLE0 = 0x100  # query q of a batch: fact 0x100 + 2q, dim 0x101 + 2q
 
 # fact columns
 C_FK, C_PRED, C_VAL, C_FK_ROW = 0, 1, 2, 3
+C_SEMI0 = 8          # fact column tag of the key into semi-join dim s: C_SEMI0 + s
+SEMI_TABLE_STEP = 0x10  # semi-join dim s of a query: table dim_table + SEMI_TABLE_STEP * (s + 1)
 # dim columns
 C_PK_TAG, C_GRP, C_FLAG_TAG, C_KEY_SALT, C_DATTR = 0, 1, 2, 3, 4
 
@@ -143,6 +145,9 @@ class StarSpec:
     group_flag: bool = False    # group key (grp, flag) = bijection of dim row onto [0, m/2) x {0,1}
     dim_attr_bound: int = 0     # > 0: dim column dattr uniform in [0, dim_attr_bound)
     dt: int = 0                 # with dattr: the dim-side predicate dattr < dt
+    semi: int = 0               # further dims joined as filters (star query), 0..3
+    semi_m: int = 0             # rows of each: pk a permutation of [0, semi_m), attr in [0, 100)
+    semi_t: int = 50            # the filter dims' predicate attr < semi_t
     aggs: str = "sum,count,min,max"
     seed: int = 0
     fact_table: int = FACT
@@ -167,6 +172,13 @@ def plain_scale(n: int = 600_000_000, m: int = 15_000_000, composite: bool = Fal
     name = "plain_600M" + ("_composite" if composite else "") + (f"_dim{dt}" if dt else "")
     return StarSpec(name, n=n, m=m, fk_domain=m, grp_bound=100_000, t=30, composite=composite,
                     seed=seed, dim_attr_bound=100 if dt else 0, dt=dt)
+
+
+def star(n: int = 600_000_000, m: int = 15_000_000, seed: int = 0) -> StarSpec:
+    """The 600M-row query joined to two more dims as filters (a star query of three dims): two
+    1.5M-row dims, each keeping the rows with attr < 50, so a quarter of the fact rows join."""
+    return StarSpec("star_600M", n=n, m=m, fk_domain=m, grp_bound=100_000, t=30, seed=seed,
+                    semi=2, semi_m=1_500_000, semi_t=50)
 
 
 def skewed(n: int = 300_000_000, m: int = 10_000_000, seed: int = 0) -> StarSpec:
@@ -233,7 +245,26 @@ def gen_fact_host(spec: StarSpec, i0: int = 0, i1: Optional[int] = None,
         out["fk"] = bounded(r_fk, spec.fk_domain).astype(np.int32)
     out["pred"] = bounded(stream(s, T, C_PRED, i0, i1), spec.pred_bound).astype(np.int32)
     out["val"] = bounded(stream(s, T, C_VAL, i0, i1), spec.val_bound)
+    for k in range(spec.semi):
+        out[f"sk{k}"] = bounded(stream(s, T, C_SEMI0 + k, i0, i1), spec.semi_m).astype(np.int32)
     return out
+
+
+def gen_semi_dims_host(spec: StarSpec):
+    """The star query's filter dims as numpy arrays: pk int32 (a permutation), attr int32."""
+    out = []
+    for k in range(spec.semi):
+        T = spec.dim_table + SEMI_TABLE_STEP * (k + 1)
+        out.append({"pk": permutation(spec.seed, T, C_PK_TAG, spec.semi_m).astype(np.int32),
+                    "attr": bounded(stream(spec.seed, T, C_DATTR, 0, spec.semi_m), 100).astype(np.int32)})
+    return out
+
+
+def semi_args(spec: StarSpec, fact, semi_dims):
+    """The `semi` argument (filter dims of a star query) of the oracle's pipeline and of the
+    binding's make_desc: fact column sk<k> against filter dim k, attr < semi_t."""
+    return [{"fk": fact[f"sk{k}"], "dim": semi_dims[k], "op": "lt", "literal": spec.semi_t}
+            for k in range(spec.semi)]
 
 
 # ----------------------------------------------------------------------------- device tables
@@ -361,4 +392,18 @@ def gen_fact_device(spec: StarSpec, dim_dev=None, device="cuda", cdf_dev=None):
         out["fk"] = _dbounded(b_fk, 0, n, spec.fk_domain, device, torch.int32)
     out["pred"] = _dbounded(stream_base(s, T, C_PRED), 0, n, spec.pred_bound, device, torch.int32)
     out["val"] = _dbounded(stream_base(s, T, C_VAL), 0, n, spec.val_bound, device, torch.int64)
+    for k in range(spec.semi):
+        out[f"sk{k}"] = _dbounded(stream_base(s, T, C_SEMI0 + k), 0, n, spec.semi_m, device, torch.int32)
+    return out
+
+
+def gen_semi_dims_device(spec: StarSpec, device="cuda"):
+    """The star query's filter dims as device tensors, bit-identical to gen_semi_dims_host."""
+    import torch
+    out = []
+    for k in range(spec.semi):
+        T = spec.dim_table + SEMI_TABLE_STEP * (k + 1)
+        out.append({"pk": _dpermutation(spec.seed, T, C_PK_TAG, spec.semi_m, device).to(torch.int32),
+                    "attr": _dbounded(stream_base(spec.seed, T, C_DATTR), 0, spec.semi_m, 100, device,
+                                      torch.int32)})
     return out

@@ -36,6 +36,15 @@ class SiriusError(RuntimeError):
         self.needed = needed
 
 
+class Semijoin(ctypes.Structure):
+    _fields_ = [("fk", ctypes.c_void_p), ("fk_hi", ctypes.c_void_p), ("pk", ctypes.c_void_p),
+                ("pk_hi", ctypes.c_void_p), ("attr", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("op", ctypes.c_int32), ("literal", ctypes.c_int32)]
+
+
+MAX_SEMIJOINS = 3
+
+
 class PipelineDesc(ctypes.Structure):
     _fields_ = [("fk", ctypes.c_void_p), ("fk_hi", ctypes.c_void_p), ("pred", ctypes.c_void_p),
                 ("val", ctypes.c_void_p), ("n", ctypes.c_int64),
@@ -47,7 +56,8 @@ class PipelineDesc(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("probe_variant", ctypes.c_int32),
                 ("join_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("dpred", ctypes.c_void_p), ("dop", ctypes.c_int32), ("dliteral", ctypes.c_int32),
-                ("bloom", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("bloom", ctypes.c_int32), ("nsemi", ctypes.c_int32),
+                ("semi", Semijoin * MAX_SEMIJOINS)]
 
 
 class Result(ctypes.Structure):
@@ -335,10 +345,13 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
               literal: int = 50, aggs="sum,count,min,max", group_cap_hint: int = 0,
               load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
               blocks_per_sm: int = 0, host: bool = False, probe_variant="auto",
-              join_mode="auto", dim_op=None, dim_literal: int = 0, bloom="auto") -> PipelineDesc:
+              join_mode="auto", dim_op=None, dim_literal: int = 0, bloom="auto",
+              semi=None) -> PipelineDesc:
     """A pipeline descriptor over device columns (host=True: over host columns, for
     sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?, and
-    dattr when dim_op is given (the dim-side predicate dattr <dim_op> dim_literal)."""
+    dattr when dim_op is given (the dim-side predicate dattr <dim_op> dim_literal).
+    semi: up to MAX_SEMIJOINS further dims joined as filters (a star query), each a dict
+    {"fk": fact key column, "fk_hi"?, "dim": {"pk", "pk_hi"?, "attr"?}, "op", "literal"}."""
     P = _host_ptr if host else _ptr
     g = lambda d, k: P(d.get(k)) if d.get(k) is not None else None  # noqa: E731
     d = PipelineDesc(
@@ -352,8 +365,19 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
         g(dim, "dattr") if dim_op is not None else None,
         (OPS[dim_op] if isinstance(dim_op, str) else int(dim_op)) if dim_op is not None else 0,
         int(dim_literal), BLOOM_MODES[bloom] if isinstance(bloom, str) else int(bloom), 0)
+    semi = list(semi or [])
+    if len(semi) > MAX_SEMIJOINS:
+        raise ValueError(f"at most {MAX_SEMIJOINS} semi-join dims")
+    keep = []
+    for i, sj in enumerate(semi):
+        sd = sj["dim"]
+        d.semi[i] = Semijoin(P(sj["fk"]), P(sj.get("fk_hi")) if sj.get("fk_hi") is not None else None,
+                             g(sd, "pk"), g(sd, "pk_hi"), g(sd, "attr"), sd["pk"].numel(),
+                             OPS[sj.get("op", "lt")], int(sj.get("literal", 0)))
+        keep.append((sj["fk"], sj.get("fk_hi"), dict(sd)))
+    d.nsemi = len(semi)
     # the descriptor holds raw pointers: keep the tensors they point into alive with it
-    d._columns = (dict(fact), dict(dim))
+    d._columns = (dict(fact), dict(dim), keep)
     return d
 
 

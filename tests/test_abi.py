@@ -103,7 +103,8 @@ def test_struct_layouts_match_header(tmp_path):
         pytest.skip("no C compiler")
     from paper_2508_04701_gb300 import sirius as S
     structs = {"sirius_pipeline_desc": S.PipelineDesc, "sirius_result": S.Result,
-               "sirius_dim_index": S.DimIndex, "sirius_join_table": S.JoinTable}
+               "sirius_dim_index": S.DimIndex, "sirius_join_table": S.JoinTable,
+               "sirius_semijoin": S.Semijoin}
     lines = ['#include "sirius.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

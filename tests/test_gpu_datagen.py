@@ -43,3 +43,17 @@ def test_stream_offsets_match():
     assert rc == 0
     want = dg.stream(0, dg.FACT, dg.C_VAL, 123_456_789, 123_457_789)
     assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
+
+
+def test_star_filter_dims_match_host():
+    spec = dg.star(n=200_003, m=20_000)
+    spec = dg.StarSpec(**{**spec.__dict__, "semi_m": 30_001})
+    hs, ds = dg.gen_semi_dims_host(spec), dg.gen_semi_dims_device(spec)
+    assert len(hs) == len(ds) == 2
+    for h, d in zip(hs, ds):
+        for k in h:
+            assert np.array_equal(h[k], d[k].cpu().numpy()), k
+    hf = dg.gen_fact_host(spec)
+    df = dg.gen_fact_device(spec)
+    for k in ("sk0", "sk1"):
+        assert np.array_equal(hf[k], df[k].cpu().numpy()), k

@@ -423,3 +423,76 @@ def test_dim_predicate_resident_index_and_host_columns(S):
     want = O.pipeline(fact, dim, "lt", 30, dim_op="lt", dim_literal=15)
     for c in COLS:
         assert np.array_equal(got[c], want[c]), c
+
+
+# ----------------------------------------------------------------------------- star queries
+def star_check(S, fact, dim, semi, t=30, hint=100_000, **kw):
+    dsemi = [dict(sj, fk=dev({"k": sj["fk"]})["k"], fk_hi=(dev({"k": sj["fk_hi"]})["k"] if sj.get("fk_hi") is not None else None),
+                  dim=dev(sj["dim"])) for sj in semi]
+    got = S.run_pipeline(dev(fact), dev(dim), "lt", t, "sum,count,min,max", hint, semi=dsemi, **kw)
+    torch.cuda.synchronize()
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in got.items()})
+    want = O.pipeline(fact, dim, "lt", t, dim_op=kw.get("dim_op"), dim_literal=kw.get("dim_literal", 0), semi=semi)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), (kw, c)
+    return want["key"].size
+
+
+@pytest.mark.parametrize("nsemi", [1, 2, 3])
+@pytest.mark.parametrize("agg_mode", ["auto", "smem", "global", "hot"])
+def test_star_query(S, nsemi, agg_mode):
+    """The fused pass with further dims joined as filters (bitmap membership: dense keys)."""
+    groups = 1000 if agg_mode == "smem" else 100_000   # a 2049-slot table fits shared memory
+    spec = dg.StarSpec("star", n=700_003, m=40_000, fk_domain=40_000, grp_bound=groups,
+                       t=30, semi=nsemi, semi_m=25_000 + 1000 * nsemi, semi_t=60, seed=nsemi)
+    dim, fact, sd = dg.gen_dim_host(spec), dg.gen_fact_host(spec), dg.gen_semi_dims_host(spec)
+    assert star_check(S, fact, dim, dg.semi_args(spec, fact, sd), hint=groups, agg_mode=agg_mode) > 0
+
+
+def test_star_query_hash_sets_composite_and_edges(S):
+    """Filter dims whose keys need the hash set (sparse one-column keys, two-column keys, keys
+    the fact never references, duplicates), no attr predicate, a predicate nothing passes, and
+    a dim-side predicate with its Bloom filter on the main dim at the same time."""
+    rng = np.random.default_rng(77)
+    n, m = 500_003, 30_000
+    fact = {"fk": rng.integers(0, m, size=n).astype(np.int32), "pred": rng.integers(0, 100, size=n).astype(np.int32),
+            "val": rng.integers(-10**12, 10**12, size=n),
+            "s0": rng.integers(-2**31, 2**31 - 1, size=n).astype(np.int32)}
+    dim = {"pk": rng.permutation(m).astype(np.int32), "grp": rng.integers(0, 3000, size=m).astype(np.int32),
+           "dattr": rng.integers(0, 100, size=m).astype(np.int32)}
+    sparse = {"pk": np.concatenate([fact["s0"][:: 7][:20_000], rng.integers(-2**31, 2**31 - 1, size=5000)]).astype(np.int32),
+              "attr": rng.integers(0, 100, size=25_000).astype(np.int32)}
+    pool = rng.integers(-2**31, 2**31, size=(4000, 2)).astype(np.int64)
+    fi = rng.integers(0, 6000, size=n) % 4000
+    fact["w_lo"], fact["w_hi"] = pool[fi, 1].astype(np.int32), pool[fi, 0].astype(np.int32)
+    wide = {"pk": pool[:2500, 1].astype(np.int32), "pk_hi": pool[:2500, 0].astype(np.int32),
+            "attr": rng.integers(0, 100, size=2500).astype(np.int32)}
+    wide_dups = {k: np.concatenate([v, v[:300]]) for k, v in wide.items()}
+    s_sparse = {"fk": fact["s0"], "dim": sparse, "op": "lt", "literal": 70}
+    s_wide = {"fk": fact["w_lo"], "fk_hi": fact["w_hi"], "dim": wide_dups, "op": "ge", "literal": 30}
+    s_all = {"fk": fact["fk"], "dim": {"pk": dim["pk"]}, "op": "lt", "literal": 0}
+    assert star_check(S, fact, dim, [s_sparse]) > 0
+    assert star_check(S, fact, dim, [s_wide, s_sparse]) > 0
+    assert star_check(S, fact, dim, [s_all, s_wide]) > 0
+    none = {"fk": fact["fk"], "dim": {"pk": dim["pk"], "attr": dim["dattr"]}, "op": "lt", "literal": 0}
+    assert star_check(S, fact, dim, [s_wide, none]) == 0
+    for bloom in ("auto", "off"):
+        star_check(S, fact, dim, [s_sparse], dim_op="lt", dim_literal=40, join_mode="hash", bloom=bloom)
+
+
+def test_star_query_rejected_where_not_taken(S):
+    spec = dg.star(n=10_000, m=2000)
+    spec = dg.StarSpec(**{**spec.__dict__, "semi_m": 1000})
+    dim, fact, sd = dg.gen_dim_host(spec), dg.gen_fact_host(spec), dg.gen_semi_dims_host(spec)
+    semi = [dict(sj, fk=dev({"k": sj["fk"]})["k"], dim=dev(sj["dim"])) for sj in dg.semi_args(spec, fact, sd)]
+    desc = S.make_desc(dev(fact), dev(dim), "lt", 30, group_cap_hint=100_000, semi=semi)
+    outs = S.PipelineOutputs(100_001)
+    plan = S.BatchPlan(1)
+    with pytest.raises(S.SiriusError) as e:
+        plan.run([desc], [outs])
+    assert e.value.status == S.ERR_INVALID
+    plan.close()
+    index = S.sirius_dim_index_build(desc)
+    with pytest.raises(S.SiriusError) as e:
+        S.sirius_run_probe(desc, index, outs)
+    assert e.value.status == S.ERR_INVALID

@@ -235,6 +235,57 @@ def check_dim_predicate_brute(o, seed):
     assert none["key"].size == 0
 
 
+def check_semi_brute(o, seed):
+    """Star query: one or two further dims joined as filters (duplicate keys, misses, a
+    predicate on each or none, two-column keys for one of them), against Python loops."""
+    rng = np.random.default_rng(seed)
+    n, m = int(rng.integers(0, 300)), int(rng.integers(1, 40))
+    fact = {"fk": rng.integers(0, 30, size=n).astype(np.int32),
+            "pred": rng.integers(0, 10, size=n).astype(np.int32),
+            "val": rng.integers(-10**6, 10**6, size=n).astype(np.int64)}
+    dim = {"pk": rng.integers(0, 25, size=m).astype(np.int32), "grp": rng.integers(0, 5, size=m).astype(np.int32)}
+    semi = []
+    for s_ in range(int(rng.integers(1, 3))):
+        ms = int(rng.integers(0, 30))
+        wide = bool(rng.integers(0, 2)) and s_ == 1
+        sd = {"pk": rng.integers(0, 20, size=ms).astype(np.int32), "attr": rng.integers(0, 10, size=ms).astype(np.int32)}
+        sj = {"fk": rng.integers(0, 24, size=n).astype(np.int32), "dim": sd,
+              "op": o.OPS[int(rng.integers(0, 6))], "literal": int(rng.integers(0, 11))}
+        if wide:
+            sd["pk_hi"] = rng.integers(-1, 2, size=ms).astype(np.int32)
+            sj["fk_hi"] = rng.integers(-1, 2, size=n).astype(np.int32)
+        if rng.integers(0, 4) == 0:
+            del sd["attr"]
+        semi.append(sj)
+    cmp = {"lt": lambda a, b: a < b, "le": lambda a, b: a <= b, "gt": lambda a, b: a > b,
+           "ge": lambda a, b: a >= b, "eq": lambda a, b: a == b, "ne": lambda a, b: a != b}
+
+    def key(cols_lo, cols_hi, i):
+        return (int(cols_hi[i]) if cols_hi is not None else 0, int(cols_lo[i]))
+    acc = {}
+    for i in range(n):
+        if not int(fact["pred"][i]) < 7:
+            continue
+        ok = True
+        for sj in semi:
+            sd = sj["dim"]
+            k = key(sj["fk"], sj.get("fk_hi"), i)
+            ok = ok and any(key(sd["pk"], sd.get("pk_hi"), j) == k and
+                            ("attr" not in sd or cmp[sj["op"]](int(sd["attr"][j]), sj["literal"]))
+                            for j in range(sd["pk"].size))
+        if not ok:
+            continue
+        for j in range(m):
+            if int(dim["pk"][j]) == int(fact["fk"][i]):
+                g, v = int(dim["grp"][j]), int(fact["val"][i])
+                a = acc.setdefault(g, [0, 0, v, v])
+                a[0] += v; a[1] += 1; a[2] = min(a[2], v); a[3] = max(a[3], v)
+    r = o.pipeline(fact, dim, "lt", 7, semi=semi)
+    assert r["key"].tolist() == sorted(acc)
+    for k, s_, c, mn, mx in zip(r["key"], r["sum"], r["count"], r["min"], r["max"]):
+        assert acc[int(k)] == [int(s_), int(c), int(mn), int(mx)], int(k)
+
+
 # ----------------------------------------------------------------------------- the pins
 @pytest.mark.parametrize("seed", range(60))
 def test_filter_brute(seed):
@@ -287,6 +338,11 @@ def test_composite_and_group_keys(seed):
 
 
 @pytest.mark.parametrize("seed", range(40))
+def test_semi_join_brute(seed):
+    check_semi_brute(O, seed)
+
+
+@pytest.mark.parametrize("seed", range(40))
 def test_dim_predicate_brute(seed):
     check_dim_predicate_brute(O, seed)
 
@@ -324,11 +380,15 @@ def _mutant(**over):
     for k, v in over.items():
         setattr(m, k, v)
     # pipeline must call the mutant's pieces, so rebuild it over the namespace
-    def pipeline(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0):
+    def pipeline(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0, semi=None):
         if dim_op is not None:
             keep = m.filter_rows(dim["dattr"], dim_op, dim_literal).astype(np.int64)
             dim = {k: v[keep] for k, v in dim.items()}
         sel = m.filter_rows(fact["pred"], op, literal).astype(np.int64)
+        for sj in semi or []:
+            keys = O.join_key({"fk": sj["fk"], "fk_hi": sj.get("fk_hi")}, "fk", "fk_hi")[sel]
+            sop = sj.get("op") if sj["dim"].get("attr") is not None else None
+            sel = sel[m.semi_keep(keys, sj["dim"], sop, sj.get("literal", 0))]
         fk = O.join_key(fact, "fk", "fk_hi")[sel]
         pk = O.join_key(dim, "pk", "pk_hi")
         p, b = m.join_sorted(fk, pk)
@@ -378,11 +438,24 @@ def _flag_signed_shift(grp, flag=None):
     return g * 256 + np.asarray(flag, dtype=np.int64)   # sign-extended byte: (g, -1) == (g-1, 255)
 
 
-def _ignores_dim_predicate(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0):
-    return O.pipeline(fact, dim, op, literal, join)
+def _ignores_dim_predicate(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0,
+                           semi=None):
+    return O.pipeline(fact, dim, op, literal, join, semi=semi)
+
+
+def _ignores_semi_joins(fact, dim, op="lt", literal=50, join="sorted", dim_op=None, dim_literal=0, semi=None):
+    return O.pipeline(fact, dim, op, literal, join, dim_op, dim_literal)
+
+
+def _semi_ignores_predicate(fact_keys, dim, op, literal):
+    return O.semi_keep(fact_keys, dim, None, literal)
 
 
 MUTANTS = [
+    ("semi-joins ignored", dict(pipeline=_ignores_semi_joins),
+     lambda m: [check_semi_brute(m, s) for s in range(10)]),
+    ("semi-join predicate ignored", dict(semi_keep=_semi_ignores_predicate),
+     lambda m: [check_semi_brute(m, s) for s in range(10)]),
     ("dim predicate ignored", dict(pipeline=_ignores_dim_predicate),
      lambda m: [check_dim_predicate_brute(m, s) for s in range(10)]),
     ("filter le for lt (dim predicate)", dict(filter_rows=_le_instead_of_lt),
