@@ -471,7 +471,8 @@ def run_configs(S, torch, dev, rank):
     must give the same groups), and as a one-query batch plan.  The 600M-row query on two-column join keys (hash-table join):
     rows/s and phases.  300M-row Zipf(1.1) query with (grp, flag) group keys: rows/s
     and G, then the same query with group_cap_hint a quarter of the dim's 10M group keys, which
-    must fail with TABLE_FULL, and its retry with the full hint."""
+    must fail with TABLE_FULL, its retry with the full hint, and the top 100 of its groups by
+    COUNT (sirius_topn_groups over 5.9M groups)."""
     from paper_2508_04701_gb300 import datagen as dg
     stream = torch.cuda.current_stream(dev)
     out = {}
@@ -642,11 +643,16 @@ def run_configs(S, torch, dev, rank):
         first = S.STATUS_NAMES.get(e.status, str(e.status))
     g_retry = S.sirius_run_pipeline(desc, o, scr, stream, sync=True)
     t_retry = time.perf_counter() - t0
+    # ORDER BY COUNT DESC, key LIMIT 100 over the 5.9M groups
+    keys_t, cnt_t = o.t["key"][:g_retry], o.t["count"][:g_retry]
+    tscr = torch.empty(S.lib().sirius_topn_scratch_bytes(100), dtype=torch.uint8, device=dev)
+    us_top = median_us(lambda: S.sirius_topn_groups(keys_t, cnt_t, 100, True, scratch=tscr, stream=stream), 3, 10)
     out["skewed_300M"] = {"rows": spec.n, "groups": g, "ms_per_query": ms, "rows_per_s": spec.n / (ms / 1e3),
                           "aggregates": spec.aggs, "group_keys_in_dim": need,
                           "undersized_hint": {"group_cap_hint": small, "first_status": first, "retries": 1,
                                               "groups_after_retry": g_retry,
-                                              "ms_failed_run_plus_retry": t_retry * 1e3}}
+                                              "ms_failed_run_plus_retry": t_retry * 1e3},
+                          "top100_by_count_us": us_top}
     del fact, dim, desc, desc_s, scr, scr_s, o, o_s
     return out
 

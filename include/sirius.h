@@ -184,6 +184,20 @@ sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_width, const in
                                  int64_t* d_groups, int64_t* h_groups, void* d_scratch,
                                  size_t scratch_bytes, sirius_stream stream);
 
+/* ------------------------------------------------------------------ top N groups
+ * ORDER BY order DESC|ASC, key ASC LIMIT n_top over a group-by result (Sec. 4.2: top-N ends
+ * several of the measured queries): d_out_idx[0 .. min(n_top, g)) receives the positions of the
+ * chosen groups in the input arrays, best first; the caller gathers the columns it wants
+ * (sirius_gather_i64).  d_keys: the g group keys (unique); d_order: the column ordered by (an
+ * aggregate, or the keys themselves).  Ties of the order value go to the smaller key, so the
+ * result is unique.  n_top in [1, 8192].  The count min(n_top, g) goes to *d_count (nullable) and
+ * *h_count (nullable; synchronises).  Scratch: sirius_topn_scratch_bytes(n_top).  Errors:
+ * INVALID, SCRATCH, OOM, CUDA. */
+size_t sirius_topn_scratch_bytes(int64_t n_top);
+sirius_status sirius_topn_groups(const int64_t* d_keys, const int64_t* d_order, int64_t g, int32_t descending,
+                                 int64_t n_top, uint32_t* d_out_idx, int64_t* d_count, int64_t* h_count,
+                                 void* d_scratch, size_t scratch_bytes, sirius_stream stream);
+
 /* ------------------------------------------------------------------ A7: fused pipeline
  * SELECT g, SUM(val), COUNT(*), MIN(val), MAX(val) FROM fact JOIN dim ON fk = pk
  * WHERE pred <op> literal GROUP BY g, with g = dim.grp or (dim.grp, dim.flag).

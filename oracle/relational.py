@@ -221,6 +221,15 @@ def pipeline(fact: Dict[str, np.ndarray], dim: Dict[str, np.ndarray], op: str = 
     return gb(gkey, val)
 
 
+# ------------------------------------------------------------------------------- top N
+def topn(keys: np.ndarray, order: np.ndarray, n: int, descending: bool = True) -> np.ndarray:
+    """ORDER BY order DESC|ASC, key ASC LIMIT n over group-by outputs: the positions of the
+    first n groups (Python's sort on exact integers)."""
+    sign = -1 if descending else 1
+    idx = sorted(range(len(keys)), key=lambda i: (sign * int(order[i]), int(keys[i])))
+    return np.asarray(idx[:n], dtype=np.int64)
+
+
 def merge_partials(parts) -> Dict[str, np.ndarray]:
     """Combine group-by results of disjoint row chunks: SUM and COUNT add, MIN and MAX take
     the extreme (all four aggregates are distributive)."""
@@ -267,6 +276,6 @@ def sort_groups(res: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
     return {k: np.asarray(v)[o] for k, v in res.items()}
 
 
-__all__ = ["OPS", "filter_rows", "filter_rows_loop", "pack_composite", "pack_group", "semi_keep",
+__all__ = ["OPS", "filter_rows", "filter_rows_loop", "pack_composite", "pack_group", "semi_keep", "topn",
            "join_key", "join_sorted", "join_loop", "groupby_agg", "groupby_loop", "pipeline",
            "merge_partials", "restrict_dim", "sort_pairs", "sort_groups"]

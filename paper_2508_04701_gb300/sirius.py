@@ -103,6 +103,8 @@ SIGNATURES = {
     "sirius_gather_i64": (_I32, [_VP, _VP, _I64, _VP, _VP]),
     "sirius_gather_group_key": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP]),
     "sirius_groupby_capacity": (_I64, [_I64]),
+    "sirius_topn_scratch_bytes": (_SZ, [_I64]),
+    "sirius_topn_groups": (_I32, [_VP, _VP, _I64, _I32, _I64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "sirius_groupby_scratch_bytes": (_SZ, [_I64]),
     "sirius_groupby_agg": (_I32, [_VP, _I32, _VP, _I64, _U32, _I64, _VP, _VP, _VP, _VP, _VP,
                                   _I64, _VP, _VP, _VP, _SZ, _VP]),
@@ -287,6 +289,21 @@ def sirius_gather(src: torch.Tensor, idx: torch.Tensor, stream=None) -> torch.Te
         raise TypeError("gather supports int32 and int64 columns")
     _check(st)
     return dst
+
+
+def sirius_topn_groups(keys: torch.Tensor, order: torch.Tensor, n_top: int, descending: bool = True,
+                       scratch: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Positions (int32 tensor, best first) of the n_top groups by (order, key): ORDER BY order
+    DESC|ASC, key ASC LIMIT n_top over group-by outputs; gather columns with sirius_gather."""
+    g = keys.numel()
+    out = torch.empty(max(min(n_top, g), 1), dtype=torch.int32, device=keys.device)
+    if scratch is None:
+        scratch = _scratch(int(lib().sirius_topn_scratch_bytes(n_top)), keys.device)
+    cnt = ctypes.c_int64(0)
+    _check(lib().sirius_topn_groups(_ptr(keys) if g else None, _ptr(order) if g else None, g,
+                                    1 if descending else 0, int(n_top), _ptr(out), None, ctypes.byref(cnt),
+                                    _ptr(scratch), scratch.numel(), _stream(stream)))
+    return out[:cnt.value]
 
 
 def sirius_gather_group_key(grp: torch.Tensor, flag: Optional[torch.Tensor], idx: torch.Tensor,

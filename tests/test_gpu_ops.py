@@ -202,3 +202,39 @@ def test_groupby_capacity(S):
     with pytest.raises(S.SiriusError) as e:
         S.sirius_groupby_agg(dev(keys), dev(vals), group_cap_hint=1000, out_cap=10)
     assert e.value.status == S.ERR_CAPACITY and e.value.needed == 1000
+
+
+# ----------------------------------------------------------------------------- top N groups
+@pytest.mark.parametrize("g", [0, 1, 5, 1000, 100_003, 1_000_000])
+@pytest.mark.parametrize("n_top", [1, 10, 100, 8192])
+def test_topn(S, g, n_top):
+    rng = np.random.default_rng(g + n_top)
+    keys = rng.permutation(np.arange(-g, 4 * g + 1, dtype=np.int64))[:g]
+    order = rng.integers(-50, 50, size=g).astype(np.int64) * (10**15 if g % 2 else 1)  # many ties
+    if g > 2:
+        order[:2] = [np.iinfo(np.int64).min, np.iinfo(np.int64).max]
+    dk, do = torch.from_numpy(keys).cuda(), torch.from_numpy(order).cuda()
+    for desc in (True, False):
+        got = S.sirius_topn_groups(dk, do, n_top, desc).cpu().numpy().astype(np.int64)
+        want = O.topn(keys, order, n_top, desc)
+        assert np.array_equal(got, want), desc
+
+
+def test_topn_of_pipeline_and_errors(S):
+    """ORDER BY SUM DESC, key LIMIT 100 after the fused pipeline, the columns gathered."""
+    spec = dg.plain_scale(n=2_000_000, m=50_000)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    res = S.run_pipeline({k: torch.from_numpy(v).cuda() for k, v in fact.items()},
+                         {k: torch.from_numpy(v).cuda() for k, v in dim.items()}, "lt", spec.t,
+                         group_cap_hint=100_000)
+    pos = S.sirius_topn_groups(res["key"], res["sum"], 100, True)
+    got = {c: S.sirius_gather(res[c], pos).cpu().numpy() for c in res}
+    want = O.pipeline(fact, dim, "lt", spec.t)
+    top = O.topn(want["key"], want["sum"], 100, True)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(got[c], want[c][top]), c
+    k = torch.arange(10, dtype=torch.int64, device="cuda")
+    for bad in (0, 8193):
+        with pytest.raises(S.SiriusError) as e:
+            S.sirius_topn_groups(k, k, bad)
+        assert e.value.status == S.ERR_INVALID

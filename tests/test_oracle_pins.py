@@ -286,6 +286,30 @@ def check_semi_brute(o, seed):
         assert acc[int(k)] == [int(s_), int(c), int(mn), int(mx)], int(k)
 
 
+def check_topn(o, seed):
+    """Top N: against numpy's lexsort (a library routine) on inputs with many ties, and by its
+    invariants: distinct positions, non-increasing order values with ties in ascending key
+    order, nothing outside better than the last one taken."""
+    rng = np.random.default_rng(seed)
+    g = int(rng.integers(0, 400))
+    keys = rng.permutation(np.arange(-200, 10_000, dtype=np.int64))[:g]
+    order = rng.integers(-5, 6, size=g).astype(np.int64) * (10**17 if seed % 3 == 0 else 1)
+    if g and seed % 4 == 0:
+        order[0], keys[0] = np.iinfo(np.int64).min, np.iinfo(np.int64).max
+    for desc in (True, False):
+        n = int(rng.integers(1, 50)) if seed % 5 else g + 7
+        got = o.topn(keys, order, n, desc)
+        ref = np.lexsort((keys, -order.astype(object) if desc else order))[:n]
+        assert got.tolist() == [int(x) for x in ref], (desc, n)
+        assert len(set(got.tolist())) == got.size == min(n, g)
+        vals = [int(order[i]) * (-1 if desc else 1) for i in got]
+        assert all((vals[i], int(keys[got[i]])) < (vals[i + 1], int(keys[got[i + 1]])) for i in range(len(vals) - 1))
+        if got.size and got.size < g:
+            last = (vals[-1], int(keys[got[-1]]))
+            rest = set(range(g)) - set(got.tolist())
+            assert all((int(order[i]) * (-1 if desc else 1), int(keys[i])) > last for i in rest)
+
+
 # ----------------------------------------------------------------------------- the pins
 @pytest.mark.parametrize("seed", range(60))
 def test_filter_brute(seed):
@@ -335,6 +359,11 @@ def test_special_cases():
 @pytest.mark.parametrize("seed", range(5))
 def test_composite_and_group_keys(seed):
     check_composite_and_group_keys(O, seed)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_topn_against_lexsort(seed):
+    check_topn(O, seed)
 
 
 @pytest.mark.parametrize("seed", range(40))
@@ -451,7 +480,19 @@ def _semi_ignores_predicate(fact_keys, dim, op, literal):
     return O.semi_keep(fact_keys, dim, None, literal)
 
 
+def _topn_ascending(keys, order, n, descending=True):
+    return O.topn(keys, order, n, not descending)
+
+
+def _topn_ties_by_larger_key(keys, order, n, descending=True):
+    sign = -1 if descending else 1
+    idx = sorted(range(len(keys)), key=lambda i: (sign * int(order[i]), -int(keys[i])))
+    return np.asarray(idx[:n], dtype=np.int64)
+
+
 MUTANTS = [
+    ("topn ascending for descending", dict(topn=_topn_ascending), lambda m: [check_topn(m, s) for s in range(5)]),
+    ("topn ties by larger key", dict(topn=_topn_ties_by_larger_key), lambda m: [check_topn(m, s) for s in range(5)]),
     ("semi-joins ignored", dict(pipeline=_ignores_semi_joins),
      lambda m: [check_semi_brute(m, s) for s in range(10)]),
     ("semi-join predicate ignored", dict(semi_keep=_semi_ignores_predicate),
