@@ -244,8 +244,9 @@ typedef struct {
                                3510 slots); 2 global reductions; 3 partitioned: the probe pass
                                writes (group slot, value) per joined row, grouped by 4096-slot
                                partition within 4096-row tiles, and a second pass aggregates
-                               each partition in shared memory (group table of at most 2^20
-                               slots); 4 global reductions behind a per-block cache of 2048
+                               each partition in shared memory (group table of at most
+                               2^19 + 1 slots, group_cap_hint <= 2^18; larger tables use 2);
+                               4 global reductions behind a per-block cache of 2048
                                hot groups in shared memory (skewed keys).  Auto: 1 when it
                                fits, else 4 from 1Mi fact rows, else 2 */
   int64_t group_cap_hint;   /* expected distinct group keys in the dim; 0 -> m */
@@ -358,7 +359,7 @@ sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q, sirius_res
  * the call synchronises and fills every results[i].groups / .status.  The return value is the
  * first failing query's status; per-query statuses are in results[i].status.
  * Tuning: rows_per_unit (0 = 65536) is the probe work unit; queries whose group table fits
- * (<= 3072 slots) aggregate each unit in shared memory.  Scratch:
+ * (<= 3510 slots) aggregate each unit in shared memory.  Scratch:
  * sirius_pipeline_batch_scratch_bytes(qs, nq, indexes); queries' tables live at fixed offsets
  * in it, so two batches in flight need two scratch buffers (and two plans). */
 typedef struct sirius_batch_plan_s* sirius_batch_plan;
