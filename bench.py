@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--fifo-seconds", type=float, default=3.0)
+    p.add_argument("--serve-sweep", default="8000,16000,32000,64000",
+                   help="further arrival rates (q/s), one second each, to find where serving saturates")
     return p.parse_args()
 
 
@@ -460,8 +462,22 @@ def run_served(S, torch, args, dev, rank):
     fifo_reqs = [serve.Request(r.rid, r.fact_id, r.t, r.arrival) for r in reqs if r.arrival < args.fifo_seconds]
     serve.sequential_fifo(pool, fifo_reqs)
     fst = serve.latency_stats(fifo_reqs)
+    # the arrival rate swept upwards: throughput follows the offered rate until the GPU (or the
+    # host loop) saturates, then the queue and the p99 grow
+    sweep = []
+    for k, rate in enumerate(float(x) for x in args.serve_sweep.split(",") if x.strip()):
+        rq = serve.poisson_requests(rate, 1.3, len(pool.facts), seed=rank + 1000 + k)
+        srv.run(rq)
+        sw = serve.latency_stats(rq, warmup=0.3)
+        sw["offered_qps"] = rate
+        done = [r for r in rq if r.arrival >= 0.3 and r.done == r.done]  # completed (done is not NaN)
+        span = (max(r.done for r in done) - min(r.arrival for r in done)) if done else 0.0
+        sw["rows_per_s"] = sum(pool.fact_rows[r.fact_id] for r in done) / span if span > 0 else 0.0
+        sw["statuses_ok"] = all(r.status == 0 for r in rq)
+        sweep.append({k2: sw.get(k2) for k2 in ("offered_qps", "throughput_qps", "p50_ms", "p99_ms", "rows_per_s",
+                                                "requests", "statuses_ok")})
     return {"rate_qps": args.serve_rate, "seconds": args.serve_seconds, "served": st,
-            "plain_fifo": fst, "fifo_seconds": args.fifo_seconds}
+            "plain_fifo": fst, "fifo_seconds": args.fifo_seconds, "rate_sweep": sweep}
 
 
 def run_configs(S, torch, dev, rank):
