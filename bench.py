@@ -631,6 +631,26 @@ def run_configs(S, torch, dev, rank):
     del fact, dim, sdims, desc, o, scr
     torch.cuda.empty_cache()
 
+    # ---- group-by alone, hash table vs sort: 100M rows, int32 keys over 1e5 and 1e7 values
+    n = 100_000_000
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    vals = torch.randint(0, 10**8, (n,), dtype=torch.int64, device=dev, generator=gen)
+    gb = {}
+    for dom in (100_000, 10_000_000):
+        keys = torch.randint(0, dom, (n,), dtype=torch.int32, device=dev, generator=gen)
+        res = {}
+        for name, fn in (("hash", lambda: S.sirius_groupby_agg(keys, vals, group_cap_hint=dom, stream=stream)),
+                         ("sort", lambda: S.sirius_groupby_sort(keys, vals, out_cap=dom, stream=stream))):
+            g_ = int(fn()["key"].numel())
+            torch.cuda.synchronize()
+            res[name] = {"ms": median_us(fn, 1, 3) / 1e3, "groups": g_}
+        gb[f"keys_{dom}"] = res
+        del keys
+    out["groupby_hash_vs_sort_100M"] = gb
+    del vals
+    torch.cuda.empty_cache()
+
     # ---- 300M-row Zipf query, 10M group keys
     spec = dg.skewed(seed=rank)
     dim = dg.gen_dim_device(spec, dev)

@@ -184,6 +184,18 @@ sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_width, const in
                                  int64_t* d_groups, int64_t* h_groups, void* d_scratch,
                                  size_t scratch_bytes, sirius_stream stream);
 
+/* Sort-based group-by (Sec. 4.2 sets hash against sort group-by): the same inputs, aggregates,
+ * outputs and errors as sirius_groupby_agg, without a hash table -- the (key, value) pairs are
+ * sorted by key (least-significant-digit radix sort, 8-bit digits; a digit that no two keys
+ * differ in is skipped), then each run of equal keys is reduced.  Groups come out in ascending
+ * key order.  No table limit, so no TABLE_FULL; G > out_cap -> CAPACITY (with h_groups).
+ * Scratch: sirius_groupby_sort_scratch_bytes(n) (about 32 bytes per row). */
+size_t sirius_groupby_sort_scratch_bytes(int64_t n);
+sirius_status sirius_groupby_sort(const void* d_keys, int32_t key_width, const int64_t* d_vals, int64_t n,
+                                  uint32_t aggs, int64_t* d_out_keys, int64_t* d_sum, int64_t* d_count,
+                                  int64_t* d_min, int64_t* d_max, int64_t out_cap, int64_t* d_groups,
+                                  int64_t* h_groups, void* d_scratch, size_t scratch_bytes, sirius_stream stream);
+
 /* ------------------------------------------------------------------ top N groups
  * ORDER BY order DESC|ASC, key ASC LIMIT n_top over a group-by result (Sec. 4.2: top-N ends
  * several of the measured queries): d_out_idx[0 .. min(n_top, g)) receives the positions of the

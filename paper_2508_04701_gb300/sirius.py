@@ -104,6 +104,9 @@ SIGNATURES = {
     "sirius_gather_group_key": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP]),
     "sirius_groupby_capacity": (_I64, [_I64]),
     "sirius_topn_scratch_bytes": (_SZ, [_I64]),
+    "sirius_groupby_sort_scratch_bytes": (_SZ, [_I64]),
+    "sirius_groupby_sort": (_I32, [_VP, _I32, _VP, _I64, _U32, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP,
+                                   _VP, _SZ, _VP]),
     "sirius_topn_groups": (_I32, [_VP, _VP, _I64, _I32, _I64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "sirius_groupby_scratch_bytes": (_SZ, [_I64]),
     "sirius_groupby_agg": (_I32, [_VP, _I32, _VP, _I64, _U32, _I64, _VP, _VP, _VP, _VP, _VP,
@@ -340,6 +343,31 @@ def sirius_groupby_agg(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,m
     h = ctypes.c_int64(0)
     st = lib().sirius_groupby_agg(
         _ptr(keys), kw, _ptr(vals), n, mask, group_cap_hint, _ptr(outs["key"]),
+        _ptr(outs["sum"]) if mask & AGG_SUM else None, _ptr(outs["count"]),
+        _ptr(outs["min"]) if mask & AGG_MIN else None,
+        _ptr(outs["max"]) if mask & AGG_MAX else None, out_cap, None, ctypes.byref(h),
+        _ptr(scratch), scratch.numel(), _stream(stream))
+    _check(st, h.value)
+    g = h.value
+    return {c: t[:g] for c, t in outs.items()}
+
+
+def sirius_groupby_sort(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,min,max",
+                        out_cap: Optional[int] = None, stream=None) -> Dict[str, torch.Tensor]:
+    """The sort-based group-by: the same results as sirius_groupby_agg, groups in ascending
+    key order.  out_cap defaults to the row count (every key distinct at worst)."""
+    n = keys.numel()
+    kw = {torch.int32: 4, torch.int64: 8}[keys.dtype]
+    mask = _agg_mask(aggs)
+    if out_cap is None:
+        out_cap = max(n, 1)
+    dev = keys.device
+    outs = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, device=dev)
+            for c in ("key", "sum", "count", "min", "max")}
+    scratch = _scratch(lib().sirius_groupby_sort_scratch_bytes(n), dev)
+    h = ctypes.c_int64(0)
+    st = lib().sirius_groupby_sort(
+        _ptr(keys) if n else None, kw, _ptr(vals) if n else None, n, mask, _ptr(outs["key"]),
         _ptr(outs["sum"]) if mask & AGG_SUM else None, _ptr(outs["count"]),
         _ptr(outs["min"]) if mask & AGG_MIN else None,
         _ptr(outs["max"]) if mask & AGG_MAX else None, out_cap, None, ctypes.byref(h),

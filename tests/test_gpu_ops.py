@@ -238,3 +238,48 @@ def test_topn_of_pipeline_and_errors(S):
         with pytest.raises(S.SiriusError) as e:
             S.sirius_topn_groups(k, k, bad)
         assert e.value.status == S.ERR_INVALID
+
+
+# ----------------------------------------------------------------------------- sort-based group-by
+@pytest.mark.parametrize("n", [0, 1, 2, 2047, 2048, 2049, 100_003, 3_000_001])
+@pytest.mark.parametrize("dom", [1, 7, 1000, 100_000, None])
+def test_groupby_sort(S, n, dom):
+    """Same results as the definition, groups in ascending key order: int32 keys with
+    negatives, int64 keys with the extreme values, every key distinct (dom None)."""
+    rng = np.random.default_rng(n * 7 + (dom or 3))
+    if dom is None:
+        k32 = rng.permutation(np.arange(-(n // 2), n - n // 2, dtype=np.int64)).astype(np.int32)
+    else:
+        k32 = rng.integers(-dom // 2, dom - dom // 2 + 1, size=n).astype(np.int32)
+    vals = rng.integers(-10**12, 10**12, size=n)
+    for keys in (k32, k32.astype(np.int64) * 1_000_003 + (np.iinfo(np.int64).min // 2 if dom == 7 else 0)):
+        if keys.dtype == np.int64 and n > 2:
+            keys[:2] = [np.iinfo(np.int64).min, np.iinfo(np.int64).max]
+        got = S.sirius_groupby_sort(torch.from_numpy(keys).cuda(), torch.from_numpy(vals).cuda())
+        got = {c: v.cpu().numpy() for c, v in got.items()}
+        want = O.groupby_agg(keys, vals)
+        for c in ("key", "sum", "count", "min", "max"):
+            assert np.array_equal(got[c], want[c]), (keys.dtype, c)
+
+
+def test_groupby_sort_skipped_digits_subsets_and_capacity(S):
+    rng = np.random.default_rng(3)
+    keys = (rng.integers(0, 50, size=500_000).astype(np.int64) << 40) | 0x1234  # only high digits vary
+    vals = rng.integers(0, 10**9, size=500_000)
+    dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals).cuda()
+    want = O.groupby_agg(keys, vals)
+    for aggs in ("sum,count", "count,min", "count,max", "sum,count,min,max"):
+        got = S.sirius_groupby_sort(dk, dv, aggs)
+        for c in ["key", "count"] + [a for a in ("sum", "min", "max") if a in aggs]:
+            assert np.array_equal(got[c].cpu().numpy(), want[c]), (aggs, c)
+    same = S.sirius_groupby_sort(torch.full((10_000,), 42, dtype=torch.int32, device="cuda"),
+                                 torch.ones(10_000, dtype=torch.int64, device="cuda"))
+    assert same["key"].tolist() == [42] and same["count"].tolist() == [10_000] and same["sum"].tolist() == [10_000]
+    with pytest.raises(S.SiriusError) as e:
+        S.sirius_groupby_sort(dk, dv, out_cap=10)
+    assert e.value.status == S.ERR_CAPACITY and e.value.needed == want["key"].size
+    # the hash group-by on the same input gives the same groups
+    h = S.sirius_groupby_agg(dk, dv, group_cap_hint=100)
+    order = torch.argsort(h["key"]).cpu().numpy()
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(h[c].cpu().numpy()[order], want[c]), c
