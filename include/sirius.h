@@ -189,7 +189,9 @@ sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_width, const in
  * sorted by key (least-significant-digit radix sort, 8-bit digits; a digit that no two keys
  * differ in is skipped), then each run of equal keys is reduced.  Groups come out in ascending
  * key order.  No table limit, so no TABLE_FULL; G > out_cap -> CAPACITY (with h_groups).
- * Scratch: sirius_groupby_sort_scratch_bytes(n) (about 32 bytes per row). */
+ * d_vals needs only 8-byte alignment (16-byte aligned values are fetched by bulk copies).
+ * Scratch: sirius_groupby_sort_scratch_bytes(n) (about 32 bytes per row, for either key width).
+ * A bounded device wait that runs out gives TIMEOUT through h_groups and -1 in *d_groups. */
 size_t sirius_groupby_sort_scratch_bytes(int64_t n);
 sirius_status sirius_groupby_sort(const void* d_keys, int32_t key_width, const int64_t* d_vals, int64_t n,
                                   uint32_t aggs, int64_t* d_out_keys, int64_t* d_sum, int64_t* d_count,

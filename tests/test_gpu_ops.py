@@ -278,6 +278,12 @@ def test_groupby_sort_skipped_digits_subsets_and_capacity(S):
     with pytest.raises(S.SiriusError) as e:
         S.sirius_groupby_sort(dk, dv, out_cap=10)
     assert e.value.status == S.ERR_CAPACITY and e.value.needed == want["key"].size
+    # values that start off a 16-byte boundary (no bulk copy for the first pass): same groups
+    sub = S.sirius_groupby_sort(dk[1:], dv[1:])
+    want_sub = O.groupby_agg(keys[1:], vals[1:])
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(sub[c].cpu().numpy(), want_sub[c]), c
+    assert dv[1:].data_ptr() % 16 == 8
     # the hash group-by on the same input gives the same groups
     h = S.sirius_groupby_agg(dk, dv, group_cap_hint=100)
     order = torch.argsort(h["key"]).cpu().numpy()
