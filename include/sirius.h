@@ -198,6 +198,44 @@ sirius_status sirius_groupby_sort(const void* d_keys, int32_t key_width, const i
                                   int64_t* d_min, int64_t* d_max, int64_t out_cap, int64_t* d_groups,
                                   int64_t* h_groups, void* d_scratch, size_t scratch_bytes, sirius_stream stream);
 
+/* ------------------------------------------------------------------ string keys
+ * A string column in the Arrow layout: row i is the bytes d_chars[off[i] .. off[i+1]) with
+ * int32 offsets (n + 1 of them, non-decreasing, within [0, n_chars]); strings compare by bytes.
+ * Rows whose offsets break that rule are skipped and the call returns INVALID (code -1).
+ *
+ * Dictionary encoding (Sec. 4.2: group-by on string keys is a measured bottleneck; the library
+ * path groups them by sorting): codes[i] = c when row i holds the c-th distinct string in
+ * order of first occurrence; d_dict_rows[c] = the first row holding string c (so the rows
+ * come out ascending).  Exact: strings are hashed (64 bits) into an open-addressing table of
+ * sirius_dict_capacity(distinct_hint) strings, and equal hashes are settled by comparing the
+ * bytes.  More distinct strings than that -> TABLE_FULL (retry with a larger hint).
+ * D = the number of distinct strings goes to *d_ndict (-1 after an error) and *h_ndict
+ * (synchronises); D > dict_cap -> CAPACITY with D in *h_ndict.
+ * flags: 0, or SIRIUS_DICT_WEAK_HASH, for tests: an 8-bit hash, so that many distinct strings
+ * share a hash and the byte comparison decides.  Errors: INVALID, TABLE_FULL, CAPACITY,
+ * SCRATCH, OOM, CUDA. */
+#define SIRIUS_DICT_WEAK_HASH 1u
+int64_t sirius_dict_capacity(int64_t distinct_hint);
+size_t sirius_dict_scratch_bytes(int64_t n, int64_t distinct_hint);
+sirius_status sirius_dict_encode(const int32_t* d_offsets, const uint8_t* d_chars, int64_t n_chars, int64_t n,
+                                 int64_t distinct_hint, uint32_t flags, int32_t* d_codes, int64_t* d_dict_rows,
+                                 int64_t dict_cap, int64_t* d_ndict, int64_t* h_ndict, void* d_scratch,
+                                 size_t scratch_bytes, sirius_stream stream);
+
+/* GROUP BY a string column: per distinct string s, SUM / COUNT(*) / MIN / MAX of d_vals (those
+ * in `aggs`; COUNT always), the groups in code order (first occurrence, as sirius_dict_encode
+ * numbers them): d_out_rows[c] = the first row holding string c, d_sum[c] ... its aggregates.
+ * The strings are dictionary-encoded, then the codes go through the hash group-by.  G = D goes
+ * to *d_groups / *h_groups (synchronises); G > out_cap -> CAPACITY with G in *h_groups.
+ * Scratch: sirius_groupby_string_scratch_bytes(n, distinct_hint).  Errors as sirius_dict_encode. */
+size_t sirius_groupby_string_scratch_bytes(int64_t n, int64_t distinct_hint);
+sirius_status sirius_groupby_string(const int32_t* d_offsets, const uint8_t* d_chars, int64_t n_chars,
+                                    const int64_t* d_vals, int64_t n, int64_t distinct_hint, uint32_t flags,
+                                    uint32_t aggs, int64_t* d_out_rows, int64_t* d_sum, int64_t* d_count,
+                                    int64_t* d_min, int64_t* d_max, int64_t out_cap, int64_t* d_groups,
+                                    int64_t* h_groups, void* d_scratch, size_t scratch_bytes,
+                                    sirius_stream stream);
+
 /* ------------------------------------------------------------------ top N groups
  * ORDER BY order DESC|ASC, key ASC LIMIT n_top over a group-by result (Sec. 4.2: top-N ends
  * several of the measured queries): d_out_idx[0 .. min(n_top, g)) receives the positions of the

@@ -6,4 +6,8 @@ The product path (the CUDA library and its Python binding) never touches it and 
 with it.
 """
 from .relational import *  # noqa: F401,F403
-from .relational import __all__  # noqa: F401
+from .relational import __all__ as _rel_all
+from .strings import *  # noqa: F401,F403
+from .strings import __all__ as _str_all
+
+__all__ = list(_rel_all) + list(_str_all)

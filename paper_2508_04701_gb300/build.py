@@ -24,7 +24,7 @@ FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr"]
 
 LIBS = {
-    "libsirius.so": ["api.cu", "filter.cu", "hashjoin.cu", "groupby.cu", "pipeline.cu", "batch.cu", "topn.cu", "sortgroup.cu"],
+    "libsirius.so": ["api.cu", "filter.cu", "hashjoin.cu", "groupby.cu", "pipeline.cu", "batch.cu", "topn.cu", "sortgroup.cu", "strings.cu"],
     "libsirius_datagen.so": ["datagen.cu"],
 }
 

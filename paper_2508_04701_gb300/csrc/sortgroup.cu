@@ -18,7 +18,7 @@
 // every element its group index; a thread reduces its 16 consecutive elements (staged in shared
 // memory) run by run, stores runs that start and end within it, and combines the runs that
 // cross thread boundaries within the warp before one set of atomics per run.
-#include "tables.cuh"
+#include "scan.cuh"
 
 namespace sirius {
 namespace {
@@ -28,8 +28,6 @@ constexpr int kSgWarps = kSgThreads / 32;
 constexpr int kSgItems = 16;                       // keys per thread and tile
 constexpr int kSgTile = kSgThreads * kSgItems;     // 4096
 constexpr int kSgWarpSpan = kSgTile / kSgWarps;    // 512 consecutive keys ranked by one warp
-constexpr int kSgScanThreads = 1024;
-constexpr int kSgScanSeg = 4096;                   // entries per block of the multi-block scan
 
 struct SgHeader {
   unsigned long long diff;       // OR over keys of (key ^ key[0]): the bits that vary
@@ -152,76 +150,6 @@ sg_upfront_kernel(const K* __restrict__ in, int64_t n, SgHeader* h, unsigned lon
     uint32_t c = 0;
     for (int q = 0; q < kC; ++q) c += hs[(p * kC + q) * 256 + threadIdx.x];
     if (c) atomicAdd(&gcount[p * 256 + threadIdx.x], (unsigned long long)c);
-  }
-}
-
-// Multi-block exclusive scan of m 32-bit counts in place (three launches): partial sums per
-// segment, their scan in one block, then each segment scanned with its base added.
-__global__ void __launch_bounds__(kSgScanThreads)
-sg_scan_partials_kernel(const uint32_t* a, int64_t m, const SgHeader* h, int pass, unsigned long long* part) {
-  if (pass >= 0 && pass_skipped(h, pass)) return;
-  __shared__ unsigned long long s[kSgScanThreads / 32];
-  unsigned long long acc = 0;
-  const int64_t base = (int64_t)blockIdx.x * kSgScanSeg;
-  for (int64_t i = base + threadIdx.x; i < base + kSgScanSeg && i < m; i += blockDim.x) acc += a[i];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long t = 0;
-    for (int w = 0; w < kSgScanThreads / 32; ++w) t += s[w];
-    part[blockIdx.x] = t;
-  }
-}
-
-__global__ void __launch_bounds__(kSgScanThreads)
-sg_scan_top_kernel(unsigned long long* part, int64_t nb, const SgHeader* h, int pass, unsigned long long* total) {
-  if (pass >= 0 && pass_skipped(h, pass)) return;
-  __shared__ unsigned long long s[kSgScanThreads];
-  unsigned long long carry = 0;
-  for (int64_t b0 = 0; b0 < nb; b0 += kSgScanThreads) {
-    const int64_t i = b0 + threadIdx.x;
-    const unsigned long long v = i < nb ? part[i] : 0ull;
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < kSgScanThreads; o <<= 1) {
-      const unsigned long long x = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0ull;
-      __syncthreads();
-      s[threadIdx.x] += x;
-      __syncthreads();
-    }
-    if (i < nb) part[i] = carry + s[threadIdx.x] - v;  // exclusive
-    const unsigned long long blk = s[kSgScanThreads - 1];
-    __syncthreads();
-    carry += blk;
-  }
-  if (threadIdx.x == 0 && total) *total = carry;
-}
-
-__global__ void __launch_bounds__(kSgScanThreads)
-sg_scan_apply_kernel(uint32_t* a, int64_t m, const unsigned long long* part, const SgHeader* h, int pass) {
-  if (pass >= 0 && pass_skipped(h, pass)) return;
-  // segment of kSgScanSeg entries: 4 per thread, thread-local sums, block scan of those
-  __shared__ unsigned long long s[kSgScanThreads];
-  const int64_t base = (int64_t)blockIdx.x * kSgScanSeg + (int64_t)threadIdx.x * 4;
-  uint32_t v[4];
-  unsigned long long loc = 0;
-  for (int j = 0; j < 4; ++j) {
-    v[j] = base + j < m ? a[base + j] : 0u;
-    loc += v[j];
-  }
-  s[threadIdx.x] = loc;
-  __syncthreads();
-  for (int o = 1; o < kSgScanThreads; o <<= 1) {
-    const unsigned long long x = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0ull;
-    __syncthreads();
-    s[threadIdx.x] += x;
-    __syncthreads();
-  }
-  unsigned long long run = part[blockIdx.x] + s[threadIdx.x] - loc;
-  for (int j = 0; j < 4; ++j) {
-    if (base + j < m) a[base + j] = (uint32_t)run;
-    run += v[j];
   }
 }
 
@@ -614,7 +542,7 @@ struct SgLayout {
 SgLayout sg_layout(int64_t n, int key_width) {
   const int64_t nn = n > 0 ? n : 1;
   const int64_t ntiles = (nn + kSgTile - 1) / kSgTile;
-  const int64_t nb = (ntiles + kSgScanSeg - 1) / kSgScanSeg;
+  const int64_t nb = scan_part_entries(ntiles);
   SgLayout L;
   size_t off = align_up(256 + (size_t)nn * key_width, 256);  // header, keys buffer 0
   L.k1 = off;
@@ -632,18 +560,6 @@ SgLayout sg_layout(int64_t n, int key_width) {
   L.part = off;
   L.total = align_up(off + (size_t)nb * 8, 256);
   return L;
-}
-
-sirius_status sg_scan(uint32_t* a, int64_t m, unsigned long long* part, const SgHeader* h, int pass,
-                      unsigned long long* total, cudaStream_t s) {
-  const int64_t nb = (m + kSgScanSeg - 1) / kSgScanSeg;
-  sg_scan_partials_kernel<<<(unsigned)nb, kSgScanThreads, 0, s>>>(a, m, h, pass, part);
-  SIRIUS_LAUNCH_CHECK();
-  sg_scan_top_kernel<<<1, kSgScanThreads, 0, s>>>(part, nb, h, pass, total);
-  SIRIUS_LAUNCH_CHECK();
-  sg_scan_apply_kernel<<<(unsigned)nb, kSgScanThreads, 0, s>>>(a, m, part, h, pass);
-  SIRIUS_LAUNCH_CHECK();
-  return SIRIUS_OK;
 }
 
 __global__ void sg_copy_groups_kernel(const SgHeader* h, int64_t* d_groups) {
@@ -695,7 +611,7 @@ sirius_status sg_run(const void* d_keys, const int64_t* d_vals, int64_t n, const
   }
   sg_heads_kernel<K><<<(unsigned)ntiles, kSgThreads, 0, s>>>(b, n, hdr, cnt);
   SIRIUS_LAUNCH_CHECK();
-  if ((st = sg_scan(cnt, ntiles, part, hdr, -1, &hdr->groups, s)) != SIRIUS_OK) return st;
+  if ((st = exclusive_scan_u32(cnt, ntiles, part, &hdr->groups, s)) != SIRIUS_OK) return st;
   sg_init_out_kernel<<<grid_for(o.cap > 0 ? o.cap : 1, 256), 256, 0, s>>>(o, hdr);
   SIRIUS_LAUNCH_CHECK();
   sg_reduce_kernel<K><<<(unsigned)ntiles, kSgThreads, kSgReduceSmem(sizeof(K)), s>>>(b, n, hdr, cnt, o);

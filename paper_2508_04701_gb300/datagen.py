@@ -407,3 +407,99 @@ def gen_semi_dims_device(spec: StarSpec, device="cuda"):
                     "attr": _dbounded(stream_base(spec.seed, T, C_DATTR), 0, spec.semi_m, 100, device,
                                       torch.int32)})
     return out
+
+
+# ----------------------------------------------------------------------------- string columns
+# A string column (Arrow layout: int32 offsets[n + 1], uint8 chars) of n rows over d distinct
+# strings.  String k is `p#k`: a prefix p of 0..12 lowercase letters, '#', then k in decimal
+# (no letter or '#' among the digits, so the d strings are distinct).  Row i holds string
+# id_i = bounded(elem(seed, STR_TABLE, C_SID, i), d), uniform; its value is
+# bounded(elem(seed, STR_TABLE, C_SVAL, i), val_bound).  Prefix length of string k:
+# bounded(elem(.., C_SLEN, k), 13); its letter j: 'a' + bounded(elem(.., C_SCHAR, 13 k + j), 26).
+STR_TABLE = 0x10000
+C_SLEN, C_SCHAR, C_SID, C_SVAL = 0, 1, 2, 3
+STR_PREFIX_MAX = 12
+
+
+@dataclasses.dataclass(frozen=True)
+class StringSpec:
+    n: int
+    d: int
+    seed: int = 0
+    val_bound: int = 1_000_000
+
+
+def strcol_from_list(strs) -> tuple:
+    """(offsets int32[n + 1], chars uint8) of a list of bytes objects."""
+    lens = np.array([len(s) for s in strs], dtype=np.int64)
+    off = np.zeros(len(strs) + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    assert off[-1] < (1 << 31)
+    chars = np.frombuffer(b"".join(strs), dtype=np.uint8).copy()
+    return off.astype(np.int32), chars
+
+
+def string_dict_host(spec: StringSpec) -> tuple:
+    """The d distinct strings: (offsets int64[d + 1], chars uint8)."""
+    d = spec.d
+    k = np.arange(d, dtype=np.int64)
+    plen = bounded(stream(spec.seed, STR_TABLE, C_SLEN, 0, d), STR_PREFIX_MAX + 1)
+    letters = (97 + bounded(stream(spec.seed, STR_TABLE, C_SCHAR, 0, d * (STR_PREFIX_MAX + 1)), 26)
+               ).astype(np.uint8).reshape(d, STR_PREFIX_MAX + 1)
+    ndig = np.ones(d, dtype=np.int64)
+    for p in range(1, 20):
+        ndig += (k >= 10 ** p)
+    lens = plen + 1 + ndig
+    off = np.zeros(d + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    chars = np.empty(int(off[-1]), dtype=np.uint8)
+    for j in range(STR_PREFIX_MAX):
+        m = plen > j
+        chars[off[:-1][m] + j] = letters[m, j]
+    chars[off[:-1] + plen] = ord("#")
+    for t in range(int(ndig.max()) if d else 0):
+        m = ndig > t
+        digit = (k[m] // (10 ** (ndig[m] - 1 - t))) % 10
+        chars[off[:-1][m] + plen[m] + 1 + t] = (48 + digit).astype(np.uint8)
+    return off, chars
+
+
+def _rows_from_ids(ids, lens, doff, dchars, xp, repeat, arange):
+    n = ids.shape[0]
+    rl = lens[ids]
+    off = arange(n + 1) * 0
+    off[1:] = xp.cumsum(rl, 0)
+    total = int(off[-1])
+    assert total < (1 << 31), "a string column holds fewer than 2**31 bytes (int32 offsets)"
+    row = repeat(rl)
+    pos = doff[ids][row] + (arange(total) - off[:-1][row])
+    return off, dchars[pos]
+
+
+def gen_strings_host(spec: StringSpec) -> Dict[str, np.ndarray]:
+    """Rows: offsets int32[n + 1], chars uint8, vals int64, ids int64 (the string of each row)."""
+    doff, dchars = string_dict_host(spec)
+    ids = bounded(stream(spec.seed, STR_TABLE, C_SID, 0, spec.n), spec.d)
+    vals = bounded(stream(spec.seed, STR_TABLE, C_SVAL, 0, spec.n), spec.val_bound)
+    lens = np.diff(doff)
+    off, chars = _rows_from_ids(ids, lens, doff, dchars, np,
+                                lambda rl: np.repeat(np.arange(spec.n, dtype=np.int64), rl),
+                                lambda t: np.arange(t, dtype=np.int64))
+    return {"offsets": off.astype(np.int32), "chars": chars, "vals": vals, "ids": ids}
+
+
+def gen_strings_device(spec: StringSpec, device="cuda"):
+    """The same columns as gen_strings_host, as device tensors (ids and values drawn by the CUDA
+    twin of the streams; the dictionary of d strings made on the host)."""
+    import torch
+    doff_h, dchars_h = string_dict_host(spec)
+    doff = torch.from_numpy(doff_h).to(device)
+    dchars = torch.from_numpy(dchars_h).to(device)
+    ids = _dbounded(stream_base(spec.seed, STR_TABLE, C_SID), 0, spec.n, spec.d, device, torch.int64)
+    vals = _dbounded(stream_base(spec.seed, STR_TABLE, C_SVAL), 0, spec.n, spec.val_bound, device, torch.int64)
+    lens = doff[1:] - doff[:-1]
+    off, chars = _rows_from_ids(
+        ids, lens, doff, dchars, torch,
+        lambda rl: torch.repeat_interleave(torch.arange(spec.n, dtype=torch.int64, device=device), rl),
+        lambda t: torch.arange(t, dtype=torch.int64, device=device))
+    return {"offsets": off.to(torch.int32), "chars": chars, "vals": vals, "ids": ids}

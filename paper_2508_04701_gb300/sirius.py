@@ -108,6 +108,13 @@ SIGNATURES = {
     "sirius_groupby_sort": (_I32, [_VP, _I32, _VP, _I64, _U32, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP,
                                    _VP, _SZ, _VP]),
     "sirius_topn_groups": (_I32, [_VP, _VP, _I64, _I32, _I64, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "sirius_dict_capacity": (_I64, [_I64]),
+    "sirius_dict_scratch_bytes": (_SZ, [_I64, _I64]),
+    "sirius_dict_encode": (_I32, [_VP, _VP, _I64, _I64, _I64, _U32, _VP, _VP, _I64, _VP, _VP, _VP, _SZ,
+                                  _VP]),
+    "sirius_groupby_string_scratch_bytes": (_SZ, [_I64, _I64]),
+    "sirius_groupby_string": (_I32, [_VP, _VP, _I64, _VP, _I64, _I64, _U32, _U32, _VP, _VP, _VP, _VP, _VP,
+                                     _I64, _VP, _VP, _VP, _SZ, _VP]),
     "sirius_groupby_scratch_bytes": (_SZ, [_I64]),
     "sirius_groupby_agg": (_I32, [_VP, _I32, _VP, _I64, _U32, _I64, _VP, _VP, _VP, _VP, _VP,
                                   _I64, _VP, _VP, _VP, _SZ, _VP]),
@@ -375,6 +382,61 @@ def sirius_groupby_sort(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,
     _check(st, h.value)
     g = h.value
     return {c: t[:g] for c, t in outs.items()}
+
+
+# ---------------------------------------------------------------------------- string keys
+DICT_WEAK_HASH = 1
+
+
+def _strcol(offsets: torch.Tensor, chars: torch.Tensor):
+    if offsets.dtype != torch.int32 or chars.dtype != torch.uint8:
+        raise ValueError("a string column is int32 offsets (n + 1) and uint8 chars")
+    if offsets.numel() < 1:
+        raise ValueError("offsets hold n + 1 entries")
+    return offsets.numel() - 1, chars.numel()
+
+
+def sirius_dict_encode(offsets: torch.Tensor, chars: torch.Tensor, distinct_hint: int = 1024,
+                       weak_hash: bool = False, dict_cap: Optional[int] = None, stream=None):
+    """Codes of a string column in order of first occurrence: (codes int32[n], dict_rows
+    int64[D]) with dict_rows[c] the first row holding string c."""
+    n, n_chars = _strcol(offsets, chars)
+    dev = offsets.device
+    if dict_cap is None:
+        dict_cap = int(lib().sirius_dict_capacity(distinct_hint))
+    codes = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    rows = torch.empty(max(dict_cap, 1), dtype=torch.int64, device=dev)
+    scratch = _scratch(lib().sirius_dict_scratch_bytes(n, distinct_hint), dev)
+    h = ctypes.c_int64(0)
+    st = lib().sirius_dict_encode(_ptr(offsets), _ptr(chars) if n_chars else None, n_chars, n, distinct_hint,
+                                  DICT_WEAK_HASH if weak_hash else 0, _ptr(codes), _ptr(rows), dict_cap, None,
+                                  ctypes.byref(h), _ptr(scratch), scratch.numel(), _stream(stream))
+    _check(st, h.value)
+    return codes[:n], rows[:h.value]
+
+
+def sirius_groupby_string(offsets: torch.Tensor, chars: torch.Tensor, vals: torch.Tensor,
+                          aggs="sum,count,min,max", distinct_hint: int = 1024, weak_hash: bool = False,
+                          out_cap: Optional[int] = None, stream=None) -> Dict[str, torch.Tensor]:
+    """GROUP BY a string column, groups in order of first occurrence: 'row' (the first row
+    holding the group's string), 'sum', 'count', 'min', 'max'."""
+    n, n_chars = _strcol(offsets, chars)
+    mask = _agg_mask(aggs)
+    dev = offsets.device
+    if out_cap is None:
+        out_cap = int(lib().sirius_dict_capacity(distinct_hint))
+    outs = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, device=dev)
+            for c in ("row", "sum", "count", "min", "max")}
+    scratch = _scratch(lib().sirius_groupby_string_scratch_bytes(n, distinct_hint), dev)
+    h = ctypes.c_int64(0)
+    st = lib().sirius_groupby_string(
+        _ptr(offsets), _ptr(chars) if n_chars else None, n_chars, _ptr(vals) if n else None, n, distinct_hint,
+        DICT_WEAK_HASH if weak_hash else 0, mask, _ptr(outs["row"]),
+        _ptr(outs["sum"]) if mask & AGG_SUM else None, _ptr(outs["count"]),
+        _ptr(outs["min"]) if mask & AGG_MIN else None, _ptr(outs["max"]) if mask & AGG_MAX else None,
+        out_cap, None, ctypes.byref(h), _ptr(scratch), scratch.numel(), _stream(stream))
+    _check(st, h.value)
+    return {c: t[:h.value] for c, t in outs.items()}
 
 
 # ---------------------------------------------------------------------------- A7: pipeline

@@ -124,3 +124,18 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_string_calls_reject_bad_arguments_on_the_host(lib):
+    from paper_2508_04701_gb300 import sirius as S
+    h = ctypes.c_int64(0)
+    enc = lib.sirius_dict_encode
+    assert enc(None, None, 0, 5, 10, 0, None, None, 0, None, ctypes.byref(h), None, 0, None) == S.ERR_INVALID
+    assert enc(None, None, 0, 0, 10, 2, None, None, 0, None, ctypes.byref(h), None, 0, None) == S.ERR_INVALID
+    assert enc(None, None, 1 << 31, 0, 10, 0, None, None, 0, None, None, None, 0, None) == S.ERR_INVALID
+    assert enc(None, None, 0, -1, 10, 0, None, None, 0, None, None, None, 0, None) == S.ERR_INVALID
+    gb = lib.sirius_groupby_string
+    assert gb(None, None, 0, None, 0, 10, 0, 15, None, None, None, None, None, 0, None, None, None, 0,
+              None) == S.ERR_INVALID  # NULL count output
+    assert lib.sirius_dict_capacity(1000) >= 1000
+    assert lib.sirius_groupby_string_scratch_bytes(10**6, 1000) > lib.sirius_dict_scratch_bytes(10**6, 1000)

@@ -119,3 +119,27 @@ def test_batch_query_sizes():
     assert ts.min() >= 5 and ts.max() <= 90
     # log-uniform: mean of N = 1e4 * 1999 / ln 2000 ~ 2.63M (loose, 512 draws)
     assert 1.5e6 < ns.mean() < 4e6
+
+
+def test_string_dictionary_format_and_distinct():
+    import re
+    sp = dg.StringSpec(n=10, d=20_000, seed=5)
+    off, chars = dg.string_dict_host(sp)
+    strs = [bytes(chars[off[i]:off[i + 1]]) for i in range(sp.d)]
+    assert len(set(strs)) == sp.d
+    pat = re.compile(rb"^[a-z]{0,12}#(\d+)$")
+    for k, s in enumerate(strs):
+        m = pat.match(s)
+        assert m and int(m.group(1)) == k
+
+
+def test_string_rows_follow_ids():
+    sp = dg.StringSpec(n=5_000, d=300, seed=2)
+    r = dg.gen_strings_host(sp)
+    off, chars = dg.string_dict_host(sp)
+    dstr = [bytes(chars[off[i]:off[i + 1]]) for i in range(sp.d)]
+    o, c = r["offsets"], r["chars"]
+    assert o.dtype == np.int32 and c.dtype == np.uint8 and o[0] == 0 and o[-1] == c.size
+    assert [bytes(c[o[i]:o[i + 1]]) for i in range(sp.n)] == [dstr[k] for k in r["ids"]]
+    assert r["ids"].min() >= 0 and r["ids"].max() < sp.d and r["vals"].max() < sp.val_bound
+    assert np.array_equal(r["ids"], dg.bounded(dg.stream(sp.seed, dg.STR_TABLE, dg.C_SID, 0, sp.n), sp.d))

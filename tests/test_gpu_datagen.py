@@ -57,3 +57,11 @@ def test_star_filter_dims_match_host():
     df = dg.gen_fact_device(spec)
     for k in ("sk0", "sk1"):
         assert np.array_equal(hf[k], df[k].cpu().numpy()), k
+
+
+@pytest.mark.parametrize("n,d", [(1, 1), (100_003, 5000)])
+def test_string_columns_match_host(n, d):
+    spec = dg.StringSpec(n=n, d=d, seed=9)
+    h, dv = dg.gen_strings_host(spec), dg.gen_strings_device(spec)
+    for k in ("offsets", "chars", "vals", "ids"):
+        assert np.array_equal(h[k], dv[k].cpu().numpy()), k

@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_2508_04701_gb300 import datagen as dg
 
 
 # ----------------------------------------------------------------------------- checks
@@ -401,6 +402,68 @@ def test_restrict_dim_selects_groups():
         assert np.array_equal(part[c], full[c][keep])
 
 
+# ----------------------------------------------------------------------------- string keys
+def _tiny_strcol(rng, n):
+    """Strings of 0..4 bytes over a 3-letter alphabet: duplicates, prefixes, the empty string."""
+    strs = [bytes(rng.choice(list(b"abz"), size=int(rng.integers(0, 5))).tolist()) for _ in range(n)]
+    return strs
+
+
+def check_dict_brute(m, seed):
+    """Codes by the definition, O(n^2): code_i = the number of distinct strings among the rows
+    before the first row holding s_i; the dictionary lists those first rows."""
+    rng = np.random.default_rng(seed)
+    strs = _tiny_strcol(rng, int(rng.integers(1, 40)))
+    off, chars = dg.strcol_from_list(strs)
+    if seed % 2:  # a slice of a longer column: offsets need not start at 0
+        off, chars = (off + 3).astype(np.int32), np.concatenate([np.frombuffer(b"xyz", np.uint8), chars])
+    codes, rows = m.dict_encode(off, chars)
+    n = len(strs)
+    first = [min(j for j in range(n) if strs[j] == strs[i]) for i in range(n)]
+    want = [len({strs[j] for j in range(first[i])}) for i in range(n)]
+    assert codes.tolist() == want
+    assert rows.tolist() == sorted(set(first))
+
+
+def check_groupby_string_vs_ints(m, seed):
+    """Strings written from integer keys (decimal, so one string per key): the same groups and
+    aggregates as the integer group-by, each group's row its key's first row."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 300))
+    k = rng.integers(-20, 20, size=n)
+    v = rng.integers(-10**6, 10**6, size=n)
+    off, chars = dg.strcol_from_list([str(int(x)).encode() for x in k])
+    got = m.groupby_string(off, chars, v)
+    want = O.groupby_agg(k, v)
+    keys = k[got["row"]]
+    order = np.argsort(keys)
+    assert np.array_equal(keys[order], want["key"])
+    for c in ("sum", "count", "min", "max"):
+        assert np.array_equal(got[c][order], want[c]), c
+    assert all(int(np.flatnonzero(k == k[r])[0]) == int(r) for r in got["row"])
+    assert np.all(np.diff(got["row"]) > 0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_dict_encode_brute(seed):
+    check_dict_brute(O, seed)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_groupby_string_against_integer_keys(seed):
+    check_groupby_string_vs_ints(O, seed)
+
+
+def test_dict_encode_special_cases():
+    codes, rows = O.dict_encode(np.zeros(1, np.int32), np.zeros(0, np.uint8))      # no rows
+    assert codes.size == 0 and rows.size == 0
+    codes, rows = O.dict_encode(np.zeros(6, np.int32), np.zeros(0, np.uint8))      # five empty strings
+    assert codes.tolist() == [0] * 5 and rows.tolist() == [0]
+    off, chars = dg.strcol_from_list([b"a\x00", b"a", b"a\x00", b"\xff", b"a"])     # bytes, not text
+    codes, rows = O.dict_encode(off, chars)
+    assert codes.tolist() == [0, 1, 0, 2, 1] and rows.tolist() == [0, 1, 3]
+
+
 # ----------------------------------------------------------------------------- planted mistakes
 def _mutant(**over):
     """A copy of the oracle's public functions with some replaced by broken versions."""
@@ -490,7 +553,31 @@ def _topn_ties_by_larger_key(keys, order, n, descending=True):
     return np.asarray(idx[:n], dtype=np.int64)
 
 
+def _dict_last_occurrence(offsets, chars):
+    strs = O.strings_of(offsets, chars)
+    rev_codes, rev_rows = O.dict_encode(*dg.strcol_from_list(strs[::-1]))
+    n = len(strs)
+    return rev_codes[::-1].copy(), np.sort(n - 1 - rev_rows)
+
+
+def _dict_prefix2(offsets, chars):
+    strs = [s[:2] for s in O.strings_of(offsets, chars)]   # compares only two bytes
+    return O.dict_encode(*dg.strcol_from_list(strs))
+
+
+def _groupby_string_max_is_min(offsets, chars, vals):
+    r = O.groupby_string(offsets, chars, vals)
+    r["max"] = r["min"]
+    return r
+
+
 MUTANTS = [
+    ("dictionary by last occurrence", dict(dict_encode=_dict_last_occurrence),
+     lambda m: [check_dict_brute(m, s) for s in range(12)]),
+    ("dictionary compares a prefix", dict(dict_encode=_dict_prefix2),
+     lambda m: [check_dict_brute(m, s) for s in range(12)]),
+    ("string group-by max is min", dict(groupby_string=_groupby_string_max_is_min),
+     lambda m: [check_groupby_string_vs_ints(m, s) for s in range(6)]),
     ("topn ascending for descending", dict(topn=_topn_ascending), lambda m: [check_topn(m, s) for s in range(5)]),
     ("topn ties by larger key", dict(topn=_topn_ties_by_larger_key), lambda m: [check_topn(m, s) for s in range(5)]),
     ("semi-joins ignored", dict(pipeline=_ignores_semi_joins),
