@@ -651,6 +651,26 @@ def run_configs(S, torch, dev, rank):
     del vals
     torch.cuda.empty_cache()
 
+    # ---- string keys: 50M rows over 1e5 and 1e6 distinct strings (2..20 bytes, mean ~12)
+    sg = {}
+    for d in (100_000, 1_000_000):
+        col = dg.gen_strings_device(dg.StringSpec(n=50_000_000, d=d, seed=rank), dev)
+        off, ch, v = col["offsets"], col["chars"], col["vals"]
+        ids32 = col["ids"].to(torch.int32)
+        res = {"rows": int(v.numel()), "chars_bytes": int(ch.numel())}
+        for name, fn in (
+                ("dict_encode", lambda: S.sirius_dict_encode(off, ch, distinct_hint=d, stream=stream)),
+                ("groupby_string", lambda: S.sirius_groupby_string(off, ch, v, distinct_hint=d, stream=stream)),
+                ("groupby_int_hash_same_ids", lambda: S.sirius_groupby_agg(ids32, v, group_cap_hint=d, stream=stream)),
+                ("groupby_int_sort_same_ids", lambda: S.sirius_groupby_sort(ids32, v, out_cap=d, stream=stream))):
+            res[name + "_ms"] = median_us(fn, 1, 3) / 1e3
+        res["groupby_string_rows_per_s"] = res["rows"] / (res["groupby_string_ms"] / 1e3)
+        res["groups"] = int(S.sirius_groupby_string(off, ch, v, distinct_hint=d, stream=stream)["row"].numel())
+        sg[f"distinct_{d}"] = res
+        del col, off, ch, v, ids32
+        torch.cuda.empty_cache()
+    out["groupby_string_50M"] = sg
+
     # ---- 300M-row Zipf query, 10M group keys
     spec = dg.skewed(seed=rank)
     dim = dg.gen_dim_device(spec, dev)

@@ -206,9 +206,10 @@ sirius_status sirius_groupby_sort(const void* d_keys, int32_t key_width, const i
  * Dictionary encoding (Sec. 4.2: group-by on string keys is a measured bottleneck; the library
  * path groups them by sorting): codes[i] = c when row i holds the c-th distinct string in
  * order of first occurrence; d_dict_rows[c] = the first row holding string c (so the rows
- * come out ascending).  Exact: strings are hashed (64 bits) into an open-addressing table of
+ * come out ascending).  Exact: strings are hashed (32 bits) into an open-addressing table of
  * sirius_dict_capacity(distinct_hint) strings, and equal hashes are settled by comparing the
  * bytes.  More distinct strings than that -> TABLE_FULL (retry with a larger hint).
+ * distinct_hint <= 2^31.
  * D = the number of distinct strings goes to *d_ndict (-1 after an error) and *h_ndict
  * (synchronises); D > dict_cap -> CAPACITY with D in *h_ndict.
  * flags: 0, or SIRIUS_DICT_WEAK_HASH, for tests: an 8-bit hash, so that many distinct strings

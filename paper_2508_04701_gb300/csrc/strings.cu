@@ -2,7 +2,7 @@
 // library path grouping them by sorting).  The GB300 path hashes each string once into a
 // dictionary of dense int32 codes and groups the codes with the integer group-by.
 //
-// Dictionary encoding, exact: a string's 64-bit hash (below) selects a slot of an
+// Dictionary encoding, exact: a string's 32-bit hash (below) selects a slot of an
 // open-addressing table; a slot holds (hash, where the representative's bytes are) and is
 // claimed by a 128-bit compare-and-swap, so the pair is never seen half written.  A row whose
 // hash equals a slot's compares its bytes with the representative's: equal -> the same string;
@@ -11,21 +11,21 @@
 // the first rows are marked in a bitmap over the rows, and a string's code is the number of
 // marks before its first row (an exclusive scan of the bitmap words' popcounts).
 //
-// String hash: the bytes are taken 8 at a time as little-endian words (the tail zero-padded);
-// each word, finalized by MurmurHash3's fmix64, is xored into the state, which is multiplied
-// by the 64-bit FNV prime and rotated; the length and a last fmix64 close it.
+// String hash (32 bits; the table settles equality by bytes, so the hash only picks the slot
+// and filters): the bytes as 4-byte little-endian words, the tail zero-padded, each mixed in by
+// the body round of MurmurHash3_x86_32 (Austin Appleby, public domain); the length and that
+// hash's finalizer close it.  The home slot is the hash scaled to the table by a multiply-high.
 #include "scan.cuh"
 
 namespace sirius {
 namespace {
 
 constexpr int kDictThreads = 256;
-constexpr uint64_t kFnvPrime = 0x100000001B3ull;
 
 struct DictHeader {
   int32_t status;
   uint32_t pad0;
-  unsigned long long claimed;  // slots taken
+  unsigned long long pad1;
   unsigned long long ndict;    // D, the number of distinct strings
   unsigned long long groups;   // string group-by: G (= D)
   unsigned long long pad[28];
@@ -39,7 +39,16 @@ struct __align__(16) DictSlot {
   unsigned long long rep;
 };
 
-__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+__device__ __forceinline__ uint32_t mm3_round(uint32_t h, uint32_t k) {
+  k *= 0xcc9e2d51u;
+  k = rotl32(k, 15);
+  k *= 0x1b873593u;
+  h ^= k;
+  h = rotl32(h, 13);
+  return h * 5u + 0xe6546b64u;
+}
 
 // Word j of a string: its bytes 8j .. 8j+7 as a little-endian word, zero past the end.  Read
 // as the one or two aligned 8-byte words that hold those bytes -- only words holding at least
@@ -55,16 +64,17 @@ __device__ __forceinline__ uint64_t str_word(const uint8_t* p, int len, int j) {
   return v;
 }
 
-__device__ uint64_t str_hash(const uint8_t* p, int len, bool weak) {
-  uint64_t h = 0x243F6A8885A308D3ull;
+__device__ uint32_t str_hash(const uint8_t* p, int len, bool weak) {
+  uint32_t h = 0x9747b28cu;
   const int words = (len + 7) >> 3;
   for (int j = 0; j < words; ++j) {
-    const uint64_t w = str_word(p, len, j) ^ (8 * j + 8 > len ? 0xA5A5A5A5A5A5A5A5ull : 0ull);
-    h = rotl64((h ^ fmix64(w)) * kFnvPrime, 31);
+    const uint64_t w = str_word(p, len, j);
+    h = mm3_round(h, (uint32_t)w);
+    if (8 * j + 4 < len) h = mm3_round(h, (uint32_t)(w >> 32));
   }
-  h = fmix64(h ^ (uint64_t)len);
-  if (weak) h = (h & 0xFFull) + 1;  // 256 values: distinct strings share hashes (tests)
-  return h ? h : 1;
+  h = fmix32(h ^ (uint32_t)len);
+  if (weak) h = (h & 0xFFu) + 1u;  // 256 values: distinct strings share hashes (tests)
+  return h ? h : 1u;
 }
 
 __device__ __forceinline__ bool str_equal(const uint8_t* a, const uint8_t* b, int len) {
@@ -94,8 +104,8 @@ __device__ __forceinline__ bool str_bounds(const StrCol& c, int64_t i, int32_t* 
 }
 
 __global__ void __launch_bounds__(kDictThreads)
-dict_insert_kernel(StrCol c, DictSlot* slots, uint32_t* smin, int64_t cap, unsigned long long limit,
-                   uint32_t* row_slot, DictHeader* hdr, int weak) {
+dict_insert_kernel(StrCol c, DictSlot* slots, uint32_t* smin, int64_t cap, uint32_t* row_slot, DictHeader* hdr,
+                   int weak) {
   const uint64_t mask = (uint64_t)cap - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t a, len;
@@ -103,30 +113,40 @@ dict_insert_kernel(StrCol c, DictSlot* slots, uint32_t* smin, int64_t cap, unsig
     if (str_bounds(c, i, &a, &len, &hdr->status)) {
       const uint8_t* p = c.chars + a;
       const uint64_t h = str_hash(p, len, weak != 0);
-      uint64_t s = h & mask;
-      for (int64_t probe = 0; probe < cap; ++probe, s = (s + 1) & mask) {
+      uint64_t s = (h * (uint64_t)cap) >> 32;  // cap <= 2^32
+      int64_t left = cap;  // slots not yet visited
+      while (left > 0) {
+        // scan to the first slot that is empty or carries this hash (a short, tight loop)
+        unsigned long long hs = __ldcg(&slots[s].hash);
+        while (hs != 0 && hs != h && --left > 0) {
+          s = (s + 1) & mask;
+          hs = __ldcg(&slots[s].hash);
+        }
+        if (left == 0) break;
         DictSlot* sl = &slots[s];
         // read through L2 (slots change while the kernel runs); a torn or stale read can only
-        // show "empty" or "not yet written", which the compare-and-swap below settles
-        unsigned long long hs = __ldcg(&sl->hash), rep = __ldcg(&sl->rep);
-        if (hs == 0 || (hs == h && rep == 0)) {
+        // show "empty" or "not yet written", which the compare-and-swap settles
+        unsigned long long rep = __ldcg(&sl->rep);
+        if (hs == 0 || rep == 0) {
           unsigned long long olo, ohi;
           const unsigned long long mine = ((unsigned long long)(uint32_t)len << 32) | (unsigned long long)(a + 1);
           cas128(reinterpret_cast<unsigned long long*>(sl), 0ull, 0ull, h, mine, olo, ohi);
           if (olo == 0) {  // claimed: this row represents its string
-            if (atomicAdd(&hdr->claimed, 1ull) + 1 > limit) set_status(&hdr->status, SIRIUS_ERR_TABLE_FULL);
             found = (uint32_t)s;
             break;
           }
           hs = olo;
           rep = ohi;
         }
-        if (hs != h) continue;
-        const int32_t ra = (int32_t)(uint32_t)rep - 1, rlen = (int32_t)(rep >> 32);
-        if (rlen == len && str_equal(p, c.chars + ra, len)) {
-          found = (uint32_t)s;
-          break;
+        if (hs == h) {
+          const int32_t ra = (int32_t)(uint32_t)rep - 1, rlen = (int32_t)(rep >> 32);
+          if (rlen == len && str_equal(p, c.chars + ra, len)) {
+            found = (uint32_t)s;
+            break;
+          }
         }
+        s = (s + 1) & mask;  // another string here (same hash, or claimed just before us)
+        --left;
       }
       if (found == 0xFFFFFFFFu) set_status(&hdr->status, SIRIUS_ERR_TABLE_FULL);
     }
@@ -159,6 +179,11 @@ __global__ void dict_code_kernel(const DictSlot* slots, const uint32_t* smin, in
     slot_code[s] = code;
     if (dict_rows && (int64_t)code < dict_cap) dict_rows[code] = r;
   }
+}
+
+// More distinct strings than the table's load limit -> TABLE_FULL (as for the group table).
+__global__ void dict_check_kernel(DictHeader* hdr, unsigned long long limit) {
+  if (hdr->ndict > limit) set_status(&hdr->status, SIRIUS_ERR_TABLE_FULL);
 }
 
 __global__ void dict_assign_kernel(const uint32_t* row_slot, int64_t n, const uint32_t* slot_code, int32_t* codes) {
@@ -213,7 +238,7 @@ sirius_status dict_run(const StrCol& c, int64_t hint, uint32_t flags, int32_t* d
   SIRIUS_CUDA_TRY(cudaMemsetAsync(bits, 0, (size_t)L.words * 4, s));
   if (c.n == 0) return SIRIUS_OK;
   dict_insert_kernel<<<grid_for(c.n, kDictThreads), kDictThreads, 0, s>>>(
-      c, slots, smin, L.cap, group_limit_for(L.cap), row_slot, hdr, (flags & SIRIUS_DICT_WEAK_HASH) ? 1 : 0);
+      c, slots, smin, L.cap, row_slot, hdr, (flags & SIRIUS_DICT_WEAK_HASH) ? 1 : 0);
   SIRIUS_LAUNCH_CHECK();
   dict_mark_kernel<<<grid_for(L.cap, 256), 256, 0, s>>>(slots, smin, L.cap, bits);
   SIRIUS_LAUNCH_CHECK();
@@ -221,6 +246,8 @@ sirius_status dict_run(const StrCol& c, int64_t hint, uint32_t flags, int32_t* d
   SIRIUS_LAUNCH_CHECK();
   sirius_status st = exclusive_scan_u32(cnt, L.words, part, &hdr->ndict, s);
   if (st != SIRIUS_OK) return st;
+  dict_check_kernel<<<1, 1, 0, s>>>(hdr, group_limit_for(L.cap));
+  SIRIUS_LAUNCH_CHECK();
   dict_code_kernel<<<grid_for(L.cap, 256), 256, 0, s>>>(slots, smin, L.cap, bits, cnt, slot_code, d_dict_rows,
                                                         dict_cap);
   SIRIUS_LAUNCH_CHECK();
@@ -337,6 +364,7 @@ extern "C" sirius_status sirius_dict_encode(const int32_t* d_offsets, const uint
   if (st != SIRIUS_OK) return st;
   SIRIUS_REQUIRE(n == 0 || d_codes, "dict_encode: NULL codes");
   SIRIUS_REQUIRE(dict_cap >= 0, "dict_encode: negative dict_cap");
+  SIRIUS_REQUIRE(distinct_hint <= (1ll << 31), "dict_encode: distinct_hint above 2^31");
   SIRIUS_REQUIRE((flags & ~(uint32_t)SIRIUS_DICT_WEAK_HASH) == 0, "dict_encode: unknown flags 0x%x", flags);
   const DictLayout L = dict_layout(n, distinct_hint);
   Scratch sc;
@@ -371,6 +399,7 @@ extern "C" sirius_status sirius_groupby_string(const int32_t* d_offsets, const u
   SIRIUS_REQUIRE(d_count, "groupby_string: NULL count output");
   SIRIUS_REQUIRE(out_cap >= 0, "groupby_string: negative out_cap");
   SIRIUS_REQUIRE(aggs <= SIRIUS_AGG_ALL, "groupby_string: bad aggregate mask");
+  SIRIUS_REQUIRE(distinct_hint <= (1ll << 31), "groupby_string: distinct_hint above 2^31");
   SIRIUS_REQUIRE((flags & ~(uint32_t)SIRIUS_DICT_WEAK_HASH) == 0, "groupby_string: unknown flags 0x%x", flags);
   const StrGroupLayout L = strgroup_layout(n, distinct_hint);
   Scratch sc;
