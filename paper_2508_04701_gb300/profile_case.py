@@ -2,6 +2,11 @@
 
     python -m paper_2508_04701_gb300.profile_case [--n ROWS] [--m DIM_ROWS] [--variant direct|staged]
                                                   [--load-factor LF] [--runs R]
+    python -m paper_2508_04701_gb300.profile_case --op sort --n ROWS --m DISTINCT_KEYS
+    python -m paper_2508_04701_gb300.profile_case --op strings --n ROWS --m DISTINCT_STRINGS
+
+--op sort runs the sort-based group-by on int32 keys U[0, m) with int64 values; --op strings
+dictionary-encodes a seeded string column of n rows over m distinct strings.
 
 Builds the 600M-row query's distributions at a reduced fact size (default 100M rows, 1.6 GB of
 columns, above the L2 size) against the full 15M-row dim table, and runs the pipeline R times.
@@ -24,11 +29,29 @@ def main():
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
     p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot"])
     p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
+    p.add_argument("--op", default="pipeline", choices=["pipeline", "sort", "strings"])
     a = p.parse_args()
     import torch
 
     from paper_2508_04701_gb300 import datagen as dg
     from paper_2508_04701_gb300 import sirius as S
+    if a.op == "sort":
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(1)
+        vals = torch.randint(0, 10**8, (a.n,), dtype=torch.int64, device="cuda", generator=gen)
+        keys = torch.randint(0, a.m, (a.n,), dtype=torch.int32, device="cuda", generator=gen)
+        for _ in range(a.runs):
+            g = S.sirius_groupby_sort(keys, vals, out_cap=a.m)
+        torch.cuda.synchronize()
+        print(f"profile case ok: sort group-by of {a.n} rows, {g['key'].numel()} groups")
+        return
+    if a.op == "strings":
+        col = dg.gen_strings_device(dg.StringSpec(n=a.n, d=a.m, seed=1))
+        for _ in range(a.runs):
+            codes, rows = S.sirius_dict_encode(col["offsets"], col["chars"], distinct_hint=a.m)
+        torch.cuda.synchronize()
+        print(f"profile case ok: dictionary of {a.n} strings ({col['chars'].numel()} bytes), {rows.numel()} distinct")
+        return
     if a.batch > 0:
         specs = [dg.batch_query(q) for q in range(a.batch)]
         keep, descs = [], []
