@@ -226,8 +226,10 @@ sirius_status sirius_dict_encode(const int32_t* d_offsets, const uint8_t* d_char
 /* GROUP BY a string column: per distinct string s, SUM / COUNT(*) / MIN / MAX of d_vals (those
  * in `aggs`; COUNT always), the groups in code order (first occurrence, as sirius_dict_encode
  * numbers them): d_out_rows[c] = the first row holding string c, d_sum[c] ... its aggregates.
- * The strings are dictionary-encoded, then the codes go through the hash group-by.  G = D goes
- * to *d_groups / *h_groups (synchronises); G > out_cap -> CAPACITY with G in *h_groups.
+ * The strings are dictionary-encoded and, in the same pass, each row's value is aggregated into
+ * its string's table slot (COUNT and the selected aggregates); the groups are then listed in code
+ * order.  G = D goes to *d_groups / *h_groups (synchronises); G > out_cap -> CAPACITY with G in
+ * *h_groups.
  * Scratch: sirius_groupby_string_scratch_bytes(n, distinct_hint).  Errors as sirius_dict_encode. */
 size_t sirius_groupby_string_scratch_bytes(int64_t n, int64_t distinct_hint);
 sirius_status sirius_groupby_string(const int32_t* d_offsets, const uint8_t* d_chars, int64_t n_chars,

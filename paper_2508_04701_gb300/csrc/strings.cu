@@ -1,6 +1,7 @@
 // String keys (Sec. 4.2: group-by on string keys is among the measured bottlenecks, the
 // library path grouping them by sorting).  The GB300 path hashes each string once into a
-// dictionary of dense int32 codes and groups the codes with the integer group-by.
+// dictionary of dense int32 codes; GROUP BY a string column aggregates each row's value into its
+// string's slot in the same pass, and lists the groups in code order.
 //
 // Dictionary encoding, exact: a string's 32-bit hash (below) selects a slot of an
 // open-addressing table; a slot holds (hash, where the representative's bytes are) and is
@@ -12,9 +13,17 @@
 // marks before its first row (an exclusive scan of the bitmap words' popcounts).
 //
 // String hash (32 bits; the table settles equality by bytes, so the hash only picks the slot
-// and filters): the bytes as 4-byte little-endian words, the tail zero-padded, each mixed in by
-// the body round of MurmurHash3_x86_32 (Austin Appleby, public domain); the length and that
-// hash's finalizer close it.  The home slot is the hash scaled to the table by a multiply-high.
+// and filters): the bytes as 8-byte little-endian words, the tail zero-padded; each word's two
+// halves, offset by its position, go through MurmurHash3's finalizer fmix32 (Austin Appleby,
+// public domain); the sum of those and of the length, finalized once more, is the hash.  A sum
+// does not depend on the order the words are taken in, so a warp hashes its 32 strings word by
+// word across its lanes.  The home slot is the hash scaled to the table by a multiply-high.
+//
+// Work per warp: 32 consecutive rows, whose bytes are contiguous.  Their words are dealt out to
+// the lanes in rounds of 32 (consecutive lanes read consecutive words), each word's mix added
+// to its string's sum in shared memory; then every lane probes the table for its own string,
+// and the byte comparison with a slot's representative is dealt out the same way.  A warp
+// whose strings hold more than kWarpWords words in all works string by string per lane.
 #include "scan.cuh"
 
 namespace sirius {
@@ -39,20 +48,22 @@ struct __align__(16) DictSlot {
   unsigned long long rep;
 };
 
-__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
-
-__device__ __forceinline__ uint32_t mm3_round(uint32_t h, uint32_t k) {
-  k *= 0xcc9e2d51u;
-  k = rotl32(k, 15);
-  k *= 0x1b873593u;
-  h ^= k;
-  h = rotl32(h, 13);
-  return h * 5u + 0xe6546b64u;
-}
 
 // Word j of a string: its bytes 8j .. 8j+7 as a little-endian word, zero past the end.  Read
 // as the one or two aligned 8-byte words that hold those bytes -- only words holding at least
 // one byte of the string, so no read leaves the pages the column occupies.
+// Aggregates of one string for GROUP BY a string column (32 bytes: one sector).
+struct __align__(32) SlotAgg {
+  unsigned long long sum;    // two's-complement sum (exact while the true sum fits int64)
+  unsigned long long count;
+  long long mn, mx;
+};
+
+__global__ void slot_agg_init_kernel(SlotAgg* agg, int64_t cap) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < cap; s += (int64_t)gridDim.x * blockDim.x)
+    agg[s] = SlotAgg{0ull, 0ull, INT64_MAX, INT64_MIN};
+}
+
 __device__ __forceinline__ uint64_t str_word(const uint8_t* p, int len, int j) {
   const int nb = len - 8 * j < 8 ? len - 8 * j : 8;  // 1..8
   const uintptr_t ua = (uintptr_t)(p + 8 * j);
@@ -64,17 +75,25 @@ __device__ __forceinline__ uint64_t str_word(const uint8_t* p, int len, int j) {
   return v;
 }
 
-__device__ uint32_t str_hash(const uint8_t* p, int len, bool weak) {
-  uint32_t h = 0x9747b28cu;
-  const int words = (len + 7) >> 3;
-  for (int j = 0; j < words; ++j) {
-    const uint64_t w = str_word(p, len, j);
-    h = mm3_round(h, (uint32_t)w);
-    if (8 * j + 4 < len) h = mm3_round(h, (uint32_t)(w >> 32));
-  }
-  h = fmix32(h ^ (uint32_t)len);
+// Word j's contribution: its two halves, each offset by a constant times the word's position,
+// through MurmurHash3's fmix32.  A string's hash is the finalized sum of its words'
+// contributions plus its length, so the words can be mixed in any order (by different lanes).
+__device__ __forceinline__ uint32_t mixw(uint64_t w, int j) {
+  return fmix32((uint32_t)w + 0x9e3779b9u * (uint32_t)(2 * j + 1)) +
+         fmix32((uint32_t)(w >> 32) + 0x85ebca6bu * (uint32_t)(2 * j + 2));
+}
+
+__device__ __forceinline__ uint32_t hash_finish(uint32_t acc, int len, bool weak) {
+  uint32_t h = fmix32(acc + 0xc2b2ae35u * (uint32_t)len);
   if (weak) h = (h & 0xFFu) + 1u;  // 256 values: distinct strings share hashes (tests)
   return h ? h : 1u;
+}
+
+__device__ uint32_t str_hash(const uint8_t* p, int len, bool weak) {
+  uint32_t acc = 0;
+  const int words = (len + 7) >> 3;
+  for (int j = 0; j < words; ++j) acc += mixw(str_word(p, len, j), j);
+  return hash_finish(acc, len, weak);
 }
 
 __device__ __forceinline__ bool str_equal(const uint8_t* a, const uint8_t* b, int len) {
@@ -103,55 +122,152 @@ __device__ __forceinline__ bool str_bounds(const StrCol& c, int64_t i, int32_t* 
   return true;
 }
 
-__global__ void __launch_bounds__(kDictThreads)
+constexpr int kWarpWords = 256;  // words of a warp's 32 strings dealt out across its lanes
+
+// Probe for a string from slot s with `left` slots still unvisited: the first slot that is empty
+// (claimed by compare-and-swap) or holds the same string (same hash, equal bytes).
+__device__ uint32_t probe_lane(DictSlot* slots, uint64_t mask, uint64_t s, int64_t left, uint64_t h,
+                               const uint8_t* chars, int32_t a, int32_t len) {
+  while (left > 0) {
+    // scan to the first slot that is empty or carries this hash (a short, tight loop)
+    unsigned long long hs = __ldcg(&slots[s].hash);
+    while (hs != 0 && hs != h && --left > 0) {
+      s = (s + 1) & mask;
+      hs = __ldcg(&slots[s].hash);
+    }
+    if (left == 0) break;
+    DictSlot* sl = &slots[s];
+    // read through L2 (slots change while the kernel runs); a torn or stale read can only show
+    // "empty" or "not yet written", which the compare-and-swap settles
+    unsigned long long rep = __ldcg(&sl->rep);
+    if (hs == 0 || rep == 0) {
+      unsigned long long olo, ohi;
+      const unsigned long long mine = ((unsigned long long)(uint32_t)len << 32) | (unsigned long long)(a + 1);
+      cas128(reinterpret_cast<unsigned long long*>(sl), 0ull, 0ull, h, mine, olo, ohi);
+      if (olo == 0) return (uint32_t)s;  // claimed: this row represents its string
+      hs = olo;
+      rep = ohi;
+    }
+    if (hs == h) {
+      const int32_t ra = (int32_t)(uint32_t)rep - 1, rlen = (int32_t)(rep >> 32);
+      if (rlen == len && str_equal(chars + a, chars + ra, len)) return (uint32_t)s;
+    }
+    s = (s + 1) & mask;  // another string here (same hash, or claimed just before us)
+    --left;
+  }
+  return 0xFFFFFFFFu;
+}
+
+__global__ void __launch_bounds__(kDictThreads, 6)
 dict_insert_kernel(StrCol c, DictSlot* slots, uint32_t* smin, int64_t cap, uint32_t* row_slot, DictHeader* hdr,
-                   int weak) {
+                   int weak, const int64_t* __restrict__ vals, SlotAgg* agg, uint32_t aggs) {
+  __shared__ uint8_t s_map[kDictThreads / 32][kWarpWords];  // word -> lane of its string
+  __shared__ uint32_t s_acc[kDictThreads / 32][32];          // hash sums, then "bytes differ" flags
   const uint64_t mask = (uint64_t)cap - 1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n; i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t a, len;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint8_t* map = s_map[wib];
+  uint32_t* acc = s_acc[wib];
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < c.n; base += warps * 32) {
+    const int64_t i = base + lane;
+    int32_t a = 0, len = 0;
+    const bool valid = i < c.n && str_bounds(c, i, &a, &len, &hdr->status);
+    if (!valid) len = 0;
+    const int words = (len + 7) >> 3;
+    int P = words;  // exclusive prefix of the words over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, P, o);
+      if (lane >= o) P += y;
+    }
+    const int W = __shfl_sync(0xffffffffu, P, 31);
+    P -= words;
     uint32_t found = 0xFFFFFFFFu;
-    if (str_bounds(c, i, &a, &len, &hdr->status)) {
-      const uint8_t* p = c.chars + a;
-      const uint64_t h = str_hash(p, len, weak != 0);
-      uint64_t s = (h * (uint64_t)cap) >> 32;  // cap <= 2^32
-      int64_t left = cap;  // slots not yet visited
-      while (left > 0) {
-        // scan to the first slot that is empty or carries this hash (a short, tight loop)
+    if (W > kWarpWords) {  // long strings: each lane on its own (warp-uniform branch)
+      if (valid) {
+        const uint64_t h = str_hash(c.chars + a, len, weak != 0);
+        found = probe_lane(slots, mask, (h * (uint64_t)cap) >> 32, cap, h, c.chars, a, len);
+      }
+    } else {
+      // hash: the warp's words dealt out across the lanes
+      acc[lane] = 0;
+      for (int k = 0; k < words; ++k) map[P + k] = (uint8_t)lane;
+      __syncwarp();
+      for (int q0 = 0; q0 < W; q0 += 32) {
+        const int q = q0 + lane;
+        const int sl = q < W ? map[q] : 0;
+        const int ps = __shfl_sync(0xffffffffu, P, sl);
+        const int as = __shfl_sync(0xffffffffu, a, sl);
+        const int ls = __shfl_sync(0xffffffffu, len, sl);
+        if (q < W) atomicAdd(&acc[sl], mixw(str_word(c.chars + as, ls, q - ps), q - ps));
+      }
+      __syncwarp();
+      const uint64_t h = hash_finish(acc[lane], len, weak != 0);
+      // probe: the first slot that is empty (claim it) or carries this hash (compare below)
+      uint64_t s = (h * (uint64_t)cap) >> 32;
+      int64_t left = cap;
+      bool cmp = false;
+      int32_t ra = 0;
+      if (valid) {
         unsigned long long hs = __ldcg(&slots[s].hash);
         while (hs != 0 && hs != h && --left > 0) {
           s = (s + 1) & mask;
           hs = __ldcg(&slots[s].hash);
         }
-        if (left == 0) break;
-        DictSlot* sl = &slots[s];
-        // read through L2 (slots change while the kernel runs); a torn or stale read can only
-        // show "empty" or "not yet written", which the compare-and-swap settles
-        unsigned long long rep = __ldcg(&sl->rep);
-        if (hs == 0 || rep == 0) {
-          unsigned long long olo, ohi;
-          const unsigned long long mine = ((unsigned long long)(uint32_t)len << 32) | (unsigned long long)(a + 1);
-          cas128(reinterpret_cast<unsigned long long*>(sl), 0ull, 0ull, h, mine, olo, ohi);
-          if (olo == 0) {  // claimed: this row represents its string
-            found = (uint32_t)s;
-            break;
+        if (left > 0) {
+          DictSlot* sl = &slots[s];
+          unsigned long long rep = __ldcg(&sl->rep);
+          if (hs == 0 || rep == 0) {
+            unsigned long long olo, ohi;
+            const unsigned long long mine = ((unsigned long long)(uint32_t)len << 32) | (unsigned long long)(a + 1);
+            cas128(reinterpret_cast<unsigned long long*>(sl), 0ull, 0ull, h, mine, olo, ohi);
+            if (olo == 0) found = (uint32_t)s;
+            hs = olo;
+            rep = ohi;
           }
-          hs = olo;
-          rep = ohi;
-        }
-        if (hs == h) {
-          const int32_t ra = (int32_t)(uint32_t)rep - 1, rlen = (int32_t)(rep >> 32);
-          if (rlen == len && str_equal(p, c.chars + ra, len)) {
-            found = (uint32_t)s;
-            break;
+          if (found == 0xFFFFFFFFu && hs == h && (int32_t)(rep >> 32) == len) {
+            cmp = true;
+            ra = (int32_t)(uint32_t)rep - 1;
           }
         }
-        s = (s + 1) & mask;  // another string here (same hash, or claimed just before us)
-        --left;
       }
-      if (found == 0xFFFFFFFFu) set_status(&hdr->status, SIRIUS_ERR_TABLE_FULL);
+      // byte comparison with the representative, dealt out the same way (acc: 1 = differ)
+      __syncwarp();
+      acc[lane] = 0;
+      __syncwarp();
+      for (int q0 = 0; q0 < W; q0 += 32) {
+        const int q = q0 + lane;
+        const int sl = q < W ? map[q] : 0;
+        const int ps = __shfl_sync(0xffffffffu, P, sl);
+        const int as = __shfl_sync(0xffffffffu, a, sl);
+        const int ls = __shfl_sync(0xffffffffu, len, sl);
+        const int rs = __shfl_sync(0xffffffffu, ra, sl);
+        const bool cs = __shfl_sync(0xffffffffu, cmp, sl);
+        if (q < W && cs && str_word(c.chars + as, ls, q - ps) != str_word(c.chars + rs, ls, q - ps)) acc[sl] = 1;
+      }
+      __syncwarp();
+      if (cmp && acc[lane] == 0) found = (uint32_t)s;
+      // the rest (a different string at this slot: hash collision, other length, or a claim
+      // lost to another string) probes on by itself
+      if (valid && found == 0xFFFFFFFFu && left > 0)
+        found = probe_lane(slots, mask, (s + 1) & mask, left - 1, h, c.chars, a, len);
+      __syncwarp();
     }
-    row_slot[i] = found;
-    if (found != 0xFFFFFFFFu && (uint32_t)i < __ldcg(&smin[found])) atomicMin(&smin[found], (uint32_t)i);
+    if (valid && found == 0xFFFFFFFFu) set_status(&hdr->status, SIRIUS_ERR_TABLE_FULL);
+    if (i < c.n) row_slot[i] = found;
+    // the smallest row of each string, and for GROUP BY the row's value into its string's
+    // aggregates: reductions whose results nobody waits for
+    if (found != 0xFFFFFFFFu) {
+      atomicMin(&smin[found], (uint32_t)i);
+      if (agg) {
+        const long long v = vals[i];
+        SlotAgg* g = &agg[found];
+        atomicAdd(&g->count, 1ull);
+        if (aggs & SIRIUS_AGG_SUM) atomicAdd(&g->sum, (unsigned long long)v);
+        if (aggs & SIRIUS_AGG_MIN) atomicMin(&g->mn, v);
+        if (aggs & SIRIUS_AGG_MAX) atomicMax(&g->mx, v);
+      }
+    }
   }
 }
 
@@ -222,8 +338,10 @@ DictLayout dict_layout(int64_t n, int64_t hint) {
 }
 
 // The encoding proper, into a scratch region laid out by dict_layout; D goes to hdr->ndict.
+// With agg (GROUP BY), each row's value is aggregated into its string's slot during the insert.
 sirius_status dict_run(const StrCol& c, int64_t hint, uint32_t flags, int32_t* d_codes, int64_t* d_dict_rows,
-                       int64_t dict_cap, char* base, const DictLayout& L, cudaStream_t s) {
+                       int64_t dict_cap, char* base, const DictLayout& L, cudaStream_t s,
+                       const int64_t* vals = nullptr, SlotAgg* agg = nullptr, uint32_t aggs = 0) {
   DictHeader* hdr = (DictHeader*)base;
   DictSlot* slots = (DictSlot*)(base + L.slots);
   uint32_t* smin = (uint32_t*)(base + L.smin);
@@ -236,9 +354,13 @@ sirius_status dict_run(const StrCol& c, int64_t hint, uint32_t flags, int32_t* d
   SIRIUS_CUDA_TRY(cudaMemsetAsync(slots, 0, (size_t)L.cap * sizeof(DictSlot), s));
   SIRIUS_CUDA_TRY(cudaMemsetAsync(smin, 0xFF, (size_t)L.cap * 4, s));
   SIRIUS_CUDA_TRY(cudaMemsetAsync(bits, 0, (size_t)L.words * 4, s));
+  if (agg) {
+    slot_agg_init_kernel<<<grid_for(L.cap, 256), 256, 0, s>>>(agg, L.cap);
+    SIRIUS_LAUNCH_CHECK();
+  }
   if (c.n == 0) return SIRIUS_OK;
   dict_insert_kernel<<<grid_for(c.n, kDictThreads), kDictThreads, 0, s>>>(
-      c, slots, smin, L.cap, row_slot, hdr, (flags & SIRIUS_DICT_WEAK_HASH) ? 1 : 0);
+      c, slots, smin, L.cap, row_slot, hdr, (flags & SIRIUS_DICT_WEAK_HASH) ? 1 : 0, vals, agg, aggs);
   SIRIUS_LAUNCH_CHECK();
   dict_mark_kernel<<<grid_for(L.cap, 256), 256, 0, s>>>(slots, smin, L.cap, bits);
   SIRIUS_LAUNCH_CHECK();
@@ -251,8 +373,10 @@ sirius_status dict_run(const StrCol& c, int64_t hint, uint32_t flags, int32_t* d
   dict_code_kernel<<<grid_for(L.cap, 256), 256, 0, s>>>(slots, smin, L.cap, bits, cnt, slot_code, d_dict_rows,
                                                         dict_cap);
   SIRIUS_LAUNCH_CHECK();
-  dict_assign_kernel<<<grid_for(c.n, 256), 256, 0, s>>>(row_slot, c.n, slot_code, d_codes);
-  SIRIUS_LAUNCH_CHECK();
+  if (d_codes) {
+    dict_assign_kernel<<<grid_for(c.n, 256), 256, 0, s>>>(row_slot, c.n, slot_code, d_codes);
+    SIRIUS_LAUNCH_CHECK();
+  }
   return SIRIUS_OK;
 }
 
@@ -292,7 +416,7 @@ __global__ void dict_copy_count_kernel(const DictHeader* h, int64_t* d_out) {
   *d_out = h->status == SIRIUS_OK ? (int64_t)h->ndict : -1;
 }
 
-// Group-by outputs of the codes (in table order) moved to their code's position.
+// GROUP BY outputs: each string's aggregates moved from its slot to its code's position.
 struct StrGroupOut {
   int64_t* rows;
   int64_t* sum;
@@ -302,41 +426,31 @@ struct StrGroupOut {
   int64_t cap;
 };
 
-__global__ void strgroup_place_kernel(const int64_t* gkey, const int64_t* gsum, const int64_t* gcount,
-                                      const int64_t* gmin, const int64_t* gmax, const int64_t* d_groups,
-                                      const int64_t* dict_rows, StrGroupOut o) {
-  const int64_t g = *d_groups;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t code = gkey[i];
-    if (code < 0 || code >= o.cap) continue;
-    if (o.rows) o.rows[code] = dict_rows[code];
-    if (o.sum) o.sum[code] = gsum[i];
-    o.count[code] = gcount[i];
-    if (o.min) o.min[code] = gmin[i];
-    if (o.max) o.max[code] = gmax[i];
+__global__ void strgroup_place_kernel(const DictSlot* slots, const uint32_t* smin, const uint32_t* slot_code,
+                                      const SlotAgg* agg, int64_t cap, StrGroupOut o) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < cap; s += (int64_t)gridDim.x * blockDim.x) {
+    if (slots[s].hash == 0) continue;
+    const int64_t code = slot_code[s];
+    if (code >= o.cap) continue;
+    const SlotAgg g = agg[s];
+    if (o.rows) o.rows[code] = smin[s];
+    if (o.sum) o.sum[code] = (int64_t)g.sum;
+    o.count[code] = (int64_t)g.count;
+    if (o.min) o.min[code] = g.mn;
+    if (o.max) o.max[code] = g.mx;
   }
 }
 
 struct StrGroupLayout {
   DictLayout d;
-  size_t codes, dict_rows, gout, gcount, gb, total;
+  size_t agg, total;
 };
 
 StrGroupLayout strgroup_layout(int64_t n, int64_t hint) {
   StrGroupLayout L;
   L.d = dict_layout(n, hint);
-  const int64_t nn = n > 0 ? n : 1;
-  size_t off = L.d.total;
-  L.codes = off;
-  off = align_up(off + (size_t)nn * 4, 256);
-  L.dict_rows = off;
-  off = align_up(off + (size_t)L.d.cap * 8, 256);
-  L.gout = off;  // five columns of cap entries
-  off = align_up(off + (size_t)L.d.cap * 8 * 5, 256);
-  L.gcount = off;
-  off = align_up(off + 8, 256);
-  L.gb = off;
-  L.total = align_up(off + sirius_groupby_scratch_bytes(hint), 256);
+  L.agg = L.d.total;
+  L.total = align_up(L.agg + (size_t)L.d.cap * sizeof(SlotAgg), 256);
   return L;
 }
 
@@ -406,29 +520,22 @@ extern "C" sirius_status sirius_groupby_string(const int32_t* d_offsets, const u
   if ((st = sc.acquire(d_scratch, scratch_bytes, L.total, s)) != SIRIUS_OK) return st;
   char* base = sc.base;
   DictHeader* hdr = (DictHeader*)base;
-  int32_t* codes = (int32_t*)(base + L.codes);
-  int64_t* dict_rows = (int64_t*)(base + L.dict_rows);
-  int64_t* gout = (int64_t*)(base + L.gout);
-  int64_t* gcount_dev = (int64_t*)(base + L.gcount);
-  const int64_t cap = L.d.cap;
+  SlotAgg* agg = (SlotAgg*)(base + L.agg);
   {
     PhaseTimer pt(s, SIRIUS_PHASE_GROUPBY);
     const StrCol c{d_offsets, d_chars, n, n_chars};
-    if ((st = dict_run(c, distinct_hint, flags, codes, dict_rows, cap, base, L.d, s)) != SIRIUS_OK) return st;
-  }
-  // the codes grouped by the hash group-by (a dictionary that accepted D strings has at most
-  // as many as a group table of the same hint takes), then moved to code order
-  if (n > 0) {
-    if ((st = sirius_groupby_agg(codes, 4, d_vals, n, aggs, distinct_hint, gout, gout + cap, gout + 2 * cap,
-                                 gout + 3 * cap, gout + 4 * cap, cap, gcount_dev, nullptr, base + L.gb,
-                                 L.total - L.gb, stream)) != SIRIUS_OK)
+    if ((st = dict_run(c, distinct_hint, flags, nullptr, nullptr, 0, base, L.d, s, d_vals, agg, aggs)) !=
+        SIRIUS_OK)
       return st;
-    const StrGroupOut o{d_out_rows, (aggs & SIRIUS_AGG_SUM) ? d_sum : nullptr, d_count,
-                        (aggs & SIRIUS_AGG_MIN) ? d_min : nullptr, (aggs & SIRIUS_AGG_MAX) ? d_max : nullptr,
-                        out_cap};
-    strgroup_place_kernel<<<grid_for(cap, 256), 256, 0, s>>>(gout, gout + cap, gout + 2 * cap, gout + 3 * cap,
-                                                             gout + 4 * cap, gcount_dev, dict_rows, o);
-    SIRIUS_LAUNCH_CHECK();
+    if (n > 0) {
+      const StrGroupOut o{d_out_rows, (aggs & SIRIUS_AGG_SUM) ? d_sum : nullptr, d_count,
+                          (aggs & SIRIUS_AGG_MIN) ? d_min : nullptr, (aggs & SIRIUS_AGG_MAX) ? d_max : nullptr,
+                          out_cap};
+      strgroup_place_kernel<<<grid_for(L.d.cap, 256), 256, 0, s>>>(
+          (const DictSlot*)(base + L.d.slots), (const uint32_t*)(base + L.d.smin),
+          (const uint32_t*)(base + L.d.slot_code), agg, L.d.cap, o);
+      SIRIUS_LAUNCH_CHECK();
+    }
   }
   if (d_groups) {
     dict_copy_count_kernel<<<1, 1, 0, s>>>(hdr, d_groups);
