@@ -195,13 +195,18 @@ __global__ void semi_build_kernel(SemiInput in, SemiView v) {
 }
 
 template <bool kWide, int kMode, bool kVec, bool kSemi>
-__global__ void __launch_bounds__(512)
-probe_kernel(ProbeArgs a, SemiArgs sa) {
+__device__ __forceinline__ void probe_body(ProbeArgs a, SemiArgs sa) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
   const Lookup L = read_lookup(a);
-  SemiLookups SL;
-  if (kSemi) read_semi_lookup(sa, SL);
+  // star query: the filter dims' lookups live in shared memory (read where used), not registers
+  const SemiLookups* SLp = nullptr;
+  if constexpr (kSemi) {
+    __shared__ SemiLookups s_sl;
+    if (threadIdx.x == 0) read_semi_lookup(sa, s_sl);
+    __syncthreads();
+    SLp = &s_sl;
+  }
   const uint32_t slots = kMode == kAggSmem ? a.gslots : (kMode == kAggHot ? (uint32_t)kHotEntries : 0u);
   const SmemAggs T = smem_aggs(smem_raw, slots);
   if (kMode == kAggSmem || kMode == kAggHot) {
@@ -214,10 +219,10 @@ probe_kernel(ProbeArgs a, SemiArgs sa) {
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
-    probe_quad<kWide, kMode, kVec, kSemi>(a, T, L, q, kSemi ? &SL : nullptr);
+    probe_quad<kWide, kMode, kVec, kSemi>(a, T, L, q, SLp);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-    probe_one<kWide, kMode, kSemi>(a, T, L, (nq << 2) + threadIdx.x, kSemi ? &SL : nullptr);
+    probe_one<kWide, kMode, kSemi>(a, T, L, (nq << 2) + threadIdx.x, SLp);
   if (kMode == kAggSmem || kMode == kAggHot) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
@@ -225,6 +230,21 @@ probe_kernel(ProbeArgs a, SemiArgs sa) {
       else if (T.tag[i] != kEmpty32) smem_merge(T, i, &a.tab[T.tag[i]], a.aggs);
     }
   }
+}
+
+// The fused probe pass: filter, probe and aggregate every fact row.
+template <bool kWide, int kMode, bool kVec, bool kSemi>
+__global__ void __launch_bounds__(512)
+probe_kernel(ProbeArgs a, SemiArgs sa) {
+  probe_body<kWide, kMode, kVec, kSemi>(a, sa);
+}
+
+// The same pass for a star query, held to 64 registers so that two 512-thread blocks share an
+// SM: its filter dims add dependent reads per row, and it needs the resident warps to cover them.
+template <bool kWide, int kMode, bool kVec>
+__global__ void __launch_bounds__(512, 2)
+probe_star_kernel(ProbeArgs a, SemiArgs sa) {
+  probe_body<kWide, kMode, kVec, true>(a, sa);
 }
 
 __global__ void finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __restrict__ tab, int64_t gslots,
@@ -275,7 +295,9 @@ int occupancy_blocks(K kernel, int threads, size_t smem) {
 template <bool kWide, int kMode, bool kVec, bool kSemi>
 sirius_status launch_probe(const ProbeArgs& a, const SemiArgs& sa, int threads, int blocks_per_sm, size_t smem,
                            cudaStream_t s) {
-  auto k = probe_kernel<kWide, kMode, kVec, kSemi>;
+  void (*k)(ProbeArgs, SemiArgs);
+  if constexpr (kSemi) k = probe_star_kernel<kWide, kMode, kVec>;
+  else k = probe_kernel<kWide, kMode, kVec, false>;
   if (kMode == kAggSmem || kMode == kAggHot) {
     static bool attr = false;
     if (!attr) {

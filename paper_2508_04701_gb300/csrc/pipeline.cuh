@@ -429,6 +429,38 @@ __device__ __forceinline__ uint32_t semi_filter(const SemiLookups& SL, int64_t r
   return bits;
 }
 
+// The same for the 16-byte-load path, shaped for memory parallelism when every filter dim has
+// one-column keys (two-column ones take the loop above): every dim's four keys are loaded
+// first, then every membership of every selected row is looked up (independent reads), and
+// the results are combined.
+__device__ __forceinline__ uint32_t semi_filter_vec(const SemiLookups& SL, int64_t row0, uint32_t bits) {
+  const int n = SL.n;
+  bool narrow = true;
+#pragma unroll
+  for (int i = 0; i < kMaxSemi; ++i)
+    if (i < n && SL.s[i].wide) narrow = false;
+  if (!narrow) return semi_filter<true>(SL, row0, bits);
+  uint32_t key[kMaxSemi][4];
+#pragma unroll
+  for (int i = 0; i < kMaxSemi; ++i) {
+    if (i >= n) break;
+    const int4 k4 = __ldcs(reinterpret_cast<const int4*>(SL.s[i].fk + row0));
+    key[i][0] = (uint32_t)k4.x;
+    key[i][1] = (uint32_t)k4.y;
+    key[i][2] = (uint32_t)k4.z;
+    key[i][3] = (uint32_t)k4.w;
+  }
+  uint32_t keep = bits;
+#pragma unroll
+  for (int i = 0; i < kMaxSemi; ++i) {
+    if (i >= n) break;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (((bits >> r) & 1u) && !semi_contains<false>(SL.s[i], key[i][r])) keep &= ~(1u << r);
+  }
+  return keep;
+}
+
 template <bool kWide, int kMode, bool kVec, bool kSemi = false>
 __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t q,
                                            const SemiLookups* SLp = nullptr) {
@@ -440,7 +472,23 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
     const int4 p4 = __ldcs(reinterpret_cast<const int4*>(a.pred) + q);
     bits = (uint32_t)cmp_op(p4.x, a.lit, a.op) | ((uint32_t)cmp_op(p4.y, a.lit, a.op) << 1) |
            ((uint32_t)cmp_op(p4.z, a.lit, a.op) << 2) | ((uint32_t)cmp_op(p4.w, a.lit, a.op) << 3);
-    if (kSemi && bits) bits = semi_filter<true>(*SLp, row0, bits);
+    if (kSemi) {
+      if (!bits) return;
+      // star query: the join key's load goes out with the filter dims' loads
+      const int4 k4 = __ldcs(reinterpret_cast<const int4*>(a.fk) + q);
+      int4 h4 = make_int4(0, 0, 0, 0);
+      if (kWide) h4 = __ldcs(reinterpret_cast<const int4*>(a.fk_hi) + q);
+      bits = semi_filter_vec(*SLp, row0, bits);
+      if (!bits) return;
+      key[0] = kWide ? pack_key64(h4.x, k4.x) : (uint64_t)(uint32_t)k4.x;
+      key[1] = kWide ? pack_key64(h4.y, k4.y) : (uint64_t)(uint32_t)k4.y;
+      key[2] = kWide ? pack_key64(h4.z, k4.z) : (uint64_t)(uint32_t)k4.z;
+      key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
+      probe_rows<kWide, kMode>(a, T, L, bits, key, v);
+      return;
+    }
     if (!bits) return;
     const int4 k4 = __ldcs(reinterpret_cast<const int4*>(a.fk) + q);
     if (kWide) {

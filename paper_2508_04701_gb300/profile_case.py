@@ -25,7 +25,7 @@ def main():
     p.add_argument("--variant", default="direct", choices=["auto", "direct", "staged"])
     p.add_argument("--load-factor", type=float, default=0.0)
     p.add_argument("--runs", type=int, default=2)
-    p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed"])
+    p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed", "star"])
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
     p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot"])
     p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
@@ -72,12 +72,15 @@ def main():
         return
     if a.workload == "skewed":
         spec, hint = dg.skewed(n=a.n, m=a.m), a.m
+    elif a.workload == "star":
+        spec, hint = dg.star(n=a.n, m=a.m), 100_000
     else:
         spec, hint = dg.plain_scale(n=a.n, m=a.m, composite=a.workload == "composite"), 100_000
     dim = dg.gen_dim_device(spec)
     fact = dg.gen_fact_device(spec, dim)
+    semi = dg.semi_args(spec, fact, dg.gen_semi_dims_device(spec)) if a.workload == "star" else None
     desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, hint, a.load_factor, agg_mode=a.agg_mode,
-                       probe_variant=a.variant, join_mode=a.join_mode)
+                       probe_variant=a.variant, join_mode=a.join_mode, semi=semi)
     outs = S.PipelineOutputs(hint + 1)
     scratch = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device="cuda")
     for _ in range(a.runs):
