@@ -23,7 +23,7 @@ constexpr int kInitUnit = 8192;
 constexpr int kBuildUnit = 2048;
 constexpr int kFinUnit = 4096;
 constexpr int kBatchThreads = 256;
-constexpr int kProbeThreads = 256;
+constexpr int kProbeThreads = 512;
 
 enum : uint32_t { kQWide = 1, kQSmem = 2, kQVec = 4, kQBuild = 8 };
 // Bits 0-7 of a plan's class mask: probe classes with work; this bit: some dim builds two-column keys.
@@ -214,7 +214,7 @@ batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __res
 // query: in shared-memory mode the block keeps that query's aggregates on chip across them
 // and merges them into the global table only when its query changes (and at the end).
 template <bool kWide, int kMode, bool kVec>
-__global__ void __launch_bounds__(kProbeThreads, 3)
+__global__ void __launch_bounds__(kProbeThreads, 2)
 batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int cls) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   const int qlo = H->cls_q0[cls], qhi = H->cls_q1[cls];
