@@ -253,7 +253,7 @@ batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
     const int64_t nq4 = a.n >> 2;
     const int64_t q0 = local * qpu;
     const int64_t q1 = q0 + qpu < nq4 ? q0 + qpu : nq4;
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec>(a, T, L, q);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec, false, true>(a, T, L, q);
     if (local == b.nu[2] - 1) {
       const int64_t t0 = nq4 << 2;
       if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, T, L, t0 + threadIdx.x);
