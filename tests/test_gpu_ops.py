@@ -262,6 +262,18 @@ def test_groupby_sort(S, n, dom):
             assert np.array_equal(got[c], want[c]), (keys.dtype, c)
 
 
+def test_groupby_sort_int64_keys_spanning_all_digits(S):
+    """int64 keys whose every byte varies (eight passes), with duplicates, against the oracle."""
+    rng = np.random.default_rng(9)
+    distinct = rng.integers(np.iinfo(np.int64).min, np.iinfo(np.int64).max, size=20_000, dtype=np.int64)
+    keys = distinct[rng.integers(0, distinct.size, size=700_001)]
+    vals = rng.integers(-10**15, 10**15, size=keys.size)
+    got = S.sirius_groupby_sort(torch.from_numpy(keys).cuda(), torch.from_numpy(vals).cuda())
+    want = O.groupby_agg(keys, vals)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(got[c].cpu().numpy(), want[c]), c
+
+
 def test_groupby_sort_skipped_digits_subsets_and_capacity(S):
     rng = np.random.default_rng(3)
     keys = (rng.integers(0, 50, size=500_000).astype(np.int64) << 40) | 0x1234  # only high digits vary

@@ -123,3 +123,24 @@ def test_groupby_string_weak_hash_subsets_and_capacity(S):
     with pytest.raises(S.SiriusError) as e:
         S.sirius_groupby_string(*args, distinct_hint=2000, out_cap=10)
     assert e.value.status == S.ERR_CAPACITY and e.value.needed == want["row"].size
+
+
+def test_groupby_string_hot_string_and_extreme_values(S):
+    """One string holds 60 % of the rows (every row of it reduces into one slot); values near
+    +-2^62 so that MIN / MAX and exact sums are exercised at the ends of int64."""
+    rng = np.random.default_rng(21)
+    n = 300_000
+    base = dg.gen_strings_host(dg.StringSpec(n=n, d=5000, seed=21))
+    strs = O.strings_of(base["offsets"], base["chars"])
+    hot = rng.random(n) < 0.6
+    strs = [b"the-hot-string" if h else s for h, s in zip(hot, strs)]
+    off, chars = dg.strcol_from_list(strs)
+    vals = rng.integers(-(1 << 62) // n, (1 << 62) // n, size=n)
+    vals[rng.integers(0, n, size=4)] = [(1 << 62), -(1 << 62), (1 << 62) - 1, -(1 << 62) + 1]
+    want = O.groupby_string(off, chars, vals)
+    got = S.sirius_groupby_string(dev(off), dev(chars), dev(vals), distinct_hint=6000)
+    for c in ("row", "sum", "count", "min", "max"):
+        assert np.array_equal(got[c].cpu().numpy(), want[c]), c
+    codes, rows = S.sirius_dict_encode(dev(off), dev(chars), distinct_hint=6000)
+    wc, wr = O.dict_encode(off, chars)
+    assert np.array_equal(codes.cpu().numpy(), wc) and np.array_equal(rows.cpu().numpy(), wr)
