@@ -483,7 +483,8 @@ def run_served(S, torch, args, dev, rank):
 def run_configs(S, torch, dev, rank):
     """The metric's other single-GPU configurations, measured beside the main line.
     1M-row query: latency per query, median of 100 timed runs after 10 warm-ups, as a plain
-    sirius_run_pipeline call, as the same call captured once in a CUDA graph and replayed (both
+    sirius_run_pipeline call (the single launch), through the per-phase kernels, as the same
+    call captured once in a CUDA graph and replayed (both
     must give the same groups), and as a one-query batch plan.  The 600M-row query on two-column join keys (hash-table join):
     rows/s and phases.  300M-row Zipf(1.1) query with (grp, flag) group keys: rows/s
     and G, then the same query with group_cap_hint a quarter of the dim's 10M group keys, which
@@ -516,6 +517,9 @@ def run_configs(S, torch, dev, rank):
     scr = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
     g1 = S.sirius_run_pipeline(desc, o1, scr, stream, sync=True)
     us_plain = median_us(lambda: S.sirius_run_pipeline(desc, o1, scr, stream, sync=False))
+    # the same query through the per-phase kernels (the default above is the single launch)
+    desc_multi = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, 1000, probe_variant="direct")
+    us_multi = median_us(lambda: S.sirius_run_pipeline(desc_multi, o1, scr, stream, sync=False))
     # the same call captured once into a CUDA graph and replayed
     scr2 = torch.empty_like(scr)
     us_graph, graph_error = None, None
@@ -546,12 +550,14 @@ def run_configs(S, torch, dev, rank):
     us_plan = median_us(lambda: plan.run([desc], [o3], scratch=bscr, use_graph=True, stream=stream, sync=False))
     plan.close()
     out["plain_1M"] = {"rows": spec.n, "groups": g1, "us_per_query_median": us_plain,
+                       "path": "single launch (probe_variant auto)",
+                       "us_per_query_multi_kernel_median": us_multi,
                        "rows_per_s": spec.n / (us_plain / 1e6), "us_per_query_graph_median": us_graph,
                        "rows_per_s_graph": spec.n / (us_graph / 1e6) if us_graph else None,
                        "graph_error": graph_error, "graph_results_identical": bool(same),
                        "us_per_query_one_query_plan_median": us_plan,
                        "timing": "CUDA events per query, median of 100 after 10 warm-ups"}
-    del fact, dim, desc, scr, scr2, bscr, o1, o2, o3
+    del fact, dim, desc, desc_multi, scr, scr2, bscr, o1, o2, o3
 
     # ---- 600M-row query on two-column join keys: the hash-table join at full size
     spec = dg.plain_scale(composite=True, seed=rank)

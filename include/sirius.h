@@ -75,7 +75,7 @@ enum { SIRIUS_PHASE_FILTER = 0, SIRIUS_PHASE_JOIN_BUILD = 1, SIRIUS_PHASE_JOIN_P
        SIRIUS_PHASE_PIPE_BUILD = 6, SIRIUS_PHASE_PIPE_PROBE = 7, SIRIUS_PHASE_PIPE_FINALIZE = 8,
        SIRIUS_PHASE_BATCH_GRAPH = 9, SIRIUS_PHASE_BATCH_BUILD = 10, SIRIUS_PHASE_BATCH_PROBE = 11,
        SIRIUS_PHASE_BATCH_FINALIZE = 12, SIRIUS_PHASE_COPY = 13, SIRIUS_PHASE_PIPE_AGGREGATE = 14,
-       SIRIUS_PHASES = 16 };
+       SIRIUS_PHASE_PIPE_SINGLE = 15, SIRIUS_PHASES = 16 };
 void sirius_profile_start(void);
 sirius_status sirius_profile_stop(double* ms, int64_t* launches, int32_t nphases);
 
@@ -310,7 +310,13 @@ typedef struct {
   int32_t blocks_per_sm;    /* probe kernel residency target; 0 -> occupancy maximum */
   int32_t probe_variant;    /* 0 auto; 1 direct (each thread loads its rows and buckets);
                                2 staged (TMA column tiles + cp.async bucket gathers, global
-                               aggregation, 16-byte aligned columns) */
+                               aggregation, 16-byte aligned columns); 3 single launch
+                               (sirius_run_pipeline: every phase -- clearing, key range, build,
+                               probe, finalize -- in one cooperative launch of one block per SM,
+                               phases separated by grid-wide barriers; not for star queries or
+                               partitioned aggregation, which run as 1; other calls take 3 as 1).
+                               Auto: 3 when n <= 2^22, m <= 2^20 and neither block_threads nor
+                               blocks_per_sm is set, else 1 */
   int32_t join_mode;        /* 0 auto: one-column build keys that are unique and span a range
                                of at most 2m values are joined through a direct-address array
                                (decided on the device during the build); 1 hash table always */

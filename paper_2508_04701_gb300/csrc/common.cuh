@@ -129,6 +129,11 @@ __host__ __device__ __forceinline__ uint32_t home_slot64(uint64_t key, uint32_t 
 __device__ __forceinline__ void ldg_bucket(const void* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
   asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
+// The same load through L2 only (no L1 or read-only cache): for tables written earlier in the
+// same launch by other blocks, which the non-coherent path may not see.
+__device__ __forceinline__ void ldcg_bucket(const void* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+  asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
 __host__ __device__ __forceinline__ uint64_t pack_key64(int32_t hi, int32_t lo) {
   return ((uint64_t)(uint32_t)hi << 32) | (uint64_t)(uint32_t)lo;
 }

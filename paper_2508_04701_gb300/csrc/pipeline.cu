@@ -34,11 +34,10 @@ namespace {
 // array (kEmpty32, as 16-byte words), group keys and the Bloom filter's words.  The join slots
 // are only cleared when the hash table may be needed (`jpairs` is 0 when the direct array is
 // certain to be used).
-__global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* jwords2, int64_t jpairs,
-                                ulonglong2* dwords2, int64_t dpairs, int64_t* gkeys, int64_t gslots,
-                                uint64_t* bloom, int64_t bwords) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+__device__ __forceinline__ void dim_init_rows(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* jwords2,
+                                              int64_t jpairs, ulonglong2* dwords2, int64_t dpairs, int64_t* gkeys,
+                                              int64_t gslots, uint64_t* bloom, int64_t bwords, int64_t tid,
+                                              int64_t stride) {
   if (tid < 32) {
     // word 2 of the dim header holds (key_min, key_max): start at (INT32_MAX, INT32_MIN)
     reinterpret_cast<uint64_t*>(dhdr)[tid] = tid == 2 ? 0x800000007FFFFFFFull : 0ull;
@@ -50,38 +49,63 @@ __global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* j
   for (int64_t i = tid; i < gslots; i += stride) gkeys[i] = kEmptyKey;
   for (int64_t i = tid; i < bwords; i += stride) bloom[i] = 0;
 }
+__global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* jwords2, int64_t jpairs,
+                                ulonglong2* dwords2, int64_t dpairs, int64_t* gkeys, int64_t gslots,
+                                uint64_t* bloom, int64_t bwords) {
+  dim_init_rows(dhdr, jhdr, jwords2, jpairs, dwords2, dpairs, gkeys, gslots, bloom, bwords,
+                blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
 
 // Range of the one-column build keys (for the direct-array decision).
-__global__ void dim_minmax_kernel(const int32_t* __restrict__ pk, int64_t m, DimHeader* dhdr) {
+// Every thread of the block takes part: warp reductions, then one per block, so each block
+// sends one atomic pair to the header's shared address instead of one per warp.
+__device__ __forceinline__ void dim_minmax_rows(const int32_t* __restrict__ pk, int64_t m, DimHeader* dhdr,
+                                                int64_t tid, int64_t stride) {
+  __shared__ int32_t s_lo[32], s_hi[32];
   int32_t lo = INT32_MAX, hi = INT32_MIN;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = tid; j < m; j += stride) {
     const int32_t k = pk[j];
     lo = k < lo ? k : lo;
     hi = k > hi ? k : hi;
   }
   lo = __reduce_min_sync(0xffffffffu, lo);
   hi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicMin(&dhdr->key_min, lo);
-    atomicMax(&dhdr->key_max, hi);
+    s_lo[w] = lo;
+    s_hi[w] = hi;
   }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool have = threadIdx.x < (blockDim.x >> 5);
+    lo = __reduce_min_sync(0xffffffffu, have ? s_lo[threadIdx.x] : INT32_MAX);
+    hi = __reduce_max_sync(0xffffffffu, have ? s_hi[threadIdx.x] : INT32_MIN);
+    if (threadIdx.x == 0 && lo <= hi) {
+      atomicMin(&dhdr->key_min, lo);
+      atomicMax(&dhdr->key_max, hi);
+    }
+  }
+}
+__global__ void dim_minmax_kernel(const int32_t* __restrict__ pk, int64_t m, DimHeader* dhdr) {
+  dim_minmax_rows(pk, m, dhdr, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Build.  One-column keys whose range fits the direct array are entered there; otherwise (and
 // for two-column keys) into the hash table.
+// `direct` and `kmin` come from the key range the caller read; every thread of every warp
+// takes part.
 template <bool kWide>
-__global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
-                                 const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
-                                 int64_t m, DimView d, unsigned long long glimit, DimPred P) {
-  const bool direct = !kWide && direct_applies(d, m);
-  const int32_t kmin = d.dhdr->key_min;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void dim_build_rows(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
+                                               const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
+                                               int64_t m, const DimView& d, unsigned long long glimit,
+                                               const DimPred& P, bool direct, int32_t kmin, int64_t tid,
+                                               int64_t stride) {
+  if (tid == 0) {
     d.dhdr->direct = direct ? 1u : 0u;
     if (!direct && d.bloom) d.dhdr->bloom = 1;
   }
   bool dup = false;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
-       j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = tid; j < m; j += stride) {
     if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup, P, direct, kmin))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
@@ -89,6 +113,14 @@ __global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* 
     if (direct) d.dhdr->direct_failed = 1;
     else d.jhdr->has_dups = 1;
   }
+}
+template <bool kWide>
+__global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
+                                 const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
+                                 int64_t m, DimView d, unsigned long long glimit, DimPred P) {
+  const bool direct = !kWide && direct_applies(d, m);
+  dim_build_rows<kWide>(pk, pk_hi, grp, flag, m, d, glimit, P, direct, d.dhdr->key_min,
+                        blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Clears the join slots of a large table only when the hash table turns out to be needed:
@@ -105,18 +137,25 @@ __global__ void dim_clear_join_kernel(DimView d, int64_t m, int phase, int64_t j
 
 // When a duplicate key turned the direct array down, enter every row into the hash table
 // (the group keys are already in their table; finding them again returns the same slots).
-__global__ void dim_fallback_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
-                                    const int8_t* __restrict__ flag, int64_t m, DimView d,
-                                    unsigned long long glimit, DimPred P) {
-  if (!(d.dhdr->direct && d.dhdr->direct_failed)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && d.bloom) d.dhdr->bloom = 1;
+// (Called only once the caller has seen the direct array turned down.)
+__device__ __forceinline__ void dim_fallback_rows(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
+                                                  const int8_t* __restrict__ flag, int64_t m, const DimView& d,
+                                                  unsigned long long glimit, const DimPred& P, int64_t tid,
+                                                  int64_t stride) {
+  if (tid == 0 && d.bloom) d.dhdr->bloom = 1;
   bool dup = false;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
-       j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = tid; j < m; j += stride) {
     if (!dim_build_row<false>(pk, nullptr, grp, flag, j, d, glimit, dup, P))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
+}
+__global__ void dim_fallback_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
+                                    const int8_t* __restrict__ flag, int64_t m, DimView d,
+                                    unsigned long long glimit, DimPred P) {
+  if (!(d.dhdr->direct && d.dhdr->direct_failed)) return;
+  dim_fallback_rows(pk, grp, flag, m, d, glimit, P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                    (int64_t)gridDim.x * blockDim.x);
 }
 
 __global__ void run_init_kernel(PipeHeader* phdr, Agg* aggs, int64_t gslots) {
@@ -194,11 +233,14 @@ __global__ void semi_build_kernel(SemiInput in, SemiView v) {
   }
 }
 
-template <bool kWide, int kMode, bool kVec, bool kSemi>
-__device__ __forceinline__ void probe_body(ProbeArgs a, SemiArgs sa) {
+// kFresh: the build ran earlier in the same launch (the single-launch kernel): its headers and
+// tables are read through L2 only.  Every thread of the block takes part.
+template <bool kWide, int kMode, bool kVec, bool kSemi, bool kFresh = false>
+__device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& sa) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  if (a.dhdr->status != 0) return;  // the build failed: nothing to aggregate
-  const Lookup L = read_lookup(a);
+  const int32_t dstatus = kFresh ? *(const volatile int32_t*)&a.dhdr->status : a.dhdr->status;
+  if (dstatus != 0) return;  // the build failed: nothing to aggregate
+  const Lookup L = read_lookup<kFresh>(a);
   // star query: the filter dims' lookups live in shared memory (read where used), not registers
   const SemiLookups* SLp = nullptr;
   if constexpr (kSemi) {
@@ -219,10 +261,10 @@ __device__ __forceinline__ void probe_body(ProbeArgs a, SemiArgs sa) {
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
-    probe_quad<kWide, kMode, kVec, kSemi>(a, T, L, q, SLp);
+    probe_quad<kWide, kMode, kVec, kSemi, false, kFresh>(a, T, L, q, SLp);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
-    probe_one<kWide, kMode, kSemi>(a, T, L, (nq << 2) + threadIdx.x, SLp);
+    probe_one<kWide, kMode, kSemi, kFresh>(a, T, L, (nq << 2) + threadIdx.x, SLp);
   if (kMode == kAggSmem || kMode == kAggHot) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
@@ -247,17 +289,29 @@ probe_star_kernel(ProbeArgs a, SemiArgs sa) {
   probe_body<kWide, kMode, kVec, true>(a, sa);
 }
 
-__global__ void finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __restrict__ tab, int64_t gslots,
-                                const DimHeader* __restrict__ dhdr, PipeOut out, PipeHeader* phdr) {
+// kFresh: the group table and its aggregates were written earlier in the same launch (read
+// through L2 only).  Every thread of every block takes part.
+template <bool kFresh = false>
+__device__ __forceinline__ void finalize_body(const int64_t* __restrict__ gkeys, const Agg* __restrict__ tab,
+                                              int64_t gslots, const DimHeader* __restrict__ dhdr, const PipeOut& out,
+                                              PipeHeader* phdr) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t rounds = (gslots + stride - 1) / stride;
   for (int64_t r = 0; r < rounds; ++r) {
     const int64_t i = r * stride + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool occ = i < gslots && tab[i].count > 0;
+    const bool occ = i < gslots && (kFresh ? __ldcg(&tab[i].count) : tab[i].count) > 0;
     const uint64_t pos = warp_append(&phdr->groups, occ);
     if (occ && (int64_t)pos < out.cap) {
-      const Agg t = tab[i];
-      if (out.keys) out.keys[pos] = gkeys[i];
+      Agg t;
+      if (kFresh) {
+        t.sum = __ldcg(&tab[i].sum);
+        t.count = __ldcg(&tab[i].count);
+        t.min = __ldcg(&tab[i].min);
+        t.max = __ldcg(&tab[i].max);
+      } else {
+        t = tab[i];
+      }
+      if (out.keys) out.keys[pos] = kFresh ? __ldcg(&gkeys[i]) : gkeys[i];
       if (out.sum) out.sum[pos] = (int64_t)t.sum;
       if (out.count) out.count[pos] = (int64_t)t.count;
       if (out.min) out.min[pos] = t.min;
@@ -280,6 +334,113 @@ __global__ void finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __
       if (out.d_status) *out.d_status = st;
     }
   }
+}
+__global__ void finalize_kernel(const int64_t* __restrict__ gkeys, const Agg* __restrict__ tab, int64_t gslots,
+                                const DimHeader* __restrict__ dhdr, PipeOut out, PipeHeader* phdr) {
+  finalize_body(gkeys, tab, gslots, dhdr, out, phdr);
+}
+
+// ------------------------------------------------------------------ single-launch pipeline
+// A small query is latency-bound: its seven phase kernels (clear, key range, build, fallback,
+// run clear, probe, finalize) each take a few microseconds of dependent memory round trips
+// and launch gaps, far more than its bytes need.  The single-launch form runs the same phases
+// in one cooperative launch (every block resident), separated by grid-wide barriers, so no
+// phase waits for a kernel boundary.  Tables written by one phase and read by a later one are
+// read through L2 only (volatile header reads, ld.global.cg table reads): another SM's L1 or
+// read-only cache may hold a line from before the write.
+struct SingleArgs {
+  const int32_t* pk;
+  const int32_t* pk_hi;
+  const int32_t* grp;
+  const int8_t* flag;
+  int64_t m;
+  DimPred P;
+  DimView d;
+  unsigned long long glimit;
+  int64_t jpairs, dpairs, bwords;  // extents the clearing phase covers (16-byte pairs, words)
+  ProbeArgs a;                     // the probe pass (a.tab = the run's aggregates)
+  PipeHeader* phdr;                // cleared by the caller (it holds the barrier counter)
+  PipeOut out;
+};
+
+// Spins of one barrier wait (64 ns sleeps: about half a second) before it gives up.
+constexpr uint32_t kGridBarrierSpins = 1u << 23;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  return cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(*const_cast<uint32_t*>(p))
+      .load(cuda::memory_order_acquire);
+}
+
+// Grid-wide barrier of the single-launch kernel.  Thread 0 of each block arrives on `count`
+// (zero when the launch started) and waits until `target` = barriers so far x blocks arrivals
+// have been made; the fences order every block's writes before the barrier ahead of every
+// read after it.  The wait is bounded: when it runs out, the block records
+// SIRIUS_ERR_TIMEOUT in the run header and the caller leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, int32_t* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    uint32_t spins = 0;
+    while (ld_acquire_u32(count) < target) {
+      if (++spins == kGridBarrierSpins) {
+        set_status(status, SIRIUS_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <bool kWide, int kMode, bool kVec>
+__global__ void __launch_bounds__(512)
+single_query_kernel(SingleArgs g) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t* bar = reinterpret_cast<uint32_t*>(&g.phdr->pad[0]);
+  int32_t* status = &g.phdr->status;
+  uint32_t passed = 0;
+  const DimView& d = g.d;
+  // 1. clear the dim index (headers, join slots, direct array, group keys, Bloom words) and
+  //    the run's aggregates; the run header was cleared before the launch
+  dim_init_rows(d.dhdr, d.jhdr, (ulonglong2*)d.jslots, g.jpairs, (ulonglong2*)d.dslot, g.dpairs, d.gkeys,
+                (int64_t)d.gcap + 1, d.bloom, g.bwords, tid, stride);
+  for (int64_t i = tid; i < (int64_t)g.a.gslots; i += stride) agg_identity(&g.a.tab[i]);
+  if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
+  // 2. range of the one-column build keys (the direct-array decision)
+  const bool ranged = !kWide && d.dcap > 0 && g.m > 0;
+  if (ranged) {
+    dim_minmax_rows(g.pk, g.m, d.dhdr, tid, stride);
+    if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
+  }
+  // 3. build
+  if (g.m > 0) {
+    const volatile DimHeader* vh = d.dhdr;
+    const int32_t kmin = vh->key_min;
+    const int64_t range = (int64_t)vh->key_max - (int64_t)kmin + 1;
+    const bool direct = ranged && range >= 1 && range <= d.dcap;
+    dim_build_rows<kWide>(g.pk, g.pk_hi, g.grp, g.flag, g.m, d, g.glimit, g.P, direct, kmin, tid, stride);
+    if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
+    // 4. a duplicate key turned the direct array down: every row into the (cleared) hash table
+    if (!kWide && vh->direct && vh->direct_failed) {
+      dim_fallback_rows(g.pk, g.grp, g.flag, g.m, d, g.glimit, g.P, tid, stride);
+      if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
+    }
+    // 5. filter, probe and aggregate the fact rows
+    if (g.a.n > 0) {
+      probe_body<kWide, kMode, kVec, false, true>(g.a, SemiArgs{});
+      if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
+    }
+  }
+  // 6. compact the occupied group slots into the outputs; the last block publishes G and status
+  finalize_body<true>(d.gkeys, g.a.tab, (int64_t)g.a.gslots, d.dhdr, g.out, g.phdr);
 }
 
 template <typename K>
@@ -388,6 +549,55 @@ sirius_status dispatch_probe(const ProbeArgs& a, const SemiArgs& sa, int mode, b
                : launch_probe<kWide, kAggHot, false, kSemi>(a, sa, threads, bps, kHotSmemBytes, s);
   return vec ? launch_probe<kWide, kAggGlobal, true, kSemi>(a, sa, threads, bps, 0, s)
              : launch_probe<kWide, kAggGlobal, false, kSemi>(a, sa, threads, bps, 0, s);
+}
+
+// The single-launch pipeline: the run header is cleared (it holds the grid barrier's counter),
+// then one cooperative launch of `per_sm` blocks per SM (at most the resident maximum), fewer
+// when the query has less work than that.
+template <bool kWide, int kMode, bool kVec>
+sirius_status launch_single(const SingleArgs& g, int threads, int per_sm, size_t smem, cudaStream_t s) {
+  auto k = single_query_kernel<kWide, kMode, kVec>;
+  static bool attr = false;
+  if (!attr) {
+    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  const int occ = occupancy_blocks(k, threads, smem);
+  if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+  int64_t work = (g.a.n >> 2) > g.m ? (g.a.n >> 2) : g.m;
+  const int64_t other[4] = {g.jpairs, g.dpairs, (int64_t)g.a.gslots, g.bwords};
+  for (int64_t w : other) work = w > work ? w : work;
+  int64_t grid = (work + threads - 1) / threads;
+  const int64_t most = (int64_t)sm_count() * per_sm;
+  if (grid > most) grid = most;
+  if (grid < 1) grid = 1;
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(g.phdr, 0, sizeof(PipeHeader), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  SIRIUS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, g));
+  SIRIUS_LAUNCH_CHECK();
+  return SIRIUS_OK;
+}
+
+template <bool kWide>
+sirius_status dispatch_single(const SingleArgs& g, int mode, bool vec, int threads, int per_sm, size_t smem,
+                              cudaStream_t s) {
+  if (mode == kAggSmem)
+    return vec ? launch_single<kWide, kAggSmem, true>(g, threads, per_sm, smem, s)
+               : launch_single<kWide, kAggSmem, false>(g, threads, per_sm, smem, s);
+  if (mode == kAggHot)
+    return vec ? launch_single<kWide, kAggHot, true>(g, threads, per_sm, kHotSmemBytes, s)
+               : launch_single<kWide, kAggHot, false>(g, threads, per_sm, kHotSmemBytes, s);
+  return vec ? launch_single<kWide, kAggGlobal, true>(g, threads, per_sm, 0, s)
+             : launch_single<kWide, kAggGlobal, false>(g, threads, per_sm, 0, s);
 }
 
 }  // namespace
@@ -512,7 +722,7 @@ sirius_status validate_fact(const sirius_pipeline_desc* q) {
                                            q->block_threads <= 512),
                  "pipeline: block_threads must be a multiple of 32 in [64, 512]");
   SIRIUS_REQUIRE(q->blocks_per_sm >= 0 && q->blocks_per_sm <= 32, "pipeline: blocks_per_sm out of range");
-  SIRIUS_REQUIRE(q->probe_variant >= 0 && q->probe_variant <= 2, "pipeline: bad probe_variant %d",
+  SIRIUS_REQUIRE(q->probe_variant >= 0 && q->probe_variant <= 3, "pipeline: bad probe_variant %d",
                  q->probe_variant);
   return SIRIUS_OK;
 }
@@ -602,9 +812,7 @@ sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s) {
   return SIRIUS_OK;
 }
 
-sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
-                        cudaStream_t s, const SemiView* semi, int nsemi) {
-  if (q->n == 0) return SIRIUS_OK;
+static ProbeArgs probe_args(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots) {
   ProbeArgs a;
   a.fk = q->fk;
   a.fk_hi = q->fk_hi;
@@ -621,14 +829,26 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   a.dslot = d.dslot;
   a.bloom = d.bloom;
   a.bloom_mask = d.bloom_mask;
+  a.tab = r.aggs;
+  a.gslots = (uint32_t)gslots;
+  return a;
+}
+
+// 16-byte loads of the probe columns need every one 16-byte aligned.
+static bool vec_columns(const sirius_pipeline_desc* q) {
+  return ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
+         (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+}
+
+sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
+                        cudaStream_t s, const SemiView* semi, int nsemi) {
+  if (q->n == 0) return SIRIUS_OK;
+  const ProbeArgs a = probe_args(q, d, r, gslots);
   SemiArgs sa;
   sa.nsemi = nsemi;
   for (int i = 0; i < kMaxSemi; ++i) sa.semi[i] = i < nsemi ? semi[i] : SemiView{};
-  a.tab = r.aggs;
-  a.gslots = (uint32_t)gslots;
   const int mode = r.mode;
-  bool vec = ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
-             (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
+  bool vec = vec_columns(q);
   for (int i = 0; i < nsemi; ++i)  // a star query's key columns take the vector loads too
     vec = vec && ((uintptr_t)semi[i].fk & 15) == 0 && (!semi[i].fk_hi || ((uintptr_t)semi[i].fk_hi & 15) == 0);
   if (mode == kAggPart) {
@@ -657,6 +877,45 @@ sirius_status run_finalize(const sirius_pipeline_desc* q, const DimView& d, cons
   finalize_kernel<<<grid_for(gslots, 256), 256, 0, s>>>(d.gkeys, r.aggs, gslots, d.dhdr, out, r.phdr);
   SIRIUS_LAUNCH_CHECK();
   return SIRIUS_OK;
+}
+
+// Queries up to these sizes take the single launch by default (probe_variant 0).
+constexpr int64_t kSingleMaxRows = 1ll << 22;
+constexpr int64_t kSingleMaxDimRows = 1ll << 20;
+
+// Whether sirius_run_pipeline runs the query as one launch: not for star queries or
+// partitioned aggregation; always when asked for (probe_variant 3); by default when the query
+// is small and no probe launch shape is forced.
+static bool single_applies(const sirius_pipeline_desc* q, const RunLayout& R) {
+  if (q->nsemi > 0 || R.mode == kAggPart) return false;
+  if (q->probe_variant == 3) return true;
+  if (q->probe_variant != 0 || q->block_threads > 0 || q->blocks_per_sm > 0) return false;
+  return q->n <= kSingleMaxRows && q->m <= kSingleMaxDimRows;
+}
+
+static sirius_status run_single(const sirius_pipeline_desc* q, const DimLayout& L, const DimView& d, const RunView& r,
+                                int64_t gslots, const PipeOut& out, cudaStream_t s) {
+  SingleArgs g;
+  g.pk = q->pk;
+  g.pk_hi = q->pk_hi;
+  g.grp = q->grp;
+  g.flag = q->flag;
+  g.m = q->m;
+  g.P = DimPred{q->dpred, q->dop, q->dliteral};
+  g.d = d;
+  g.glimit = group_limit_for(L.gcap);
+  g.jpairs = (L.jcap * (L.key_width == 8 ? 16 : 8) + 15) / 16;
+  g.dpairs = L.dcap / 4;
+  g.bwords = L.bloom_log2 > 0 ? (1ll << L.bloom_log2) : 0;
+  g.a = probe_args(q, d, r, gslots);
+  g.phdr = r.phdr;
+  g.out = out;
+  const int threads = q->block_threads > 0 ? q->block_threads : 512;
+  const int per_sm = q->blocks_per_sm > 0 ? q->blocks_per_sm : 1;
+  const size_t smem = r.mode == kAggSmem ? smem_aggs_bytes((uint32_t)gslots, false) : 0;
+  PhaseTimer pt(s, SIRIUS_PHASE_PIPE_SINGLE);
+  return L.key_width == 8 ? dispatch_single<true>(g, r.mode, vec_columns(q), threads, per_sm, smem, s)
+                          : dispatch_single<false>(g, r.mode, vec_columns(q), threads, per_sm, smem, s);
 }
 
 sirius_status read_run_status(const RunView& r, sirius_result* res, cudaStream_t s) {
@@ -790,6 +1049,11 @@ extern "C" sirius_status sirius_run_pipeline(const sirius_pipeline_desc* q, siri
   if (st != SIRIUS_OK) return st;
   const DimView d = dim_view(L, sc.base);
   const RunView r = run_view(R, sc.base + L.total);
+  if (single_applies(q, R)) {
+    if ((st = run_single(q, L, d, r, R.gslots, pipe_out(result), s)) != SIRIUS_OK) return st;
+    if (result->sync) return read_run_status(r, result, s);
+    return SIRIUS_OK;
+  }
   if ((st = dim_build(q, L, sc.base, s)) != SIRIUS_OK) return st;
   SemiView semi[kMaxSemi];
   if (q->nsemi > 0) {

@@ -2,6 +2,8 @@
 // batched paths: memory layouts, the probe pass's per-row device routines, host phases.
 #pragma once
 
+#include <type_traits>
+
 #include "tables.cuh"
 
 namespace sirius {
@@ -200,13 +202,20 @@ struct Lookup {
   uint32_t range;  // key_max - key_min + 1 (direct mode)
 };
 
+// kFresh: the build ran earlier in the same launch, so the headers are read through volatile
+// loads (L2), never from a line this SM's L1 may hold from before the build finished.
+template <bool kFresh = false>
 __device__ __forceinline__ Lookup read_lookup(const ProbeArgs& a) {
+  using DH = std::conditional_t<kFresh, const volatile DimHeader, const DimHeader>;
+  using JH = std::conditional_t<kFresh, const volatile JoinHeader, const JoinHeader>;
+  DH* dh = a.dhdr;
+  JH* jh = a.jhdr;
   Lookup L;
-  L.direct = a.dhdr->direct != 0 && a.dhdr->direct_failed == 0;
-  L.dups = a.jhdr->has_dups != 0;
-  L.bloom = a.bloom != nullptr && !L.direct && a.dhdr->bloom != 0;
-  L.kmin = a.dhdr->key_min;
-  L.range = (uint32_t)((int64_t)a.dhdr->key_max - (int64_t)a.dhdr->key_min + 1);
+  L.direct = dh->direct != 0 && dh->direct_failed == 0;
+  L.dups = jh->has_dups != 0;
+  L.bloom = a.bloom != nullptr && !L.direct && dh->bloom != 0;
+  L.kmin = dh->key_min;
+  L.range = (uint32_t)((int64_t)dh->key_max - (int64_t)L.kmin + 1);
   return L;
 }
 
@@ -295,17 +304,20 @@ __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T,
   }
 }
 
-// One 32-byte bucket starting at slot s: four 8-byte slots, or two 16-byte slots.
-template <bool kWide>
+// One 32-byte bucket starting at slot s: four 8-byte slots, or two 16-byte slots.  kFresh:
+// the table was written earlier in the same launch, so the load goes through L2 only.
+template <bool kWide, bool kFresh = false>
 __device__ __forceinline__ void load_bucket(const void* slots, uint32_t s, uint64_t (&w)[4]) {
   const char* p = reinterpret_cast<const char*>(slots) + (size_t)s * (kWide ? 16 : 8);
-  ldg_bucket(p, w[0], w[1], w[2], w[3]);
+  if (kFresh) ldcg_bucket(p, w[0], w[1], w[2], w[3]);
+  else ldg_bucket(p, w[0], w[1], w[2], w[3]);
 }
 
 // Probe up to four rows (bit r of `bits` set = row r selected).  The home bucket of every
 // selected row is loaded before any row is examined, so four sector misses are in flight
-// together; a walk continues bucket by bucket only past full buckets.
-template <bool kWide, int kMode>
+// together; a walk continues bucket by bucket only past full buckets.  kFresh: the join
+// structures were built earlier in the same launch (read through L2 only).
+template <bool kWide, int kMode, bool kFresh = false>
 __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, uint32_t bits,
                                            const uint64_t (&key)[4], const int64_t (&v)[4]) {
   if (!kWide && L.direct) {
@@ -314,7 +326,8 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const uint32_t k = (uint32_t)key[r] - (uint32_t)L.kmin;
-      gs[r] = (((bits >> r) & 1u) && k < L.range) ? __ldg(a.dslot + k) : kEmpty32;
+      gs[r] = (((bits >> r) & 1u) && k < L.range) ? (kFresh ? __ldcg(a.dslot + k) : __ldg(a.dslot + k))
+                                                   : kEmpty32;
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -325,7 +338,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
     // keys the filter rules out skip their bucket read (all four tests in flight together)
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (((bits >> r) & 1u) && !bloom_test(a.bloom, a.bloom_mask, key[r])) bits &= ~(1u << r);
+      if (((bits >> r) & 1u) && !bloom_test<kFresh>(a.bloom, a.bloom_mask, key[r])) bits &= ~(1u << r);
     if (!bits) return;
   }
   const bool dups = L.dups;
@@ -336,7 +349,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
   for (int r = 0; r < 4; ++r) {
     if ((bits >> r) & 1u) {
       s[r] = kWide ? home_slot64(key[r], a.jcap) : home_slot32((uint32_t)key[r], a.jcap);
-      load_bucket<kWide>(a.jslots, s[r], w[r]);
+      load_bucket<kWide, kFresh>(a.jslots, s[r], w[r]);
     }
   }
 #pragma unroll
@@ -361,7 +374,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
       if (stop) break;
       slot += kPer;
       if (slot >= a.jcap) slot = 0;
-      load_bucket<kWide>(a.jslots, slot, w[r]);
+      load_bucket<kWide, kFresh>(a.jslots, slot, w[r]);
     }
   }
 }
@@ -465,7 +478,7 @@ __device__ __forceinline__ uint32_t semi_filter_vec(const SemiLookups& SL, int64
 // before any of them is used -- three column reads in flight per thread instead of one after
 // another -- at the cost of reading the values of unselected rows (a quad's values are one
 // 32-byte sector, needed whenever any of its rows is selected).
-template <bool kWide, int kMode, bool kVec, bool kSemi = false, bool kPreload = false>
+template <bool kWide, int kMode, bool kVec, bool kSemi = false, bool kPreload = false, bool kFresh = false>
 __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t q,
                                            const SemiLookups* SLp = nullptr) {
   const int64_t row0 = q << 2;
@@ -489,7 +502,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
     key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? vv[r] : 0;
-    probe_rows<kWide, kMode>(a, T, L, bits, key, v);
+    probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
     return;
   }
   if (kVec) {
@@ -510,7 +523,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
       key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
 #pragma unroll
       for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-      probe_rows<kWide, kMode>(a, T, L, bits, key, v);
+      probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
       return;
     }
     if (!bits) return;
@@ -539,11 +552,11 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-  probe_rows<kWide, kMode>(a, T, L, bits, key, v);
+  probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
 }
 
 // Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
-template <bool kWide, int kMode, bool kSemi = false>
+template <bool kWide, int kMode, bool kSemi = false, bool kFresh = false>
 __device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t r,
                                           const SemiLookups* SLp = nullptr) {
   if (!cmp_op(a.pred[r], a.lit, a.op)) return;
@@ -552,7 +565,7 @@ __device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T,
   int64_t v[4] = {0, 0, 0, 0};
   key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
   v[0] = a.val[r];
-  probe_rows<kWide, kMode>(a, T, L, 1u, key, v);
+  probe_rows<kWide, kMode, kFresh>(a, T, L, 1u, key, v);
 }
 
 // The dim-side predicate of a build (col == nullptr: every dim row takes part).

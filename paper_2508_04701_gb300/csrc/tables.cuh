@@ -95,12 +95,15 @@ __device__ __forceinline__ void bloom_insert(uint64_t* f, uint32_t mask, uint64_
   bloom_word(key, mask, w, bits);
   atomicOr(reinterpret_cast<unsigned long long*>(&f[w]), (unsigned long long)bits);
 }
-// Read-only during the probe pass: through the non-coherent path.
+// Read-only during the probe pass: through the non-coherent path (kFresh: through L2 only,
+// for a filter built earlier in the same launch).
+template <bool kFresh = false>
 __device__ __forceinline__ bool bloom_test(const uint64_t* f, uint32_t mask, uint64_t key) {
   uint32_t w;
   uint64_t bits;
   bloom_word(key, mask, w, bits);
-  return (__ldg(reinterpret_cast<const unsigned long long*>(f) + w) & bits) == bits;
+  const unsigned long long* p = reinterpret_cast<const unsigned long long*>(f) + w;
+  return ((kFresh ? __ldcg(p) : __ldg(p)) & bits) == bits;
 }
 
 // Capacity of a group table for an expected number of distinct keys: a power of two with

@@ -24,7 +24,7 @@ LT, LE, GT, GE, EQ, NE = range(6)
 OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
 AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
 AGG_MODES = {"auto": 0, "smem": 1, "global": 2, "part": 3, "hot": 4}
-PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2}
+PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2, "single": 3}
 BLOOM_MODES = {"auto": 0, "off": 1, "on": 2}
 JOIN_MODES = {"auto": 0, "hash": 1}
 
@@ -195,7 +195,7 @@ def launch_count() -> int:
 
 PHASES = ["filter", "join_build", "join_probe", "gather", "groupby", "pipe_init", "pipe_build",
           "pipe_probe", "pipe_finalize", "batch_graph", "batch_build", "batch_probe",
-          "batch_finalize", "copy", "pipe_aggregate", "reserved15"]
+          "batch_finalize", "copy", "pipe_aggregate", "pipe_single"]
 
 
 def profile_start():
