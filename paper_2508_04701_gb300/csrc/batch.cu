@@ -90,8 +90,12 @@ batch_init_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restric
     if (local == 0 && threadIdx.x < 32) {
       reinterpret_cast<uint64_t*>(b.phdr)[threadIdx.x] = 0;
       if (build) {
-        // word 2 of the dim header: (key_min, key_max) = (INT32_MAX, INT32_MIN)
-        reinterpret_cast<uint64_t*>(b.d.dhdr)[threadIdx.x] = threadIdx.x == 2 ? 0x800000007FFFFFFFull : 0ull;
+        // word 2 of the dim header: (key_min, key_max) = (INT32_MAX, INT32_MIN); words 4 and 5:
+        // the group key range = (INT64_MAX, INT64_MIN)
+        reinterpret_cast<uint64_t*>(b.d.dhdr)[threadIdx.x] = threadIdx.x == 2   ? 0x800000007FFFFFFFull
+                                                             : threadIdx.x == 4 ? 0x7FFFFFFFFFFFFFFFull
+                                                             : threadIdx.x == 5 ? 0x8000000000000000ull
+                                                                                : 0ull;
         reinterpret_cast<uint64_t*>(b.d.jhdr)[threadIdx.x] = 0;
       }
     }
@@ -111,26 +115,34 @@ batch_init_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restric
   }
 }
 
-// Key range of every dim that may take the direct array.
+// Key range (the direct-array decision) and group key range (the direct group-slot decision)
+// of every dim the batch builds.
 __global__ void __launch_bounds__(kBatchThreads)
 batch_minmax_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q) {
   const int nq = H->nq;
   for (int64_t u = blockIdx.x; u < H->total[1]; u += gridDim.x) {
     const BatchQuery& b = Q[find_query<1>(Q, nq, u)];
-    if (b.d.dcap == 0) continue;
     const int64_t r0 = (u - b.u0[1]) * kBuildUnit;
     const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
     int32_t lo = INT32_MAX, hi = INT32_MIN;
+    long long glo = INT64_MAX, ghi = INT64_MIN;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
       const int32_t k = b.pk[j];
       lo = k < lo ? k : lo;
       hi = k > hi ? k : hi;
+      const long long g = group_key(b.grp[j], b.flag, j);
+      glo = g < glo ? g : glo;
+      ghi = g > ghi ? g : ghi;
     }
     lo = __reduce_min_sync(0xffffffffu, lo);
     hi = __reduce_max_sync(0xffffffffu, hi);
-    if ((threadIdx.x & 31) == 0) {
+    glo = warp_min_i64(glo);
+    ghi = warp_max_i64(ghi);
+    if ((threadIdx.x & 31) == 0 && lo <= hi) {
       atomicMin(&b.d.dhdr->key_min, lo);
       atomicMax(&b.d.dhdr->key_max, hi);
+      atomicMin(&b.d.dhdr->gkey_min, glo);
+      atomicMax(&b.d.dhdr->gkey_max, ghi);
     }
   }
 }
@@ -174,16 +186,22 @@ batch_build_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
     const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
     if (((b.flags & kQWide) != 0) != kWide) continue;  // block-uniform
     const DimView d = b.d;
-    const bool direct = !kWide && direct_applies(d, b.m);
-    const int32_t kmin = d.dhdr->key_min;
-    if (local == 0 && threadIdx.x == 0) d.dhdr->direct = direct ? 1u : 0u;
+    const BuildMode B = read_build_mode(d, b.m, b.glimit, !kWide);
+    if (local == 0 && threadIdx.x == 0) d.dhdr->direct = B.direct ? 1u : 0u;
+    if (B.gdirect) {  // this unit's share of the slot keys
+      const int64_t units = (b.m + kBuildUnit - 1) / kBuildUnit;
+      const int64_t per = (B.grange + units - 1) / units;
+      const int64_t i0 = local * per;
+      const int64_t i1 = i0 + per < B.grange ? i0 + per : B.grange;
+      fill_direct_group_keys(d, B, i0 + threadIdx.x, i1, blockDim.x);
+    }
     bool dup = false;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-      const bool ok = dim_build_row<kWide>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup, b.dpred, direct, kmin);
+      const bool ok = dim_build_row<kWide>(b.pk, b.pk_hi, b.grp, b.flag, j, d, b.glimit, dup, b.dpred, B);
       if (!ok) set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     }
     if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
-      if (direct) d.dhdr->direct_failed = 1;
+      if (B.direct) d.dhdr->direct_failed = 1;
       else d.jhdr->has_dups = 1;
     }
   }
@@ -199,9 +217,11 @@ batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __res
     if (!(d.dhdr->direct && d.dhdr->direct_failed)) continue;
     const int64_t r0 = (u - b.u0[1]) * kBuildUnit;
     const int64_t r1 = r0 + kBuildUnit < b.m ? r0 + kBuildUnit : b.m;
+    BuildMode B = read_build_mode(d, b.m, b.glimit, true);
+    B.direct = false;
     bool dup = false;
     for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x)
-      if (!dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup, b.dpred))
+      if (!dim_build_row<false>(b.pk, nullptr, b.grp, b.flag, j, d, b.glimit, dup, b.dpred, B))
         set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
     if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
   }

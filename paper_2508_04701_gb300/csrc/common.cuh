@@ -236,6 +236,24 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Minimum / maximum of a 64-bit value over the full warp (every lane gets the result).
+__device__ __forceinline__ long long warp_min_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u < v ? u : v;
+  }
+  return v;
+}
+__device__ __forceinline__ long long warp_max_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
 // Warp-aggregated append: every lane with `want` gets a distinct index from *counter.
 __device__ __forceinline__ uint64_t warp_append(unsigned long long* counter, bool want) {
   unsigned mask = __ballot_sync(0xffffffffu, want);

@@ -39,8 +39,12 @@ __device__ __forceinline__ void dim_init_rows(DimHeader* dhdr, JoinHeader* jhdr,
                                               int64_t gslots, uint64_t* bloom, int64_t bwords, int64_t tid,
                                               int64_t stride) {
   if (tid < 32) {
-    // word 2 of the dim header holds (key_min, key_max): start at (INT32_MAX, INT32_MIN)
-    reinterpret_cast<uint64_t*>(dhdr)[tid] = tid == 2 ? 0x800000007FFFFFFFull : 0ull;
+    // word 2 of the dim header holds (key_min, key_max): start at (INT32_MAX, INT32_MIN);
+    // words 4 and 5 the group key range: start at (INT64_MAX, INT64_MIN)
+    reinterpret_cast<uint64_t*>(dhdr)[tid] = tid == 2   ? 0x800000007FFFFFFFull
+                                             : tid == 4 ? 0x7FFFFFFFFFFFFFFFull
+                                             : tid == 5 ? 0x8000000000000000ull
+                                                        : 0ull;
     reinterpret_cast<uint64_t*>(jhdr)[tid] = 0;
   }
   const ulonglong2 ones = make_ulonglong2(kEmpty64, kEmpty64);
@@ -56,61 +60,78 @@ __global__ void dim_init_kernel(DimHeader* dhdr, JoinHeader* jhdr, ulonglong2* j
                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
-// Range of the one-column build keys (for the direct-array decision).
+// Ranges of the one-column build keys (the direct-array decision) and of the group keys (the
+// direct group-slot decision).
 // Every thread of the block takes part: warp reductions, then one per block, so each block
-// sends one atomic pair to the header's shared address instead of one per warp.
-__device__ __forceinline__ void dim_minmax_rows(const int32_t* __restrict__ pk, int64_t m, DimHeader* dhdr,
+// sends one atomic per range end to the header's shared address instead of one per warp.
+__device__ __forceinline__ void dim_minmax_rows(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
+                                                const int8_t* __restrict__ flag, int64_t m, DimHeader* dhdr,
                                                 int64_t tid, int64_t stride) {
   __shared__ int32_t s_lo[32], s_hi[32];
+  __shared__ long long s_glo[32], s_ghi[32];
   int32_t lo = INT32_MAX, hi = INT32_MIN;
+  long long glo = INT64_MAX, ghi = INT64_MIN;
   for (int64_t j = tid; j < m; j += stride) {
     const int32_t k = pk[j];
     lo = k < lo ? k : lo;
     hi = k > hi ? k : hi;
+    const long long g = group_key(grp[j], flag, j);
+    glo = g < glo ? g : glo;
+    ghi = g > ghi ? g : ghi;
   }
   lo = __reduce_min_sync(0xffffffffu, lo);
   hi = __reduce_max_sync(0xffffffffu, hi);
+  glo = warp_min_i64(glo);
+  ghi = warp_max_i64(ghi);
   const unsigned w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     s_lo[w] = lo;
     s_hi[w] = hi;
+    s_glo[w] = glo;
+    s_ghi[w] = ghi;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
     const bool have = threadIdx.x < (blockDim.x >> 5);
     lo = __reduce_min_sync(0xffffffffu, have ? s_lo[threadIdx.x] : INT32_MAX);
     hi = __reduce_max_sync(0xffffffffu, have ? s_hi[threadIdx.x] : INT32_MIN);
+    glo = warp_min_i64(have ? s_glo[threadIdx.x] : INT64_MAX);
+    ghi = warp_max_i64(have ? s_ghi[threadIdx.x] : INT64_MIN);
     if (threadIdx.x == 0 && lo <= hi) {
       atomicMin(&dhdr->key_min, lo);
       atomicMax(&dhdr->key_max, hi);
+      atomicMin(&dhdr->gkey_min, glo);
+      atomicMax(&dhdr->gkey_max, ghi);
     }
   }
 }
-__global__ void dim_minmax_kernel(const int32_t* __restrict__ pk, int64_t m, DimHeader* dhdr) {
-  dim_minmax_rows(pk, m, dhdr, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+__global__ void dim_minmax_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
+                                  const int8_t* __restrict__ flag, int64_t m, DimHeader* dhdr) {
+  dim_minmax_rows(pk, grp, flag, m, dhdr, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x);
 }
 
 // Build.  One-column keys whose range fits the direct array are entered there; otherwise (and
 // for two-column keys) into the hash table.
-// `direct` and `kmin` come from the key range the caller read; every thread of every warp
-// takes part.
+// The build mode comes from the key ranges the caller read; every thread of every warp takes
+// part.
 template <bool kWide>
 __device__ __forceinline__ void dim_build_rows(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
                                                const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
                                                int64_t m, const DimView& d, unsigned long long glimit,
-                                               const DimPred& P, bool direct, int32_t kmin, int64_t tid,
-                                               int64_t stride) {
+                                               const DimPred& P, const BuildMode& B, int64_t tid, int64_t stride) {
   if (tid == 0) {
-    d.dhdr->direct = direct ? 1u : 0u;
-    if (!direct && d.bloom) d.dhdr->bloom = 1;
+    d.dhdr->direct = B.direct ? 1u : 0u;
+    if (!B.direct && d.bloom) d.dhdr->bloom = 1;
   }
+  if (B.gdirect) fill_direct_group_keys(d, B, tid, B.grange, stride);
   bool dup = false;
   for (int64_t j = tid; j < m; j += stride) {
-    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup, P, direct, kmin))
+    if (!dim_build_row<kWide>(pk, pk_hi, grp, flag, j, d, glimit, dup, P, B))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) {
-    if (direct) d.dhdr->direct_failed = 1;
+    if (B.direct) d.dhdr->direct_failed = 1;
     else d.jhdr->has_dups = 1;
   }
 }
@@ -118,9 +139,9 @@ template <bool kWide>
 __global__ void dim_build_kernel(const int32_t* __restrict__ pk, const int32_t* __restrict__ pk_hi,
                                  const int32_t* __restrict__ grp, const int8_t* __restrict__ flag,
                                  int64_t m, DimView d, unsigned long long glimit, DimPred P) {
-  const bool direct = !kWide && direct_applies(d, m);
-  dim_build_rows<kWide>(pk, pk_hi, grp, flag, m, d, glimit, P, direct, d.dhdr->key_min,
-                        blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+  const BuildMode B = read_build_mode(d, m, glimit, !kWide);
+  dim_build_rows<kWide>(pk, pk_hi, grp, flag, m, d, glimit, P, B, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x);
 }
 
 // Clears the join slots of a large table only when the hash table turns out to be needed:
@@ -137,15 +158,17 @@ __global__ void dim_clear_join_kernel(DimView d, int64_t m, int phase, int64_t j
 
 // When a duplicate key turned the direct array down, enter every row into the hash table
 // (the group keys are already in their table; finding them again returns the same slots).
-// (Called only once the caller has seen the direct array turned down.)
+// (Called only once the caller has seen the direct array turned down; B is the build's mode,
+// whose group slots the rows find again.)
 __device__ __forceinline__ void dim_fallback_rows(const int32_t* __restrict__ pk, const int32_t* __restrict__ grp,
                                                   const int8_t* __restrict__ flag, int64_t m, const DimView& d,
-                                                  unsigned long long glimit, const DimPred& P, int64_t tid,
-                                                  int64_t stride) {
+                                                  unsigned long long glimit, const DimPred& P, BuildMode B,
+                                                  int64_t tid, int64_t stride) {
   if (tid == 0 && d.bloom) d.dhdr->bloom = 1;
+  B.direct = false;
   bool dup = false;
   for (int64_t j = tid; j < m; j += stride) {
-    if (!dim_build_row<false>(pk, nullptr, grp, flag, j, d, glimit, dup, P))
+    if (!dim_build_row<false>(pk, nullptr, grp, flag, j, d, glimit, dup, P, B))
       set_status(&d.dhdr->status, SIRIUS_ERR_TABLE_FULL);
   }
   if (__any_sync(0xffffffffu, dup) && (threadIdx.x & 31) == 0) d.jhdr->has_dups = 1;
@@ -154,8 +177,8 @@ __global__ void dim_fallback_kernel(const int32_t* __restrict__ pk, const int32_
                                     const int8_t* __restrict__ flag, int64_t m, DimView d,
                                     unsigned long long glimit, DimPred P) {
   if (!(d.dhdr->direct && d.dhdr->direct_failed)) return;
-  dim_fallback_rows(pk, grp, flag, m, d, glimit, P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                    (int64_t)gridDim.x * blockDim.x);
+  dim_fallback_rows(pk, grp, flag, m, d, glimit, P, read_build_mode(d, m, glimit, true),
+                    blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 __global__ void run_init_kernel(PipeHeader* phdr, Agg* aggs, int64_t gslots) {
@@ -414,23 +437,19 @@ single_query_kernel(SingleArgs g) {
                 (int64_t)d.gcap + 1, d.bloom, g.bwords, tid, stride);
   for (int64_t i = tid; i < (int64_t)g.a.gslots; i += stride) agg_identity(&g.a.tab[i]);
   if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
-  // 2. range of the one-column build keys (the direct-array decision)
-  const bool ranged = !kWide && d.dcap > 0 && g.m > 0;
-  if (ranged) {
-    dim_minmax_rows(g.pk, g.m, d.dhdr, tid, stride);
-    if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
-  }
-  // 3. build
   if (g.m > 0) {
+    // 2. ranges of the build keys and of the group keys (the direct-array and direct group-slot
+    //    decisions)
+    dim_minmax_rows(g.pk, g.grp, g.flag, g.m, d.dhdr, tid, stride);
+    if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
+    // 3. build
     const volatile DimHeader* vh = d.dhdr;
-    const int32_t kmin = vh->key_min;
-    const int64_t range = (int64_t)vh->key_max - (int64_t)kmin + 1;
-    const bool direct = ranged && range >= 1 && range <= d.dcap;
-    dim_build_rows<kWide>(g.pk, g.pk_hi, g.grp, g.flag, g.m, d, g.glimit, g.P, direct, kmin, tid, stride);
+    const BuildMode B = read_build_mode<true>(d, g.m, g.glimit, !kWide);
+    dim_build_rows<kWide>(g.pk, g.pk_hi, g.grp, g.flag, g.m, d, g.glimit, g.P, B, tid, stride);
     if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
     // 4. a duplicate key turned the direct array down: every row into the (cleared) hash table
     if (!kWide && vh->direct && vh->direct_failed) {
-      dim_fallback_rows(g.pk, g.grp, g.flag, g.m, d, g.glimit, g.P, tid, stride);
+      dim_fallback_rows(g.pk, g.grp, g.flag, g.m, d, g.glimit, g.P, B, tid, stride);
       if (!grid_barrier(bar, ++passed * gridDim.x, status)) return;
     }
     // 5. filter, probe and aggregate the fact rows
@@ -777,13 +796,13 @@ sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char*
     const int g = grid_for(q->m, 256);
     const unsigned long long lim = group_limit_for(L.gcap);
     const DimPred P{q->dpred, q->dop, q->dliteral};
+    dim_minmax_kernel<<<g, 256, 0, s>>>(q->pk, q->grp, q->flag, q->m, d.dhdr);
+    SIRIUS_LAUNCH_CHECK();
     if (L.key_width == 8) {
       dim_build_kernel<true><<<g, 256, 0, s>>>(q->pk, q->pk_hi, q->grp, q->flag, q->m, d, lim, P);
       SIRIUS_LAUNCH_CHECK();
     } else {
       if (L.dcap > 0) {
-        dim_minmax_kernel<<<g, 256, 0, s>>>(q->pk, q->m, d.dhdr);
-        SIRIUS_LAUNCH_CHECK();
         if (lazy_join) {
           dim_clear_join_kernel<<<grid_for(jpairs, 256), 256, 0, s>>>(d, q->m, 0, jpairs);
           SIRIUS_LAUNCH_CHECK();

@@ -20,7 +20,8 @@ struct DimHeader {
   int32_t key_min, key_max;      // range of the one-column build keys
   uint32_t direct_failed;        // a duplicate key turned the direct array down: hash table used
   uint32_t bloom;                // 1: the hash table is in use and the Bloom filter holds its keys
-  unsigned long long pad[28];
+  long long gkey_min, gkey_max;  // range of the group keys (the direct group-slot decision)
+  unsigned long long pad[26];
 };
 static_assert(sizeof(DimHeader) == 256, "dim header is 256 bytes");
 
@@ -575,20 +576,69 @@ struct DimPred {
   int32_t lit;
 };
 
+// How a build enters its rows, decided from the key ranges its range pass recorded in the
+// dim header.  Join entries: the direct array (one-column keys whose range fits it) or the hash
+// table.  Group keys: when their range spans at most the group table's limit of distinct keys,
+// slot = key - gmin directly (a dense group domain, such as a small integer attribute, needs
+// no hashing, no compare-and-swap and no shared counter), else the hash table.  Either way a
+// key has one slot, and the direct form is taken only where the hash table could not be full,
+// so results and TABLE_FULL are the same.  With direct slots the build writes every slot's key
+// (gmin + slot) once, coalesced, rather than each row its own: rows of one group would all
+// store to one address.  Slots of keys no row has keep COUNT 0 and are never output.
+struct BuildMode {
+  bool direct = false;
+  int32_t kmin = 0;
+  bool gdirect = false;
+  int64_t gmin = 0;
+  int64_t grange = 0;  // direct group slots in use: gmax - gmin + 1
+};
+
+// The keys of direct group slots [i0, i1): slot i holds gmin + i.
+__device__ __forceinline__ void fill_direct_group_keys(const DimView& d, const BuildMode& B, int64_t i0, int64_t i1,
+                                                       int64_t step) {
+  for (int64_t i = i0; i < i1; i += step) d.gkeys[i] = B.gmin + i;
+}
+
+// kFresh: the range pass ran earlier in the same launch (volatile header reads).
+template <bool kFresh = false>
+__device__ __forceinline__ BuildMode read_build_mode(const DimView& d, int64_t m, unsigned long long glimit,
+                                                     bool allow_direct) {
+  using DH = std::conditional_t<kFresh, const volatile DimHeader, const DimHeader>;
+  DH* h = d.dhdr;
+  BuildMode B;
+  B.kmin = h->key_min;
+  const int64_t range = (int64_t)h->key_max - (int64_t)B.kmin + 1;
+  B.direct = allow_direct && d.key_width == 4 && d.dcap > 0 && m > 0 && range >= 1 && range <= d.dcap;
+  B.gmin = h->gkey_min;
+  const long long gmax = h->gkey_max;
+  B.gdirect = m > 0 && gmax >= B.gmin && (unsigned long long)(gmax - B.gmin) < glimit;
+  B.grange = B.gdirect ? gmax - B.gmin + 1 : 0;
+  return B;
+}
+
 // Build step of one dim row j: unless the dim-side predicate leaves it out, enter its group
 // key into the group table (slot gs), then (pk -> gs) into the join table -- and the key into
 // the Bloom filter when there is one.  Returns false on TABLE_FULL.
 // In direct mode the row claims dslot[key - kmin] with one CAS; finding it taken means a
-// duplicate key (dup = true), which turns the direct array down for this dim.
+// duplicate key (dup = true), which turns the direct array down for this dim.  With direct
+// group slots the slot is the key's offset from gmin (the slot keys are written by the build
+// beside its rows).
 template <bool kWide>
 __device__ __forceinline__ bool dim_build_row(const int32_t* pk, const int32_t* pk_hi, const int32_t* grp,
                                               const int8_t* flag, int64_t j, const DimView& d,
                                               unsigned long long glimit, bool& dup, const DimPred& P,
-                                              bool direct = false, int32_t kmin = 0) {
+                                              const BuildMode& B) {
   if (P.col && !cmp_op(P.col[j], P.lit, P.op)) return true;
+  const bool direct = B.direct;
+  const int32_t kmin = B.kmin;
   const int64_t gk = group_key(grp[j], flag, j);
-  const int64_t gs = group_find_or_insert(d.gkeys, d.gcap, gk, &d.dhdr->distinct, glimit);
-  if (gs < 0) return false;
+  int64_t gs;
+  if (B.gdirect) {
+    gs = gk - B.gmin;
+  } else {
+    gs = group_find_or_insert(d.gkeys, d.gcap, gk, &d.dhdr->distinct, glimit);
+    if (gs < 0) return false;
+  }
   if (kWide) {
     const uint64_t key = pack_key64(pk_hi[j], pk[j]);
     if (d.bloom) bloom_insert(d.bloom, d.bloom_mask, key);

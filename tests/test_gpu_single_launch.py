@@ -200,3 +200,35 @@ def test_replayed_from_a_cuda_graph(S):
         want = O.pipeline(dict(fact, pred=pred), dim, "lt", spec.t)
         for c in COLS:
             assert np.array_equal(got[c], want[c]), (rep, c)
+
+
+@pytest.mark.parametrize("case", ["range_at_limit", "range_past_limit", "distinct_past_limit"])
+def test_group_key_range_at_the_direct_slot_limit(S, case):
+    """Group keys whose range spans exactly the group table's limit of distinct keys take
+    direct slots (slot = key - min); a range one past it takes the hash table (same distinct
+    count, one value skipped); one distinct key past the limit fails with TABLE_FULL on both
+    paths, as it does through the hash table."""
+    hint = 1000
+    cap = int(S.lib().sirius_groupby_capacity(hint))
+    limit = cap - cap // 8
+    base = -12_345
+    if case == "range_at_limit":
+        keys = base + np.arange(limit)
+    elif case == "range_past_limit":
+        keys = base + np.concatenate([np.arange(limit - 1), [limit]])
+    else:
+        keys = base + np.arange(limit + 1)
+    rng = np.random.default_rng(len(case))
+    m = 4 * len(keys)
+    dim = {"pk": rng.permutation(m).astype(np.int32), "grp": np.tile(keys, 4).astype(np.int32)}
+    fact = {"fk": rng.integers(0, m, size=400_001).astype(np.int32),
+            "pred": rng.integers(0, 100, size=400_001).astype(np.int32),
+            "val": rng.integers(-10**9, 10**9, size=400_001)}
+    if case == "distinct_past_limit":
+        for variant in VARIANTS:
+            with pytest.raises(S.SiriusError) as e:
+                S.run_pipeline(dev(fact), dev(dim), "lt", 50, group_cap_hint=hint, out_cap=cap,
+                               probe_variant=variant)
+            assert e.value.status == S.ERR_TABLE_FULL, variant
+        return
+    assert check(S, fact, dim, "lt", 50, hint, out_cap=cap) == limit
