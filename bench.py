@@ -37,7 +37,7 @@ PROBE_SOURCES = ["paper_2508_04701_gb300/csrc/pipeline.cu", "paper_2508_04701_gb
                  "paper_2508_04701_gb300/csrc/common.cuh", "paper_2508_04701_gb300/csrc/pipeline.cuh"]
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--fifo-seconds", type=float, default=3.0)
     p.add_argument("--serve-sweep", default="8000,16000,32000,64000",
                    help="further arrival rates (q/s), one second each, to find where serving saturates")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def spec_for(name: str, rank: int):
@@ -85,6 +85,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(t: float, world: int, device) -> float:
+    """The largest of every rank's t: the slowest rank sets the job's time (t itself on one
+    rank).  Every rank must call it, at the same point of its run."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rows_per_s(world: int, rows_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes its own rows_per_rank rows (weak scaling)."""
+    return world * rows_per_rank / seconds
 
 
 def measured_peaks():
@@ -273,14 +290,9 @@ def main():
     launches = S.launch_count() - l0
     barrier()
     clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_step = t_ms / args.steps
-    value = world * spec.n / (ms_step / 1e3)
+    value = job_rows_per_s(world, spec.n, ms_step / 1e3)
     status = int(outs.d_status.item())
 
     # roofline of the dominant kernel: the fused probe pass
@@ -745,13 +757,7 @@ def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
             t0 = time.perf_counter()
             g = S.sirius_run_pipeline_host(desc, outs, chunk, scratch, stream, dev)
             times.append(time.perf_counter() - t0)
-        t = sum(times) / len(times)
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([t], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        modes[name] = t
+        modes[name] = max_over_ranks(sum(times) / len(times), world, dev)
         del scratch
     best = min(modes, key=modes.get)
     t = modes[best]
@@ -776,7 +782,7 @@ def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
     torch.cuda.synchronize()
     copy_gbs = h2d / (e0.elapsed_time(e1) / 3 / 1e3) / 1e9
     del dst
-    return {"value": world * spec.n / t, "unit": "rows/s", "h2d_bytes_per_step": h2d,
+    return {"value": job_rows_per_s(world, spec.n, t), "unit": "rows/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": t * 1e3, "steps": args.e2e_steps,
             "h2d_gbs": h2d / t / 1e9, "mode": best,
             "ms_per_step_by_mode": {k: v * 1e3 for k, v in modes.items()},
