@@ -103,9 +103,11 @@ def tune_batch(plan: S.BatchPlan, descs: List[S.PipelineDesc], outputs, scratch:
 
 def tune_pipeline(desc: S.PipelineDesc, outputs: S.PipelineOutputs,
                   load_factors: Sequence[float] = LOAD_FACTORS,
-                  variants: Sequence[str] = ("direct", "staged"),
+                  variants: Sequence[str] = ("single", "direct", "staged"),
                   block_threads: Sequence[int] = (256, 512)) -> Dict:
-    """Best (load_factor, probe_variant, block_threads) for one query; sets them on desc."""
+    """Best (load_factor, probe_variant, block_threads) for one query; sets them on desc.
+    Variants: the single launch (every phase in one cooperative launch), the per-phase kernels
+    with each block shape, and the staged probe (settings a query does not take are skipped)."""
     trials = []
     for lf in load_factors:
         desc.load_factor = lf

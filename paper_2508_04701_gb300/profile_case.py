@@ -1,7 +1,9 @@
 """A small, fixed pipeline case for profiling one probe kernel under ncu.
 
-    python -m paper_2508_04701_gb300.profile_case [--n ROWS] [--m DIM_ROWS] [--variant direct|staged]
+    python -m paper_2508_04701_gb300.profile_case [--n ROWS] [--m DIM_ROWS]
+                                                  [--variant auto|direct|staged|single]
                                                   [--load-factor LF] [--runs R]
+    python -m paper_2508_04701_gb300.profile_case --workload plain_1M --variant single
     python -m paper_2508_04701_gb300.profile_case --op sort --n ROWS --m DISTINCT_KEYS
     python -m paper_2508_04701_gb300.profile_case --op strings --n ROWS --m DISTINCT_STRINGS
 
@@ -10,6 +12,8 @@ dictionary-encodes a seeded string column of n rows over m distinct strings.
 
 Builds the 600M-row query's distributions at a reduced fact size (default 100M rows, 1.6 GB of
 columns, above the L2 size) against the full 15M-row dim table, and runs the pipeline R times.
+--workload plain_1M runs the 1M-row fact / 65 536-row dim / 1 000-group query instead (its sizes
+are fixed).
 """
 import argparse
 import os
@@ -22,10 +26,10 @@ def main():
     p = argparse.ArgumentParser()
     p.add_argument("--n", type=int, default=100_000_000)
     p.add_argument("--m", type=int, default=15_000_000)
-    p.add_argument("--variant", default="direct", choices=["auto", "direct", "staged"])
+    p.add_argument("--variant", default="direct", choices=["auto", "direct", "staged", "single"])
     p.add_argument("--load-factor", type=float, default=0.0)
     p.add_argument("--runs", type=int, default=2)
-    p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed", "star"])
+    p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed", "star", "plain_1M"])
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
     p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot"])
     p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
@@ -70,7 +74,9 @@ def main():
         print(f"profile case ok: batch of {a.batch} queries, {sum(s.n for s in specs)} fact rows, "
               f"{sum(g)} groups")
         return
-    if a.workload == "skewed":
+    if a.workload == "plain_1M":   # the 1M-row / 65 536-row / 1 000-group query (sizes fixed)
+        spec, hint = dg.plain_small(), 1000
+    elif a.workload == "skewed":
         spec, hint = dg.skewed(n=a.n, m=a.m), a.m
     elif a.workload == "star":
         spec, hint = dg.star(n=a.n, m=a.m), 100_000
@@ -86,7 +92,7 @@ def main():
     for _ in range(a.runs):
         g = S.sirius_run_pipeline(desc, outs, scratch)
     torch.cuda.synchronize()
-    print(f"profile case ok: n={a.n} m={a.m} variant={a.variant} groups={g}")
+    print(f"profile case ok: n={spec.n} m={spec.m} variant={a.variant} groups={g}")
 
 
 if __name__ == "__main__":

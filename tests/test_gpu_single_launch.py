@@ -232,3 +232,22 @@ def test_group_key_range_at_the_direct_slot_limit(S, case):
             assert e.value.status == S.ERR_TABLE_FULL, variant
         return
     assert check(S, fact, dim, "lt", 50, hint, out_cap=cap) == limit
+
+
+def test_autotuner_weighs_the_single_launch(S):
+    """tune_pipeline times the single launch beside the per-phase kernels and the staged probe;
+    the settings it keeps give the oracle's result."""
+    from paper_2508_04701_gb300 import autotune
+    spec = dg.StarSpec("t", n=1_000_003, m=65_536, fk_domain=65_536, grp_bound=1000, t=50, seed=23)
+    dim, fact = dg.gen_dim_host(spec), dg.gen_fact_host(spec)
+    desc = S.make_desc(dev(fact), dev(dim), "lt", spec.t, group_cap_hint=1000)
+    outs = S.PipelineOutputs(1001)
+    best = autotune.tune_pipeline(desc, outs, load_factors=(0.5,))
+    assert {t["probe_variant"] for t in best["all"]} == {"single", "direct", "staged"}
+    assert desc.probe_variant == S.PROBE_VARIANTS[best["probe_variant"]]
+    scratch = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device="cuda")
+    g = S.sirius_run_pipeline(desc, outs, scratch)
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in outs.trimmed(g).items()})
+    want = O.pipeline(fact, dim, "lt", spec.t)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
