@@ -440,6 +440,31 @@ sirius_status sirius_run_pipeline_batch(const sirius_pipeline_desc* qs, int32_t 
                                         void* d_scratch, size_t scratch_bytes,
                                         sirius_stream stream);
 
+/* ------------------------------------------------------------------ self-tests of bounded waits
+ * Every wait of a kernel of this library on another block's progress is bounded: when the bound
+ * runs out the wait records SIRIUS_ERR_TIMEOUT in device memory and the kernel returns, so a lost
+ * arrival never hangs the device.  These two calls (no counterpart in the paper) make such a wait
+ * run out on purpose -- the awaited flag is one that nothing sets -- and report the status the
+ * device recorded; the context stays usable afterwards.  Both synchronise `stream`.
+ *
+ * sirius_selftest_lookback_timeout: one warp plays tile 1 of the filter's decoupled look-back
+ * (sirius_filter) while tile 0 never publishes; the wait gives up after about half a second.
+ * *h_status receives SIRIUS_ERR_TIMEOUT.  d_mem: at least 256 bytes, 256-byte aligned, device
+ * memory owned by the caller (overwritten).
+ *
+ * sirius_selftest_grid_barrier: `blocks` blocks (1 .. SM count, a cooperative launch) pass one
+ * grid-wide barrier of the single-launch pipeline (probe_variant 3) waiting for blocks + missing
+ * arrivals (missing 0 or 1), each wait bounded by max_spins sleeps of 64 ns (1 .. 2^23).
+ * missing = 0: every block passes (*h_status SIRIUS_OK, *h_passed = blocks); missing = 1: every
+ * wait runs out (*h_status SIRIUS_ERR_TIMEOUT, *h_passed = 0).  d_mem: at least 256 bytes,
+ * 256-byte aligned, device memory owned by the caller (overwritten).  Errors: INVALID for
+ * arguments out of range, CUDA on a launch error. */
+sirius_status sirius_selftest_lookback_timeout(void* d_mem, size_t bytes, int32_t* h_status,
+                                               sirius_stream stream);
+sirius_status sirius_selftest_grid_barrier(int32_t blocks, int32_t missing, uint32_t max_spins,
+                                           void* d_mem, size_t bytes, int32_t* h_status,
+                                           int32_t* h_passed, sirius_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

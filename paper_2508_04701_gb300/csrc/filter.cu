@@ -65,6 +65,10 @@ __device__ uint64_t look_back(uint64_t* status, int64_t tile, uint64_t total, in
   return excl;
 }
 
+// Self-test of the look-back's bounded wait: one warp plays tile 1, whose predecessor (tile 0)
+// never publishes, so the wait runs out and records SIRIUS_ERR_TIMEOUT in *err.
+__global__ void lookback_selftest_kernel(uint64_t* status, int32_t* err) { look_back(status, 1, 7, err); }
+
 template <bool kVec>
 __global__ void __launch_bounds__(kFilterThreads)
 filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_t lit,
@@ -302,5 +306,23 @@ extern "C" sirius_status sirius_filter_static(const int32_t* d_col, int64_t n, i
       return (sirius_status)h.status;
     }
   }
+  return SIRIUS_OK;
+}
+
+// ------------------------------------------------------------------ self-test of the look-back wait
+extern "C" sirius_status sirius_selftest_lookback_timeout(void* d_mem, size_t bytes, int32_t* h_status,
+                                                         sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  SIRIUS_REQUIRE(d_mem && bytes >= 256 && ((uintptr_t)d_mem & 255) == 0,
+                 "selftest: need 256 bytes of 256-byte aligned device memory");
+  SIRIUS_REQUIRE(h_status, "selftest: NULL host result");
+  int32_t* err = (int32_t*)d_mem;
+  uint64_t* status = (uint64_t*)((char*)d_mem + 64);  // two tile words, both "not ready"
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(d_mem, 0, 256, s));
+  lookback_selftest_kernel<<<1, 32, 0, s>>>(status, err);
+  SIRIUS_LAUNCH_CHECK();
+  SIRIUS_CUDA_TRY(cudaMemcpyAsync(h_status, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SIRIUS_CUDA_TRY(cudaStreamSynchronize(s));
   return SIRIUS_OK;
 }

@@ -397,9 +397,10 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 // Grid-wide barrier of the single-launch kernel.  Thread 0 of each block arrives on `count`
 // (zero when the launch started) and waits until `target` = barriers so far x blocks arrivals
 // have been made; the fences order every block's writes before the barrier ahead of every
-// read after it.  The wait is bounded: when it runs out, the block records
-// SIRIUS_ERR_TIMEOUT in the run header and the caller leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, int32_t* status) {
+// read after it.  The wait is bounded (max_spins sleeps of 64 ns): when it runs out, the block
+// records SIRIUS_ERR_TIMEOUT in the run header and the caller leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, int32_t* status,
+                                             uint32_t max_spins = kGridBarrierSpins) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -408,7 +409,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, i
     atomicAdd(count, 1u);
     uint32_t spins = 0;
     while (ld_acquire_u32(count) < target) {
-      if (++spins == kGridBarrierSpins) {
+      if (++spins >= max_spins) {
         set_status(status, SIRIUS_ERR_TIMEOUT);
         ok = 0;
         break;
@@ -460,6 +461,16 @@ single_query_kernel(SingleArgs g) {
   }
   // 6. compact the occupied group slots into the outputs; the last block publishes G and status
   finalize_body<true>(d.gkeys, g.a.tab, (int64_t)g.a.gslots, d.dhdr, g.out, g.phdr);
+}
+
+// Self-test of the grid barrier's bounded wait: the blocks of a small cooperative launch
+// arrive, and wait for `target` arrivals; a target above the block count is a wait nothing can
+// satisfy, which must run out and record SIRIUS_ERR_TIMEOUT.  Blocks that pass count themselves
+// in blocks_done.
+__global__ void barrier_selftest_kernel(PipeHeader* phdr, uint32_t target, uint32_t max_spins) {
+  uint32_t* bar = reinterpret_cast<uint32_t*>(&phdr->pad[0]);
+  if (!grid_barrier(bar, target, &phdr->status, max_spins)) return;
+  if (threadIdx.x == 0) atomicAdd(&phdr->blocks_done, 1u);
 }
 
 template <typename K>
@@ -1339,4 +1350,38 @@ extern "C" sirius_status sirius_run_pipeline_host(const sirius_pipeline_desc* q,
   for (int k = 0; k < kCols; ++k)
     if (c[k]) cudaStreamDestroy(c[k]);
   return fail;
+}
+
+// ------------------------------------------------------------------ self-test of the barrier wait
+extern "C" sirius_status sirius_selftest_grid_barrier(int32_t blocks, int32_t missing, uint32_t max_spins,
+                                                     void* d_mem, size_t bytes, int32_t* h_status,
+                                                     int32_t* h_passed, sirius_stream stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  SIRIUS_REQUIRE(blocks >= 1 && blocks <= sm_count(), "selftest: blocks=%d outside [1, %d]", blocks, sm_count());
+  SIRIUS_REQUIRE(missing >= 0 && missing <= 1, "selftest: missing=%d must be 0 or 1", missing);
+  SIRIUS_REQUIRE(max_spins >= 1 && max_spins <= kGridBarrierSpins, "selftest: max_spins out of [1, 2^23]");
+  SIRIUS_REQUIRE(d_mem && bytes >= sizeof(PipeHeader) && ((uintptr_t)d_mem & 255) == 0,
+                 "selftest: need %zu bytes of 256-byte aligned device memory", sizeof(PipeHeader));
+  SIRIUS_REQUIRE(h_status && h_passed, "selftest: NULL host result");
+  PipeHeader* phdr = (PipeHeader*)d_mem;
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(phdr, 0, sizeof(PipeHeader), s));
+  const uint32_t target = (uint32_t)(blocks + missing);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  SIRIUS_CUDA_TRY(cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, phdr, target, max_spins));
+  SIRIUS_LAUNCH_CHECK();
+  PipeHeader h;
+  SIRIUS_CUDA_TRY(cudaMemcpyAsync(&h, phdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SIRIUS_CUDA_TRY(cudaStreamSynchronize(s));
+  *h_status = h.status;
+  *h_passed = (int32_t)h.blocks_done;
+  return SIRIUS_OK;
 }

@@ -138,6 +138,8 @@ SIGNATURES = {
     "sirius_batch_plan_destroy": (None, [_VP]),
     "sirius_run_pipeline_batch": (_I32, [ctypes.POINTER(PipelineDesc), _I32, ctypes.POINTER(DimIndex),
                                          ctypes.POINTER(Result), _VP, _SZ, _VP]),
+    "sirius_selftest_lookback_timeout": (_I32, [_VP, _SZ, _VP, _VP]),
+    "sirius_selftest_grid_barrier": (_I32, [_I32, _I32, _U32, _VP, _SZ, _VP, _VP, _VP]),
 }
 
 _LIB = None

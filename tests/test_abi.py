@@ -139,3 +139,13 @@ def test_string_calls_reject_bad_arguments_on_the_host(lib):
               None) == S.ERR_INVALID  # NULL count output
     assert lib.sirius_dict_capacity(1000) >= 1000
     assert lib.sirius_groupby_string_scratch_bytes(10**6, 1000) > lib.sirius_dict_scratch_bytes(10**6, 1000)
+
+
+def test_wait_selftests_reject_bad_arguments_on_the_host(lib):
+    from paper_2508_04701_gb300 import sirius as S
+    st, passed = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    assert lib.sirius_selftest_grid_barrier(0, 0, 16, None, 0, ctypes.byref(st), ctypes.byref(passed),
+                                            None) == S.ERR_INVALID
+    assert "blocks" in S.last_error()
+    assert lib.sirius_selftest_lookback_timeout(None, 0, ctypes.byref(st), None) == S.ERR_INVALID
+    assert "256 bytes" in S.last_error()
