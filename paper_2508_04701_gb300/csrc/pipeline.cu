@@ -283,8 +283,13 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
   }
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride)
-    probe_quad<kWide, kMode, kVec, kSemi, false, kFresh>(a, T, L, q, SLp);
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if constexpr (kFresh && kVec && !kWide && !kSemi) {
+    // the single launch (one block per SM, registers to spare): two quads in flight per thread
+    if (L.direct)
+      for (; q + stride < nq; q += 2 * stride) probe_quad_pair_direct<kMode, true>(a, T, L, q, q + stride);
+  }
+  for (; q < nq; q += stride) probe_quad<kWide, kMode, kVec, kSemi, false, kFresh>(a, T, L, q, SLp);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
     probe_one<kWide, kMode, kSemi, kFresh>(a, T, L, (nq << 2) + threadIdx.x, SLp);
@@ -424,7 +429,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, i
 }
 
 template <bool kWide, int kMode, bool kVec>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 1)
 single_query_kernel(SingleArgs g) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -556,6 +556,44 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
   probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
 }
 
+// Two quads (qa, qb, both below n/4; 16-byte loads; one-column keys joined through the direct
+// array): every column read of both, then every direct-array read of both, in flight together
+// before any aggregate update -- twice the memory parallelism of probe_quad for kernels with
+// registers to spare (the single-launch kernel runs one block per SM).
+template <int kMode, bool kFresh = false>
+__device__ __forceinline__ void probe_quad_pair_direct(const ProbeArgs& a, const SmemAggs& T, const Lookup& L,
+                                                       int64_t qa, int64_t qb) {
+  const int4 pa = __ldcs(reinterpret_cast<const int4*>(a.pred) + qa);
+  const int4 pb = __ldcs(reinterpret_cast<const int4*>(a.pred) + qb);
+  const int4 ka = __ldcs(reinterpret_cast<const int4*>(a.fk) + qa);
+  const int4 kb = __ldcs(reinterpret_cast<const int4*>(a.fk) + qb);
+  int64_t va[4], vb[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    va[r] = __ldcs(a.val + (qa << 2) + r);
+    vb[r] = __ldcs(a.val + (qb << 2) + r);
+  }
+  const uint32_t ba = (uint32_t)cmp_op(pa.x, a.lit, a.op) | ((uint32_t)cmp_op(pa.y, a.lit, a.op) << 1) |
+                      ((uint32_t)cmp_op(pa.z, a.lit, a.op) << 2) | ((uint32_t)cmp_op(pa.w, a.lit, a.op) << 3);
+  const uint32_t bb = (uint32_t)cmp_op(pb.x, a.lit, a.op) | ((uint32_t)cmp_op(pb.y, a.lit, a.op) << 1) |
+                      ((uint32_t)cmp_op(pb.z, a.lit, a.op) << 2) | ((uint32_t)cmp_op(pb.w, a.lit, a.op) << 3);
+  const uint32_t kav[4] = {(uint32_t)ka.x, (uint32_t)ka.y, (uint32_t)ka.z, (uint32_t)ka.w};
+  const uint32_t kbv[4] = {(uint32_t)kb.x, (uint32_t)kb.y, (uint32_t)kb.z, (uint32_t)kb.w};
+  uint32_t ga[4], gb[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint32_t x = kav[r] - (uint32_t)L.kmin, y = kbv[r] - (uint32_t)L.kmin;
+    ga[r] = (((ba >> r) & 1u) && x < L.range) ? (kFresh ? __ldcg(a.dslot + x) : __ldg(a.dslot + x)) : kEmpty32;
+    gb[r] = (((bb >> r) & 1u) && y < L.range) ? (kFresh ? __ldcg(a.dslot + y) : __ldg(a.dslot + y)) : kEmpty32;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (ga[r] != kEmpty32) aggregate<kMode>(a, T, ga[r], va[r]);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (gb[r] != kEmpty32) aggregate<kMode>(a, T, gb[r], vb[r]);
+}
+
 // Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
 template <bool kWide, int kMode, bool kSemi = false, bool kFresh = false>
 __device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t r,
