@@ -232,9 +232,12 @@ batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __res
 // class's queries -- and their probe units -- are contiguous.  Each block takes one
 // contiguous range of the class's units, so consecutive units mostly belong to the same
 // query: in shared-memory mode the block keeps that query's aggregates on chip across them
-// and merges them into the global table only when its query changes (and at the end).
+// and merges them into the global table only when its query changes (and at the end).  One
+// 512-thread block per SM, with the registers for two quads in flight per thread (one-column
+// keys through the direct array): the same loads in flight as two blocks of one quad each,
+// without spills, and half the blocks to merge.
 template <bool kWide, int kMode, bool kVec>
-__global__ void __launch_bounds__(kProbeThreads, 2)
+__global__ void __launch_bounds__(kProbeThreads, 1)
 batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int cls) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   const int qlo = H->cls_q0[cls], qhi = H->cls_q1[cls];
@@ -273,7 +276,10 @@ batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restri
     const int64_t nq4 = a.n >> 2;
     const int64_t q0 = local * qpu;
     const int64_t q1 = q0 + qpu < nq4 ? q0 + qpu : nq4;
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec, false, true>(a, T, L, q);
+    int64_t q = q0 + threadIdx.x;
+    if (kVec && !kWide && L.direct)  // two quads in flight per thread (registers: one block per SM)
+      for (; q + blockDim.x < q1; q += 2 * (int64_t)blockDim.x) probe_quad_pair_direct<kMode>(a, T, L, q, q + blockDim.x);
+    for (; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec, false, true>(a, T, L, q);
     if (local == b.nu[2] - 1) {
       const int64_t t0 = nq4 << 2;
       if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, T, L, t0 + threadIdx.x);
