@@ -60,8 +60,13 @@ struct BatchHeader {
   int32_t cls_q0[8], cls_q1[8];  // query range of each probe class (queries sorted by class)
   int64_t cls_u0[8], cls_u1[8];  // probe-unit range of each class
   int64_t pad2[1];
+  // Probe blocks claim chunks of their class's units from cls_next (zero at every run: the
+  // header is copied in from the host each time); cls_chunk units per claim.
+  unsigned long long cls_next[8];
+  int64_t cls_chunk[8];
+  int64_t pad3[16];
 };
-static_assert(sizeof(BatchHeader) == 256, "batch header is 256 bytes");
+static_assert(sizeof(BatchHeader) == 512, "batch header is 512 bytes");
 
 struct BatchStatus {
   int64_t status;
@@ -229,60 +234,71 @@ batch_fallback_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __res
 
 // The probe phase runs one kernel per query class (key width, aggregation mode, vector
 // loads), each specialised at compile time; the host orders the task table by class, so a
-// class's queries -- and their probe units -- are contiguous.  Each block takes one
-// contiguous range of the class's units, so consecutive units mostly belong to the same
-// query: in shared-memory mode the block keeps that query's aggregates on chip across them
-// and merges them into the global table only when its query changes (and at the end).  One
+// class's queries -- and their probe units -- are contiguous.  Blocks claim chunks of
+// consecutive units from a per-class counter (32 claims per block when the class has at least
+// 32 units per block; else one chunk each), so a block that drew expensive units (high
+// selectivity) does not hold up the others, and consecutive units
+// of a block mostly belong to the same query: in shared-memory mode the block keeps that
+// query's aggregates on chip across them and merges them into the global table only when its
+// query changes (and at the end).  One
 // 512-thread block per SM, with the registers for two quads in flight per thread (one-column
 // keys through the direct array): the same loads in flight as two blocks of one quad each,
 // without spills, and half the blocks to merge.
 template <bool kWide, int kMode, bool kVec>
 __global__ void __launch_bounds__(kProbeThreads, 1)
-batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int cls) {
+batch_probe_kernel(const BatchHeader* __restrict__ H, const BatchQuery* __restrict__ Q, int cls,
+                   unsigned long long* next) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
+  __shared__ int64_t s_claim;
   const int qlo = H->cls_q0[cls], qhi = H->cls_q1[cls];
   const int64_t qpu = H->quads_per_unit;
   const int64_t U0 = H->cls_u0[cls], U1 = H->cls_u1[cls];
-  const int64_t per = (U1 - U0 + gridDim.x - 1) / gridDim.x;
-  const int64_t ub = U0 + (int64_t)blockIdx.x * per;
-  const int64_t ue = ub + per < U1 ? ub + per : U1;
+  const int64_t chunk = H->cls_chunk[cls];
   int held = -1;  // the query whose aggregates the block's shared-memory table holds
-  for (int64_t u = ub; u < ue; ++u) {  // block-uniform
-    int lo = held >= 0 ? held : qlo, hi = qhi - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (Q[mid].u0[2] <= u) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchQuery& b = Q[lo];
-    if (kMode == kAggSmem && lo != held) {
-      if (held >= 0) {
-        __syncthreads();
-        const ProbeArgs& h = Q[held].a;
-        const SmemAggs Th = smem_aggs(smem_raw, h.gslots);
-        for (uint32_t i = threadIdx.x; i < h.gslots; i += blockDim.x) smem_merge(Th, i, &h.tab[i], h.aggs);
-        __syncthreads();
+  for (;;) {
+    __syncthreads();  // every thread has read the previous claim
+    if (threadIdx.x == 0) s_claim = (int64_t)atomicAdd(next, (unsigned long long)chunk);
+    __syncthreads();
+    const int64_t ub = U0 + s_claim;
+    if (ub >= U1) break;
+    const int64_t ue = ub + chunk < U1 ? ub + chunk : U1;
+    for (int64_t u = ub; u < ue; ++u) {  // block-uniform
+      int lo = held >= 0 ? held : qlo, hi = qhi - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (Q[mid].u0[2] <= u) lo = mid;
+        else hi = mid - 1;
       }
-      const SmemAggs Tn = smem_aggs(smem_raw, b.a.gslots);
-      for (uint32_t i = threadIdx.x; i < b.a.gslots; i += blockDim.x) smem_identity(Tn, i);
-      __syncthreads();
-      held = lo;
-    }
-    if (b.d.dhdr->status != 0) continue;  // the build failed: nothing to aggregate
-    const ProbeArgs a = b.a;
-    const SmemAggs T = kMode == kAggSmem ? smem_aggs(smem_raw, a.gslots) : SmemAggs{};
-    const Lookup L = read_lookup(a);
-    const int64_t local = u - b.u0[2];
-    const int64_t nq4 = a.n >> 2;
-    const int64_t q0 = local * qpu;
-    const int64_t q1 = q0 + qpu < nq4 ? q0 + qpu : nq4;
-    int64_t q = q0 + threadIdx.x;
-    if (kVec && !kWide && L.direct)  // two quads in flight per thread (registers: one block per SM)
-      for (; q + blockDim.x < q1; q += 2 * (int64_t)blockDim.x) probe_quad_pair_direct<kMode>(a, T, L, q, q + blockDim.x);
-    for (; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec, false, true>(a, T, L, q);
-    if (local == b.nu[2] - 1) {
-      const int64_t t0 = nq4 << 2;
-      if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, T, L, t0 + threadIdx.x);
+      const BatchQuery& b = Q[lo];
+      if (kMode == kAggSmem && lo != held) {
+        if (held >= 0) {
+          __syncthreads();
+          const ProbeArgs& h = Q[held].a;
+          const SmemAggs Th = smem_aggs(smem_raw, h.gslots);
+          for (uint32_t i = threadIdx.x; i < h.gslots; i += blockDim.x) smem_merge(Th, i, &h.tab[i], h.aggs);
+          __syncthreads();
+        }
+        const SmemAggs Tn = smem_aggs(smem_raw, b.a.gslots);
+        for (uint32_t i = threadIdx.x; i < b.a.gslots; i += blockDim.x) smem_identity(Tn, i);
+        __syncthreads();
+        held = lo;
+      }
+      if (b.d.dhdr->status != 0) continue;  // the build failed: nothing to aggregate
+      const ProbeArgs a = b.a;
+      const SmemAggs T = kMode == kAggSmem ? smem_aggs(smem_raw, a.gslots) : SmemAggs{};
+      const Lookup L = read_lookup(a);
+      const int64_t local = u - b.u0[2];
+      const int64_t nq4 = a.n >> 2;
+      const int64_t q0 = local * qpu;
+      const int64_t q1 = q0 + qpu < nq4 ? q0 + qpu : nq4;
+      int64_t q = q0 + threadIdx.x;
+      if (kVec && !kWide && L.direct)  // two quads in flight per thread (registers: one block per SM)
+        for (; q + blockDim.x < q1; q += 2 * (int64_t)blockDim.x) probe_quad_pair_direct<kMode>(a, T, L, q, q + blockDim.x);
+      for (; q < q1; q += blockDim.x) probe_quad<kWide, kMode, kVec, false, true>(a, T, L, q);
+      if (local == b.nu[2] - 1) {
+        const int64_t t0 = nq4 << 2;
+        if ((int64_t)threadIdx.x < a.n - t0) probe_one<kWide, kMode>(a, T, L, t0 + threadIdx.x);
+      }
     }
   }
   if (kMode == kAggSmem && held >= 0) {
@@ -364,7 +380,7 @@ struct sirius_batch_plan_s {
   size_t smem_for_grid = (size_t)-1;
 };
 
-typedef void (*probe_kernel_t)(const BatchHeader*, const BatchQuery*, int);
+typedef void (*probe_kernel_t)(const BatchHeader*, const BatchQuery*, int, unsigned long long*);
 
 // class bits: 1 two-column keys, 2 shared-memory aggregation, 4 16-byte column loads
 static probe_kernel_t probe_kernel_for(int c) {
@@ -469,7 +485,7 @@ static sirius_status enqueue_batch(sirius_batch_plan p, size_t smem, uint32_t cl
     PhaseTimer pt(timed ? s : nullptr, timed ? SIRIUS_PHASE_BATCH_PROBE : -1);
     for (int c = 0; c < 8; ++c) {
       if (!((classes >> c) & 1u)) continue;
-      probe_kernel_for(c)<<<p->grid_probe[c], kProbeThreads, (c & 2) ? smem : 0, s>>>(dH, dQ, c);
+      probe_kernel_for(c)<<<p->grid_probe[c], kProbeThreads, (c & 2) ? smem : 0, s>>>(dH, dQ, c, &dH->cls_next[c]);
       SIRIUS_LAUNCH_CHECK();
     }
   }
@@ -643,6 +659,18 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
     SIRIUS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_build, batch_build_kernel<false>, kBatchThreads, 0));
     p->grid_build = sm_count() * (per_build > 0 ? per_build : 1);
     p->smem_for_grid = smem;
+  }
+  // Claim size per class.  At least 32 units per block (large batches): 32 claims per block,
+  // for a short tail.  Fewer (smaller batches, e.g. served requests): one contiguous chunk per
+  // block, as a static split gives -- there a claim's round trip and the merge at every change
+  // of query cost more than the imbalance they would remove (measured: a served batch of 64
+  // queries, 17 units per block, lost a fifth of its peak rate with one-unit claims).
+  for (int c = 0; c < 8; ++c) {
+    const int64_t units = H->cls_u1[c] - H->cls_u0[c];
+    const int64_t grid = p->grid_probe[c] > 0 ? p->grid_probe[c] : 1;
+    const int64_t per_block = units / grid;
+    const int64_t chunk = per_block >= 32 ? per_block / 32 : (units + grid - 1) / grid;
+    H->cls_chunk[c] = chunk > 1 ? chunk : 1;
   }
 
   if (use_graph) {
