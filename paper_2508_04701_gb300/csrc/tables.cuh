@@ -59,11 +59,13 @@ __device__ __forceinline__ int64_t group_find_or_insert(int64_t* keys, uint32_t 
   if (key == kEmptyKey) return cap;
   uint32_t s = home_slot64((uint64_t)key, cap);
   for (uint32_t step = 0; step < cap; ++step) {
-    // A walk this long only happens near or past the limit.  Past it the call fails
-    // (TABLE_FULL) and its output is unspecified, so the walk stops: otherwise inserts would
-    // go on claiming slots until none is left and every further new key would walk the whole
-    // table.
-    if ((step & 63) == 63 && ld_relaxed_u64((const uint64_t*)distinct) >= limit) return -1;
+    // A walk this long only happens near or past the limit.  Past it -- once an insert has
+    // failed, which takes the count above the limit -- the call fails (TABLE_FULL) and its
+    // output is unspecified, so the walk stops: otherwise inserts would go on claiming slots
+    // until none is left and every further new key would walk the whole table.  A table
+    // holding exactly `limit` keys is still valid (an eighth of its slots are empty), and a
+    // lookup there may walk far: it must not stop.
+    if ((step & 63) == 63 && ld_relaxed_u64((const uint64_t*)distinct) > limit) return -1;
     int64_t cur = (int64_t)ld_relaxed_u64((const uint64_t*)&keys[s]);
     if (cur == key) return s;
     if (cur == kEmptyKey) {
