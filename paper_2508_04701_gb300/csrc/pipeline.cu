@@ -597,8 +597,14 @@ sirius_status launch_single(const SingleArgs& g, int threads, int per_sm, size_t
     SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  const int occ = occupancy_blocks(k, threads, smem);
-  if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+  // One block per SM (the default) always fits: 512 threads at the 128 registers the launch
+  // bound allows, and the shared memory raised above; only a larger request asks the runtime
+  // (a query per call would add its host time to every small query).
+  if (per_sm <= 0) per_sm = 1;
+  if (per_sm > 1) {
+    const int occ = occupancy_blocks(k, threads, smem);
+    if (per_sm > occ) per_sm = occ;
+  }
   int64_t work = (g.a.n >> 2) > g.m ? (g.a.n >> 2) : g.m;
   const int64_t other[4] = {g.jpairs, g.dpairs, (int64_t)g.a.gslots, g.bwords};
   for (int64_t w : other) work = w > work ? w : work;
