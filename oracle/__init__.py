@@ -9,5 +9,7 @@ from .relational import *  # noqa: F401,F403
 from .relational import __all__ as _rel_all
 from .strings import *  # noqa: F401,F403
 from .strings import __all__ as _str_all
+from .chunked import *  # noqa: F401,F403
+from .chunked import __all__ as _chunk_all
 
-__all__ = list(_rel_all) + list(_str_all)
+__all__ = list(_rel_all) + list(_str_all) + list(_chunk_all)

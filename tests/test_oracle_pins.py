@@ -388,6 +388,87 @@ def test_merge_partials_equals_whole():
         assert np.array_equal(m[c], w[c])
 
 
+def check_merge_sorted_brute(o, seed):
+    """merge_sorted_partials against the dictionary merge and against the group-by of all rows
+    at once (Python loop): keys include negatives and INT64_MIN, values both signs."""
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(0, 400))
+    keys = rng.integers(-6, 6, size=n).astype(np.int64)
+    keys[rng.random(n) < 0.05] = O.relational.INT64_MIN
+    vals = rng.integers(-10**12, 10**12, size=n).astype(np.int64)
+    cuts = np.sort(rng.integers(0, n + 1, size=int(rng.integers(1, 6))))
+    bounds = [0] + cuts.tolist() + [n]
+    parts = [O.groupby_loop(keys[a:b], vals[a:b]) for a, b in zip(bounds[:-1], bounds[1:])]
+    got = o.merge_sorted_partials(parts)
+    for want in (O.merge_partials(parts), O.groupby_loop(keys, vals)):
+        for c in ("key", "sum", "count", "min", "max"):
+            assert np.array_equal(np.asarray(got[c]), np.asarray(want[c])), c
+
+
+def check_chunk_plan(o):
+    """Chunk ranges cover rows 0..n-1 once each, in order, whatever n and the chunk size."""
+    for n in (0, 1, 2, 7, 100, 1001):
+        for c in (1, 3, 100, 1000, 5000):
+            r = o.chunk_plan(n, c)
+            covered = [i for a, b in r for i in range(a, b)]
+            assert covered == list(range(n)), (n, c)
+            assert all(b - a <= c for a, b in r)
+
+
+def check_chunked_equals_whole(o):
+    """The chunked, multi-process oracle gives the whole-table oracle's result on every
+    workload shape: one- and two-column keys, Zipf keys with (grp, flag) groups, a dim-side
+    predicate, filter dims of a star query."""
+    specs = [dg.plain_scale(n=230_001, m=20_000),
+             dg.plain_scale(n=120_003, m=9_000, composite=True),
+             dg.skewed(n=150_007, m=40_000),
+             dg.plain_scale(n=100_000, m=8_000, dt=20),
+             dg.star(n=90_001, m=7_000)]
+    specs[4] = dg.StarSpec(**{**specs[4].__dict__, "semi_m": 5_000})
+    got = o.query_results(specs, chunk_rows=40_000, workers=2)
+    for sp, g in zip(specs, got):
+        dim, fact = dg.gen_dim_host(sp), dg.gen_fact_host(sp)
+        kw = {}
+        if sp.dt:
+            kw.update(dim_op="lt", dim_literal=sp.dt)
+        if sp.semi:
+            kw["semi"] = dg.semi_args(sp, fact, dg.gen_semi_dims_host(sp))
+        want = O.pipeline(fact, dim, "lt", sp.t, **kw)
+        assert want["key"].size > 0
+        for c in ("key", "sum", "count", "min", "max"):
+            assert np.array_equal(g[c], want[c]), (sp.name, c)
+    # a prefix of the rows: the same as the whole-table oracle on that prefix
+    sp = specs[0]
+    g = o.query_results([sp], chunk_rows=30_000, workers=1, rows=70_000)[0]
+    want = O.pipeline(dg.gen_fact_host(sp, 0, 70_000), dg.gen_dim_host(sp), "lt", sp.t)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(g[c], want[c]), c
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_merge_sorted_partials_brute(seed):
+    check_merge_sorted_brute(O, seed)
+
+
+def test_chunk_plan_covers_rows_once():
+    check_chunk_plan(O)
+
+
+def test_chunked_oracle_equals_whole_table():
+    check_chunked_equals_whole(O)
+
+
+def test_hot_oracle_equals_whole_table():
+    sp = dg.plain_scale(n=300_000, m=15_000)
+    with O.HotOracle(sp, rows=250_000, workers=2, chunk_rows=20_000) as h:
+        assert h.workers == 2
+        (a, _), (b, sec) = h.run(), h.run()
+    want = O.pipeline(dg.gen_fact_host(sp, 0, 250_000), dg.gen_dim_host(sp), "lt", sp.t)
+    for c in ("key", "sum", "count", "min", "max"):
+        assert np.array_equal(a[c], want[c]) and np.array_equal(b[c], want[c]), c
+    assert sec > 0
+
+
 def test_restrict_dim_selects_groups():
     rng = np.random.default_rng(4)
     fact = {"fk": rng.integers(0, 300, size=20000).astype(np.int32),
@@ -571,6 +652,27 @@ def _groupby_string_max_is_min(offsets, chars, vals):
     return r
 
 
+def _merge_min_of_first_part(parts):
+    r = O.merge_sorted_partials(parts)
+    first = {int(k): int(v) for k, v in zip(parts[0]["key"], parts[0]["min"])} if parts else {}
+    r["min"] = np.array([first.get(int(k), int(v)) for k, v in zip(r["key"], r["min"])], dtype=np.int64)
+    return r
+
+
+def _merge_counts_parts(parts):
+    r = O.merge_sorted_partials(parts)
+    r["count"] = O.merge_sorted_partials([dict(p, count=np.ones_like(p["count"])) for p in parts])["count"]
+    return r
+
+
+def _chunk_plan_overlaps(n, c):
+    return [(max(0, a - 1), b) for a, b in O.chunk_plan(n, c)]
+
+
+def _chunk_plan_gap(n, c):
+    return [(a, max(a, b - 1)) for a, b in O.chunk_plan(n, c)]
+
+
 MUTANTS = [
     ("dictionary by last occurrence", dict(dict_encode=_dict_last_occurrence),
      lambda m: [check_dict_brute(m, s) for s in range(12)]),
@@ -604,6 +706,12 @@ MUTANTS = [
      lambda m: [check_groupby_brute(m, s) for s in range(5)]),
     ("min is first value (pipeline)", dict(groupby_agg=_min_is_first),
      lambda m: [check_pipeline_invariants(m, s) for s in range(5)]),
+    ("merge takes MIN of the first part", dict(merge_sorted_partials=_merge_min_of_first_part),
+     lambda m: [check_merge_sorted_brute(m, s) for s in range(10)]),
+    ("merge counts parts, not rows", dict(merge_sorted_partials=_merge_counts_parts),
+     lambda m: [check_merge_sorted_brute(m, s) for s in range(10)]),
+    ("chunks overlap", dict(chunk_plan=_chunk_plan_overlaps), lambda m: check_chunk_plan(m)),
+    ("chunks leave gaps", dict(chunk_plan=_chunk_plan_gap), lambda m: check_chunk_plan(m)),
     ("group flag sign-extended", dict(pack_group=_flag_signed_shift),
      lambda m: [check_composite_and_group_keys(m, s) for s in range(3)]),
 ]
