@@ -50,7 +50,10 @@ def parse(argv=None):
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--probe-variant", default="auto", choices=["auto", "direct", "staged"])
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
+    p.add_argument("--cpu-sample-rows", type=int, default=0,
+                   help="fact rows the CPU baseline runs the oracle on (0: the whole workload)")
+    p.add_argument("--ref-rows", type=int, default=100_000_000,
+                   help="fact rows per step of the reference arm (the oracle on the host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true")
@@ -185,40 +188,40 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU baseline
 def cpu_baseline(spec, rows: int):
-    """The oracle as it stands, on the first `rows` fact rows against the full dim table."""
-    import numpy as np  # noqa: F401
+    """The oracle as it stands on every host core: the first `rows` fact rows (0 = all) in
+    chunks over one worker process per core, each worker's chunks generated beforehand (hot
+    inputs, as on the GPU), one timed run from the start message to the merged result."""
     import oracle
-    from paper_2508_04701_gb300 import datagen as dg
-    rows = min(rows, spec.n)
-    dim = dg.gen_dim_host(spec)
-    fact = dg.gen_fact_host(spec, 0, rows, dim=dim)
+    rows = spec.n if rows <= 0 else min(rows, spec.n)
     t0 = time.perf_counter()
-    res = oracle.pipeline(fact, dim, "lt", spec.t)
-    dt = time.perf_counter() - t0
-    return {"value": rows / dt, "unit": "rows/s", "cores": 1, "kind": "oracle",
+    with oracle.HotOracle(spec, rows=rows) as h:
+        setup = time.perf_counter() - t0
+        res, dt = h.run()
+        cores = h.workers
+    return {"value": rows / dt, "unit": "rows/s", "cores": cores, "kind": "oracle",
             "sample": f"first {rows} of {spec.n} fact rows of the same query against the full "
-                      f"{spec.m}-row dim table; {len(res['key'])} groups; {dt:.2f} s; numpy, one thread",
+                      f"{spec.m}-row dim table, in chunks of up to 20M rows over {cores} worker processes "
+                      f"(one per core of sched_getaffinity); {len(res['key'])} groups; one run "
+                      f"of {dt:.2f} s after {setup:.1f} s of generation",
             "seconds": dt}
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle timed on the host cores for the same metric."""
+    """--impl reference: the CPU oracle timed on the host cores for the same metric.  Each step
+    runs the oracle over a bounded sample of the workload (its first `--ref-rows` fact rows,
+    against the full dim table) on every host core; inputs are generated once, before the
+    warm-up steps."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    from paper_2508_04701_gb300 import datagen as dg
     spec, _ = spec_for(args.workload, 0)
-    rows = min(spec.n, 2_000_000)
-    dim = dg.gen_dim_host(spec)
-    fact = dg.gen_fact_host(spec, 0, rows, dim=dim)
-    for _ in range(args.warmup):
-        oracle.pipeline(fact, dim, "lt", spec.t)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.pipeline(fact, dim, "lt", spec.t)
-        times.append(time.perf_counter() - t0)
+    rows = min(spec.n, args.ref_rows)
+    with oracle.HotOracle(spec, rows=rows) as h:
+        for _ in range(args.warmup):
+            h.run()
+        times = [h.run()[1] for _ in range(args.steps)]
+        cores = h.workers
     per = sum(times) / len(times)
     value = rows / per
     line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -226,9 +229,10 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "fact_rows_per_step": rows, "dim_rows": spec.m,
                        "predicate": f"pred < {spec.t}"},
-            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: the first {rows} of {spec.n} fact rows against the "
-                                       f"full {spec.m}-row dim; numpy, one thread"},
+                                       f"full {spec.m}-row dim, in chunks of up to 20M rows over {cores} worker "
+                                       "processes (one per core of sched_getaffinity)"},
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -461,8 +465,11 @@ def run_served(S, torch, args, dev, rank):
     srv = serve.Server(pool, slots=4, max_batch=64, budget_bytes=150 * 10**9)
     warm = serve.poisson_requests(args.serve_rate, 0.3, len(pool.facts), seed=rank + 99)
     srv.run(warm)
+    batches0 = srv.batches
     srv.run(reqs)
     st = serve.latency_stats(reqs, warmup=1.0)
+    st.update(overlap_stats(srv, reqs))
+    st["batches_this_run"] = srv.batches - batches0
     rows = sum(pool.fact_rows[r.fact_id] for r in reqs if r.arrival >= 1.0)
     st["rows_per_s"] = rows / (args.serve_seconds) if args.serve_seconds > 0 else 0.0
     st["batches"] = srv.batches
@@ -479,17 +486,42 @@ def run_served(S, torch, args, dev, rank):
     sweep = []
     for k, rate in enumerate(float(x) for x in args.serve_sweep.split(",") if x.strip()):
         rq = serve.poisson_requests(rate, 1.3, len(pool.facts), seed=rank + 1000 + k)
+        b0 = srv.batches
         srv.run(rq)
         sw = serve.latency_stats(rq, warmup=0.3)
+        sw.update(overlap_stats(srv, rq))
+        sw["batches"] = srv.batches - b0
         sw["offered_qps"] = rate
         done = [r for r in rq if r.arrival >= 0.3 and r.done == r.done]  # completed (done is not NaN)
         span = (max(r.done for r in done) - min(r.arrival for r in done)) if done else 0.0
         sw["rows_per_s"] = sum(pool.fact_rows[r.fact_id] for r in done) / span if span > 0 else 0.0
         sw["statuses_ok"] = all(r.status == 0 for r in rq)
         sweep.append({k2: sw.get(k2) for k2 in ("offered_qps", "throughput_qps", "p50_ms", "p99_ms", "rows_per_s",
-                                                "requests", "statuses_ok")})
+                                                "requests", "statuses_ok", "batches", "max_busy_slots",
+                                                "max_busy_device", "device_busy_frac", "host_ms_per_request",
+                                                "host_busy_frac")})
     return {"rate_qps": args.serve_rate, "seconds": args.serve_seconds, "served": st,
             "plain_fifo": fst, "fifo_seconds": args.fifo_seconds, "rate_sweep": sweep}
+
+
+def overlap_stats(srv, reqs):
+    """How the last Server.run used the device and the host: the most batches in flight on the
+    device at once (from per-batch CUDA events), the fraction of the run's device span with at
+    least one batch in flight, the most slots the host loop had busy at once, and the host
+    loop's own time (launching batches, reading results back) per request and as a fraction of
+    the run's wall time."""
+    spans = srv.spans
+    out = {"max_busy_slots": srv.max_busy_slots, "max_busy_device": srv.max_busy_device}
+    if spans:
+        t0, t1 = min(a for a, _ in spans), max(b for _, b in spans)
+        out["device_busy_frac"] = srv.device_busy_ms() / (t1 - t0) if t1 > t0 else None
+    n = max(len(reqs), 1)
+    host_s = srv.host_launch_s + srv.host_complete_s
+    out["host_ms_per_request"] = host_s * 1e3 / n
+    done = [r.done for r in reqs if r.done == r.done]
+    wall = max(done) - min(r.arrival for r in reqs) if done else 0.0
+    out["host_busy_frac"] = host_s / wall if wall > 0 else None
+    return out
 
 
 def run_configs(S, torch, dev, rank):

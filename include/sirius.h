@@ -107,7 +107,13 @@ sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t op, int32_t
  * device looks up the array's device address (with that device current) and caches it; make
  * that first call before any stream capture.  All calls share the one array, which keeps the
  * last call's contents: two calls that may overlap on the GPU (other streams, other threads)
- * race and must be serialised by the caller. */
+ * race and must be serialised by the caller.  The cached address belongs to the device's
+ * current context: after cudaDeviceReset (or any teardown of the primary context) it is stale,
+ * so a process that resets a device must not call this function on that device again.  A
+ * device-side failure (a look-back wait that ran out: SIRIUS_ERR_TIMEOUT) is returned only
+ * when h_count is given -- the call then reads the status back; with h_count NULL the call is
+ * asynchronous, returns SIRIUS_OK after the launch, and the status stays in the library's
+ * array until the next call clears it. */
 int64_t sirius_filter_static_max_rows(void);
 sirius_status sirius_filter_static(const int32_t* d_col, int64_t n, int32_t op, int32_t literal,
                                    uint32_t* d_row_ids, int64_t* d_count, int64_t* h_count,

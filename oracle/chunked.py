@@ -183,7 +183,7 @@ class HotOracle:
     the start message to the last worker's reply plus the final merge."""
 
     def __init__(self, spec, rows: Optional[int] = None, workers: Optional[int] = None,
-                 chunk_rows: int = 5_000_000):
+                 chunk_rows: int = 20_000_000):
         self.spec = spec
         self.rows = spec.n if rows is None else min(int(rows), spec.n)
         self.workers = max(1, min(workers or host_cores(), max(1, self.rows // 100_000)))

@@ -143,7 +143,10 @@ class _Slot:
         self.h_groups = torch.empty(max_batch, dtype=torch.int64, pin_memory=True)
         self.h_status = torch.empty(max_batch, dtype=torch.int32, pin_memory=True)
         self.views = [_OutView(self, i) for i in range(max_batch)]
-        self.event = torch.cuda.Event()
+        # device-side span of the batch in flight: from the stream reaching the batch to its
+        # result copies finishing (timing events, comparable across streams)
+        self.start_event = torch.cuda.Event(enable_timing=True)
+        self.event = torch.cuda.Event(enable_timing=True)
         self.reqs: List[Request] = []
         self.bytes = 0
 
@@ -169,6 +172,15 @@ class Server:
         self.slots = [_Slot(max_batch, self.out_cap, max_batch * probe_bytes + 4096, dev) for _ in range(slots)]
         self.admission = Admission(budget_bytes, pool.bytes())
         self.batches = 0
+        # overlap and attribution of the last run(): device spans of its batches (ms from the
+        # run's reference event), the most batches in flight on the device at once, the most
+        # slots busy at once as the host loop saw them, and the host loop's own time
+        self.spans: List[tuple] = []
+        self.max_busy_device = 0
+        self.max_busy_slots = 0
+        self.host_launch_s = 0.0
+        self.host_complete_s = 0.0
+        self._ref = None
         # one descriptor per fact table; a request copies it and sets its threshold
         self._base_desc = [pool.desc(f, 50) for f in range(len(pool.facts))]
         self._keep = self._base_desc
@@ -184,6 +196,7 @@ class Server:
         descs = [self._desc(r) for r in reqs]
         idx = [self.pool.index(r.fact_id) for r in reqs]
         with torch.cuda.stream(slot.stream):
+            slot.start_event.record(slot.stream)
             slot.plan.run(descs, slot.views[:nb], indexes=idx, rows_per_unit=self.rows_per_unit,
                           use_graph=self.use_graph, scratch=slot.scratch, stream=slot.stream, sync=False)
             slot.h_out[:nb].copy_(slot.d_out[:nb], non_blocking=True)
@@ -196,6 +209,7 @@ class Server:
         slot.reqs = reqs
 
     def _complete(self, slot: _Slot, now: float, keep_results: bool):
+        self.spans.append((self._ref.elapsed_time(slot.start_event), self._ref.elapsed_time(slot.event)))
         for i, r in enumerate(slot.reqs):
             r.done = now
             r.groups = int(slot.h_groups[i])
@@ -212,6 +226,10 @@ class Server:
         """Serve requests (sorted by arrival, times relative to the call); returns them filled."""
         pending = deque()
         todo = deque(sorted(requests, key=lambda r: r.arrival))
+        self.spans, self.max_busy_slots = [], 0
+        self.host_launch_s = self.host_complete_s = 0.0
+        self._ref = torch.cuda.Event(enable_timing=True)
+        self._ref.record(torch.cuda.current_stream(self.pool.device))
         t0 = time.perf_counter()
         finished = 0
         total = len(requests)
@@ -222,7 +240,9 @@ class Server:
             for slot in self.slots:
                 if slot.busy and slot.event.query():
                     finished += len(slot.reqs)
-                    self._complete(slot, time.perf_counter() - t0, keep_results)
+                    h0 = time.perf_counter()
+                    self._complete(slot, h0 - t0, keep_results)
+                    self.host_complete_s += time.perf_counter() - h0
             for slot in self.slots:
                 if slot.busy or not pending:
                     continue
@@ -236,10 +256,42 @@ class Server:
                 if batch:
                     slot.bytes = len(batch) * self.req_bytes
                     self.admission.take(slot.bytes)
-                    self._launch(slot, batch, time.perf_counter() - t0)
+                    h0 = time.perf_counter()
+                    self._launch(slot, batch, h0 - t0)
+                    self.host_launch_s += time.perf_counter() - h0
+                    self.max_busy_slots = max(self.max_busy_slots, sum(1 for x in self.slots if x.busy))
             if poll_sleep:
                 time.sleep(poll_sleep)
+        self.max_busy_device = max_overlap(self.spans)
         return requests
+
+    def device_busy_ms(self) -> float:
+        """Time (ms) during which at least one batch of the last run was in flight on the device
+        (the union of the batches' device spans)."""
+        return union_length(self.spans)
+
+
+def max_overlap(spans) -> int:
+    """The largest number of (start, end) intervals that contain one instant."""
+    ev = sorted([(a, 1) for a, b in spans] + [(b, -1) for a, b in spans], key=lambda x: (x[0], x[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def union_length(spans) -> float:
+    """Total length covered by at least one (start, end) interval."""
+    tot, end = 0.0, None
+    for a, b in sorted(spans):
+        if end is None or a > end:
+            tot += b - a
+            end = b
+        elif b > end:
+            tot += b - end
+            end = b
+    return tot
 
 
 def sequential_fifo(pool: ResidentPool, requests: List[Request], keep_results: bool = False):

@@ -62,6 +62,8 @@ def test_overlapping_batches_with_graphs_off(env):
     reqs = serve.poisson_requests(rate=20000, duration=0.01, n_facts=len(pool.facts), seed=4)
     srv = serve.Server(pool, slots=4, max_batch=8, use_graph=False, rows_per_unit=16384)
     srv.run(reqs, keep_results=True)
+    assert srv.max_busy_slots > 1             # batches were in flight together
+    assert srv.max_busy_device >= 1 and len(srv.spans) == srv.batches
     for r in reqs[:10]:
         assert same(r.result, oracle_of(host, r))
 

@@ -49,3 +49,18 @@ def test_latency_stats():
     assert st["throughput_qps"] == pytest.approx(1000 / (0.999 + 0.002), rel=1e-6)
     # warm-up requests are excluded
     assert serve.latency_stats(reqs, warmup=0.5)["requests"] == 500
+
+
+def test_span_overlap_and_union():
+    """Device-overlap bookkeeping of the serving loop: the most spans containing one instant,
+    and the length their union covers (brute force over a fine grid)."""
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        k = int(rng.integers(0, 8))
+        a = rng.integers(0, 50, size=k)
+        spans = [(float(x), float(x + rng.integers(1, 20))) for x in a]
+        grid = np.arange(0, 80, 0.5) + 0.25
+        cover = [sum(1 for s, e in spans if s <= g < e) for g in grid]
+        assert serve.max_overlap(spans) == max(cover, default=0)
+        assert serve.union_length(spans) == pytest.approx(0.5 * sum(1 for c in cover if c > 0))
+    assert serve.max_overlap([(0.0, 1.0), (1.0, 2.0)]) == 1      # touching spans do not overlap
