@@ -308,8 +308,15 @@ typedef struct {
                                each partition in shared memory (group table of at most
                                2^19 + 1 slots, group_cap_hint <= 2^18; larger tables use 2);
                                4 global reductions behind a per-block cache of 2048
-                               hot groups in shared memory (skewed keys).  Auto: 1 when it
-                               fits, else 4 from 1Mi fact rows, else 2 */
+                               hot groups in shared memory (skewed keys); 5 routed: the group
+                               slots are dealt out to the blocks of one cooperative launch,
+                               each aggregating its share in shared memory, and every joined
+                               row's (slot, value) travels to its owner through an exchange
+                               buffer in scratch, one grid-wide barrier per round of rows
+                               (group tables up to 256 x 2000 slots; larger tables and star
+                               queries use 4; duplicate build keys make the launch use global
+                               reductions).  Auto: 1 when it fits, else 4 from 1Mi fact rows,
+                               else 2 */
   int64_t group_cap_hint;   /* expected distinct group keys in the dim; 0 -> m */
   float load_factor;        /* join table load factor; 0 -> default 0.5 */
   int32_t block_threads;    /* probe kernel block size; 0 -> default */

@@ -25,6 +25,7 @@
 #include "pipeline.cuh"
 #include "partagg.cuh"
 #include "probe_staged.cuh"
+#include "routed.cuh"
 
 namespace sirius {
 
@@ -391,43 +392,6 @@ struct SingleArgs {
   PipeOut out;
 };
 
-// Spins of one barrier wait (64 ns sleeps: about half a second) before it gives up.
-constexpr uint32_t kGridBarrierSpins = 1u << 23;
-
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  return cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(*const_cast<uint32_t*>(p))
-      .load(cuda::memory_order_acquire);
-}
-
-// Grid-wide barrier of the single-launch kernel.  Thread 0 of each block arrives on `count`
-// (zero when the launch started) and waits until `target` = barriers so far x blocks arrivals
-// have been made; the fences order every block's writes before the barrier ahead of every
-// read after it.  The wait is bounded (max_spins sleeps of 64 ns): when it runs out, the block
-// records SIRIUS_ERR_TIMEOUT in the run header and the caller leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, int32_t* status,
-                                             uint32_t max_spins = kGridBarrierSpins) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    atomicAdd(count, 1u);
-    uint32_t spins = 0;
-    while (ld_acquire_u32(count) < target) {
-      if (++spins >= max_spins) {
-        set_status(status, SIRIUS_ERR_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(64);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 template <bool kWide, int kMode, bool kVec>
 __global__ void __launch_bounds__(512, 1)
 single_query_kernel(SingleArgs g) {
@@ -573,6 +537,53 @@ sirius_status launch_staged(const ProbeArgs& a, PipeHeader* phdr, cudaStream_t s
   return SIRIUS_OK;
 }
 
+// The routed probe: one cooperative launch of every resident block (the exchange was sized for
+// r.route_blocks); its barrier counter is cleared first.
+template <bool kWide>
+sirius_status launch_routed(const ProbeArgs& a, const RunView& r, bool vec, cudaStream_t s) {
+  auto k = vec ? routed::probe_routed_kernel<kWide, true> : routed::probe_routed_kernel<kWide, false>;
+  const size_t smem = routed::smem_bytes(r.route_R);
+  SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int per_sm = occupancy_blocks(k, routed::kThreads, smem);
+  int blocks = sm_count() * (per_sm < routed::kBlocksPerSm ? per_sm : routed::kBlocksPerSm);
+  if (blocks > r.route_blocks) blocks = r.route_blocks;
+  // fewer resident blocks than planned: fewer owners, each with a larger share (the exchange,
+  // sized for the plan, holds the smaller plan: P' x B' x C' <= P x B x C)
+  int logP = r.route_logP;
+  while (logP > 0 && (1 << logP) > blocks) --logP;
+  const int64_t R = ((int64_t)a.gslots + (1 << logP) - 1) >> logP;
+  if (logP != r.route_logP && (R > (int64_t)routed::kMaxOwnerSlots || routed::smem_bytes((uint32_t)R) > smem)) {
+    set_error("pipeline: routed aggregation needs %d resident blocks, %d fit", r.route_blocks, blocks);
+    return SIRIUS_ERR_INVALID;
+  }
+  routed::RouteArgs ra;
+  ra.tval = r.rval;
+  ra.tls = r.rls;
+  ra.fill = r.rfill;
+  ra.bar = reinterpret_cast<uint32_t*>(&r.phdr->pad[1]);
+  ra.status = &r.phdr->status;
+  ra.logP = logP;
+  ra.R = (uint32_t)R;
+  ra.C = routed::run_capacity(1 << logP, routed::kIters);
+  ra.iters = routed::kIters;
+  const int64_t per_round = (int64_t)blocks * routed::kIters * routed::kThreads;  // quads
+  ra.rounds = ((a.n >> 2) + per_round - 1) / per_round;
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(ra.bar, 0, sizeof(uint32_t), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3((unsigned)routed::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  SIRIUS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, a, ra));
+  SIRIUS_LAUNCH_CHECK();
+  return SIRIUS_OK;
+}
+
 template <bool kWide, bool kSemi>
 sirius_status dispatch_probe(const ProbeArgs& a, const SemiArgs& sa, int mode, bool vec, int threads, int bps,
                              size_t smem, cudaStream_t s) {
@@ -697,6 +708,18 @@ RunLayout run_layout(int64_t gcap, int64_t n, int agg_mode) {
   R.mode = choose_mode(agg_mode, R.gslots, n);
   R.off_aggs = 256;
   size_t end = align_up(R.off_aggs + (size_t)R.gslots * sizeof(Agg), 256);
+  if (R.mode == kAggRouted) {
+    const RoutePlan rp = route_plan(R.gslots);
+    R.route_blocks = rp.blocks;
+    R.route_logP = rp.logP;
+    R.route_R = rp.R;
+    R.route_C = rp.C;
+    const size_t tuples = (size_t)2 * ((size_t)1 << rp.logP) * rp.blocks * rp.C;
+    R.off_rval = end;
+    R.off_rls = align_up(R.off_rval + tuples * 8, 256);
+    R.off_rfill = align_up(R.off_rls + tuples * 2, 256);
+    end = align_up(R.off_rfill + (size_t)2 * rp.blocks * ((size_t)1 << rp.logP) * 4, 256);
+  }
   if (R.mode == kAggPart) {
     R.parts = part::parts_for(R.gslots);
     R.ntiles = part::tiles_for(n);
@@ -733,6 +756,14 @@ RunView run_view(const RunLayout& R, char* base) {
   r.mode = R.mode;
   r.parts = R.parts;
   r.ntiles = R.ntiles;
+  const bool rt = R.mode == kAggRouted;
+  r.rval = rt ? (int64_t*)(base + R.off_rval) : nullptr;
+  r.rls = rt ? (uint16_t*)(base + R.off_rls) : nullptr;
+  r.rfill = rt ? (uint32_t*)(base + R.off_rfill) : nullptr;
+  r.route_blocks = R.route_blocks;
+  r.route_logP = R.route_logP;
+  r.route_R = R.route_R;
+  r.route_C = R.route_C;
   r.tgs = R.mode == kAggPart ? (uint32_t*)(base + R.off_tgs) : nullptr;
   r.tval = R.mode == kAggPart ? (int64_t*)(base + R.off_tval) : nullptr;
   r.prefix = R.mode == kAggPart ? (int32_t*)(base + R.off_prefix) : nullptr;
@@ -758,7 +789,7 @@ sirius_status validate_fact(const sirius_pipeline_desc* q) {
   SIRIUS_REQUIRE(q->n == 0 || (q->fk && q->pred && q->val), "pipeline: NULL fact column");
   SIRIUS_REQUIRE(q->op >= SIRIUS_LT && q->op <= SIRIUS_NE, "pipeline: bad comparison %d", q->op);
   SIRIUS_REQUIRE(q->aggs <= SIRIUS_AGG_ALL, "pipeline: bad aggregate mask");
-  SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= 4, "pipeline: bad agg_mode %d", q->agg_mode);
+  SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= kAggRouted, "pipeline: bad agg_mode %d", q->agg_mode);
   SIRIUS_REQUIRE(q->block_threads == 0 || (q->block_threads % 32 == 0 && q->block_threads >= 64 &&
                                            q->block_threads <= 512),
                  "pipeline: block_threads must be a multiple of 32 in [64, 512]");
@@ -780,6 +811,24 @@ static sirius_status validate_pair(const sirius_pipeline_desc* q) {
 
 // Shared-memory table when the group table fits a block; otherwise partitioned aggregation
 // for large inputs whose group table has at most kMaxParts partitions; otherwise reductions.
+// The routed probe's plan for a group table of gslots slots: the blocks of its cooperative
+// launch (all resident), owners = the largest power of two not above min(blocks, 256), slots
+// per owner, run capacity.  R = 0 when the owners' shares do not fit shared memory.
+RoutePlan route_plan(int64_t gslots) {
+  RoutePlan p;
+  p.blocks = sm_count() * routed::kBlocksPerSm;
+  int P = 1, logP = 0;
+  while (2 * P <= p.blocks && 2 * P <= routed::kMaxOwners) {
+    P *= 2;
+    ++logP;
+  }
+  p.logP = logP;
+  const int64_t R = (gslots + P - 1) / P;
+  p.R = R <= (int64_t)routed::kMaxOwnerSlots ? (uint32_t)R : 0u;
+  p.C = routed::run_capacity(P, routed::kIters);
+  return p;
+}
+
 int choose_mode(int agg_mode, int64_t gslots, int64_t n) {
   const bool fits = (int64_t)smem_aggs_bytes((uint32_t)(gslots < (1 << 30) ? gslots : (1 << 30)), false) <= kSmemAggMaxBytes;
   const bool part_ok = gslots <= (int64_t)part::kMaxParts * part::kPartSlots && n > 0;
@@ -787,6 +836,7 @@ int choose_mode(int agg_mode, int64_t gslots, int64_t n) {
   if (agg_mode == kAggGlobal) return kAggGlobal;
   if (agg_mode == kAggPart) return part_ok ? kAggPart : kAggGlobal;
   if (agg_mode == kAggHot) return n > 0 ? kAggHot : kAggGlobal;
+  if (agg_mode == kAggRouted) return (n > 0 && route_plan(gslots).R > 0) ? kAggRouted : (n > 0 ? kAggHot : kAggGlobal);
   if (fits) return kAggSmem;
   // large group tables: the hot-group cache (measured: skewed 300M-row query 38.5 -> 3.3 ms,
   // uniform 600M-row query 5.31 -> 5.15 ms against plain reductions)
@@ -888,13 +938,17 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   SemiArgs sa;
   sa.nsemi = nsemi;
   for (int i = 0; i < kMaxSemi; ++i) sa.semi[i] = i < nsemi ? semi[i] : SemiView{};
-  const int mode = r.mode;
+  const int mode = (r.mode == kAggRouted && nsemi > 0) ? kAggHot : r.mode;
   bool vec = vec_columns(q);
   for (int i = 0; i < nsemi; ++i)  // a star query's key columns take the vector loads too
     vec = vec && ((uintptr_t)semi[i].fk & 15) == 0 && (!semi[i].fk_hi || ((uintptr_t)semi[i].fk_hi & 15) == 0);
   if (mode == kAggPart) {
     part::PartArgs pa{r.tgs, r.tval, r.prefix, r.ntiles, r.parts, 0};
     return d.key_width == 8 ? launch_part<true>(a, pa, vec, s) : launch_part<false>(a, pa, vec, s);
+  }
+  if (mode == kAggRouted && nsemi == 0) {
+    PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
+    return d.key_width == 8 ? launch_routed<true>(a, r, vec, s) : launch_routed<false>(a, r, vec, s);
   }
   const bool staged_ok = mode == kAggGlobal && vec && ((uintptr_t)q->val & 15) == 0;
   if (staged_ok && q->probe_variant == 2 && nsemi == 0) {
@@ -1063,9 +1117,13 @@ static sirius_status semi_build(const sirius_pipeline_desc* q, char* base, SemiV
   return SIRIUS_OK;
 }
 
-// A star query takes no partitioned aggregation (its probe pass is the fused one).
+// A star query takes neither partitioned nor routed aggregation (its probe pass is the star
+// kernel): those requests run with global reductions or the hot-group cache.
 static int star_agg_mode(const sirius_pipeline_desc* q) {
-  return (q->nsemi > 0 && q->agg_mode == kAggPart) ? kAggGlobal : q->agg_mode;
+  if (q->nsemi <= 0) return q->agg_mode;
+  if (q->agg_mode == kAggPart) return kAggGlobal;
+  if (q->agg_mode == kAggRouted) return kAggHot;
+  return q->agg_mode;
 }
 
 extern "C" size_t sirius_pipeline_scratch_bytes(const sirius_pipeline_desc* q) {

@@ -8,7 +8,7 @@
 
 namespace sirius {
 
-enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2, kAggPart = 3, kAggHot = 4 };
+enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2, kAggPart = 3, kAggHot = 4, kAggRouted = 5 };
 constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up to 3510 slots
 
 // Build side ("dim index"): [DimHeader | JoinHeader + join slots | group keys[gcap + 1]].
@@ -54,6 +54,11 @@ struct RunLayout {
   int parts = 0;          // partitioned mode: partitions and pass-1 tiles
   int64_t ntiles = 0;
   size_t off_aggs = 256, off_tgs = 0, off_tval = 0, off_prefix = 0, total = 0;
+  // routed mode: blocks of the launch the exchange is sized for, owners (2^logP), slots per
+  // owner, run capacity; exchange values, local slots, run lengths
+  int route_blocks = 0, route_logP = 0;
+  uint32_t route_R = 0, route_C = 0;
+  size_t off_rval = 0, off_rls = 0, off_rfill = 0;
 };
 
 struct DimView {
@@ -79,6 +84,11 @@ struct RunView {
   int mode;
   int parts;
   int64_t ntiles;
+  int64_t* rval;      // routed mode: exchange buffers (nullptr otherwise)
+  uint16_t* rls;
+  uint32_t* rfill;
+  int route_blocks, route_logP;
+  uint32_t route_R, route_C;
 };
 
 struct PipeOut {
@@ -314,13 +324,15 @@ __device__ __forceinline__ void load_bucket(const void* slots, uint32_t s, uint6
   else ldg_bucket(p, w[0], w[1], w[2], w[3]);
 }
 
-// Probe up to four rows (bit r of `bits` set = row r selected).  The home bucket of every
-// selected row is loaded before any row is examined, so four sector misses are in flight
-// together; a walk continues bucket by bucket only past full buckets.  kFresh: the join
-// structures were built earlier in the same launch (read through L2 only).
-template <bool kWide, int kMode, bool kFresh = false>
-__device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, uint32_t bits,
-                                           const uint64_t (&key)[4], const int64_t (&v)[4]) {
+// Probe up to four rows (bit r of `bits` set = row r selected) and hand every (row, group slot,
+// value) match to emit(r, slot, value).  The home bucket of every selected row is loaded before
+// any row is examined, so four sector misses are in flight together; a walk continues bucket by
+// bucket only past full buckets.  kFresh: the join structures were built earlier in the same
+// launch (read through L2 only).  Without duplicate build keys a row matches at most once.
+// kRows < 4: the hash-table walk covers rows 0 .. kRows-1 only (fewer buckets held at once).
+template <bool kWide, bool kFresh, int kRows = 4, class Emit>
+__device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup& L, uint32_t bits,
+                                                const uint64_t (&key)[4], const int64_t (&v)[4], Emit&& emit) {
   if (!kWide && L.direct) {
     // dense keys: one 4-byte read of the direct array per selected row, all four in flight
     uint32_t gs[4];
@@ -332,7 +344,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (gs[r] != kEmpty32) aggregate<kMode>(a, T, gs[r], v[r]);
+      if (gs[r] != kEmpty32) emit(r, gs[r], v[r]);
     return;
   }
   if (L.bloom) {
@@ -344,17 +356,17 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
   }
   const bool dups = L.dups;
   constexpr int kPer = kWide ? 2 : 4;  // slots per bucket
-  uint32_t s[4];
-  uint64_t w[4][4];
+  uint32_t s[kRows];
+  uint64_t w[kRows][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < kRows; ++r) {
     if ((bits >> r) & 1u) {
       s[r] = kWide ? home_slot64(key[r], a.jcap) : home_slot32((uint32_t)key[r], a.jcap);
       load_bucket<kWide, kFresh>(a.jslots, s[r], w[r]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < kRows; ++r) {
     if (!((bits >> r) & 1u)) continue;
     uint32_t slot = s[r];
     for (uint32_t step = 0; step < a.jcap; step += kPer) {
@@ -367,7 +379,7 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
           if (p == kEmpty32) {
             stop = true;
           } else if (k == key[r]) {
-            aggregate<kMode>(a, T, p, v[r]);
+            emit(r, p, v[r]);
             stop = !dups;
           }
         }
@@ -378,6 +390,14 @@ __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T
       load_bucket<kWide, kFresh>(a.jslots, slot, w[r]);
     }
   }
+}
+
+// The same, aggregating every match into the group table (kMode: where the aggregates live).
+template <bool kWide, int kMode, bool kFresh = false>
+__device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, uint32_t bits,
+                                           const uint64_t (&key)[4], const int64_t (&v)[4]) {
+  probe_rows_emit<kWide, kFresh>(a, L, bits, key, v,
+                                 [&](int, uint32_t gs, int64_t val) { aggregate<kMode>(a, T, gs, val); });
 }
 
 // Filter, probe and aggregate the four rows of quad q (rows 4q .. 4q+3, all < n).
@@ -698,6 +718,44 @@ __device__ __forceinline__ bool direct_applies(const DimView& d, int64_t m) {
   return range >= 1 && range <= d.dcap;
 }
 
+// ------------------------------------------------------------------ grid-wide barrier
+// Spins of one barrier wait (64 ns sleeps: about half a second) before it gives up.
+constexpr uint32_t kGridBarrierSpins = 1u << 23;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  return cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(*const_cast<uint32_t*>(p))
+      .load(cuda::memory_order_acquire);
+}
+
+// Grid-wide barrier of the cooperative launches (the single-launch pipeline, the routed probe).  Thread 0 of each block arrives on `count`
+// (zero when the launch started) and waits until `target` = barriers so far x blocks arrivals
+// have been made; the fences order every block's writes before the barrier ahead of every
+// read after it.  The wait is bounded (max_spins sleeps of 64 ns): when it runs out, the block
+// records SIRIUS_ERR_TIMEOUT in the run header and the caller leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, int32_t* status,
+                                             uint32_t max_spins = kGridBarrierSpins) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    uint32_t spins = 0;
+    while (ld_acquire_u32(count) < target) {
+      if (++spins >= max_spins) {
+        set_status(status, SIRIUS_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // ------------------------------------------------------------------ host phases
 DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_factor, bool allow_direct,
                      bool bloom = false);
@@ -710,6 +768,14 @@ RunView run_view(const RunLayout& R, char* base);
 sirius_status validate_dim(const sirius_pipeline_desc* q);
 sirius_status validate_fact(const sirius_pipeline_desc* q);
 int choose_mode(int agg_mode, int64_t gslots, int64_t n);
+// Plan of the routed probe (agg_mode 5) for a group table of gslots slots; R = 0: not possible.
+struct RoutePlan {
+  int blocks = 0;   // blocks of the cooperative launch
+  int logP = 0;     // owners = 2^logP
+  uint32_t R = 0;   // slots per owner
+  uint32_t C = 0;   // tuples per (owner, block) run and round
+};
+RoutePlan route_plan(int64_t gslots);
 sirius_status dim_build(const sirius_pipeline_desc* q, const DimLayout& L, char* base, cudaStream_t s);
 sirius_status run_init(const RunLayout& R, char* base, cudaStream_t s);
 sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,
