@@ -59,6 +59,7 @@ def parse(argv=None):
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-served", action="store_true")
     p.add_argument("--no-configs", action="store_true")
+    p.add_argument("--no-operators", action="store_true")
     p.add_argument("--batch-queries", type=int, default=512)
     p.add_argument("--serve-rate", type=float, default=2000.0)
     p.add_argument("--serve-seconds", type=float, default=10.0)
@@ -330,6 +331,14 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world)
 
+    # the unfused C-ABI operators on the same tables (filter, join build / probe, gathers,
+    # group-by), each against its own roofline, and their chain against the fused call
+    operators = None
+    if not args.no_operators:
+        del scratch
+        torch.cuda.empty_cache()
+        operators = run_operators(S, torch, spec, fact, dim, dev, stream, ms_step)
+        scratch = None
     # release the 600M-row tables before the batched and served workloads
     del fact, dim, desc, scratch
     torch.cuda.empty_cache()
@@ -363,13 +372,104 @@ def main():
                        "load_factor": args.load_factor or 0.5, "agg_mode": args.agg_mode},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "phase_ms": phase_ms, "device_status": status,
-            "batched": batched, "served": served, "configs": configs,
+            "batched": batched, "served": served, "configs": configs, "operators": operators,
             "hbm_gbs_effective_step": alg_bytes / (ms_step / 1e3) / 1e9,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_operators(S, torch, spec, fact, dim, dev, stream, fused_ms):
+    """The query's operators as separate C-ABI calls on the resident 600M-row tables, outputs
+    and scratch allocated once, no host synchronisation inside a timed call: filter (pred < t)
+    -> join build over the dim keys -> probe of the selected rows' keys -> gather of their
+    values and of the matched dim rows' group keys -> hash group-by.  Each is timed with CUDA
+    events (mean of 3 after a warm-up) against its algorithmic bytes and the measured copy
+    bandwidth; the chain's total is set beside the fused call's time per query."""
+    import ctypes
+    L = S.lib()
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    n, m = spec.n, spec.m
+    st = stream.cuda_stream
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def line(ms, rows, alg_bytes, what):
+        gbs = alg_bytes / (ms / 1e3) / 1e9
+        return {"ms": ms, "rows_per_s": rows / (ms / 1e3), "algorithmic_bytes": alg_bytes,
+                "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak, "bytes": what}
+
+    def ok(status):
+        if status != S.OK:
+            raise RuntimeError(S.last_error())
+
+    out = {}
+    # ---- A2 filter
+    ids = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    fscr = torch.empty(L.sirius_filter_scratch_bytes(n), dtype=torch.uint8, device=dev)
+    pred = fact["pred"]
+    f_ms = timed(lambda: ok(L.sirius_filter(pred.data_ptr(), n, S.OPS["lt"], spec.t, ids.data_ptr(),
+                                            cnt.data_ptr(), None, fscr.data_ptr(), fscr.numel(), st)))
+    n_sel = int(cnt.item())
+    out["filter"] = line(f_ms, n, 4 * n + 4 * n_sel, "4 B per row read + 4 B per selected row id written")
+    out["filter"]["selected"] = n_sel
+    del fscr
+    # ---- A1 join build (hash table over the dim keys, load factor 1/2)
+    tab = S.HashJoinTable(m, 4, 0.5, dev)
+    cap = tab.capacity
+    b_ms = timed(lambda: ok(L.sirius_hash_join_build(dim["pk"].data_ptr(), None, m, ctypes.byref(tab.struct),
+                                                     None, st)))
+    out["join_build"] = line(b_ms, m, 8 * cap + 4 * m + 8 * m,
+                             "table cleared (8 B per slot) + 4 B key read + one 8 B slot written per row")
+    out["join_build"]["capacity"] = cap
+    # ---- A3 probe: the selected rows' keys against the table
+    pp = torch.empty(n_sel, dtype=torch.int32, device=dev)
+    pb = torch.empty(n_sel, dtype=torch.int32, device=dev)
+    pc = torch.zeros(1, dtype=torch.int64, device=dev)
+    p_ms = timed(lambda: ok(L.sirius_hash_join_probe(ctypes.byref(tab.struct), fact["fk"].data_ptr(), None,
+                                                     ids.data_ptr(), n_sel, pp.data_ptr(), pb.data_ptr(),
+                                                     n_sel, pc.data_ptr(), None, st)))
+    pairs = int(pc.item())
+    out["join_probe"] = line(p_ms, n_sel, n_sel * (4 + 4 + 32) + pairs * 8,
+                             "4 B row id + 4 B key + one 32 B bucket sector per probe, 8 B per pair out")
+    out["join_probe"]["pairs"] = pairs
+    del tab
+    # ---- A4 gathers: values by probe row, group keys by build row
+    gv = torch.empty(pairs, dtype=torch.int64, device=dev)
+    gk = torch.empty(pairs, dtype=torch.int64, device=dev)
+    v_ms = timed(lambda: ok(L.sirius_gather_i64(fact["val"].data_ptr(), pp.data_ptr(), pairs, gv.data_ptr(), st)))
+    out["gather_val"] = line(v_ms, pairs, pairs * (4 + 8 + 8), "4 B index + 8 B value read + 8 B written")
+    k_ms = timed(lambda: ok(L.sirius_gather_group_key(dim["grp"].data_ptr(), None, pb.data_ptr(), pairs,
+                                                      gk.data_ptr(), st)))
+    out["gather_group_key"] = line(k_ms, pairs, pairs * (4 + 4 + 8), "4 B index + 4 B grp read + 8 B key written")
+    del pp, pb
+    # ---- A5/A6 hash group-by of the joined rows
+    hint = 100_000
+    gouts = S.groupby_outputs(L.sirius_groupby_capacity(hint) + 1, dev)
+    gscr = torch.empty(L.sirius_groupby_scratch_bytes(hint), dtype=torch.uint8, device=dev)
+    g_ms = timed(lambda: S.sirius_groupby_agg(gk, gv, group_cap_hint=hint, stream=stream, outputs=gouts,
+                                               scratch=gscr, sync=False))
+    out["groupby"] = line(g_ms, pairs, pairs * 16, "8 B key + 8 B value per row")
+    out["groupby"]["groups"] = int(gouts["groups"].item())
+    chain = f_ms + b_ms + p_ms + v_ms + k_ms + g_ms
+    out["unfused_chain_ms"] = chain
+    out["fused_ms_per_query"] = fused_ms
+    out["fused_speedup_vs_unfused"] = chain / fused_ms if fused_ms > 0 else None
+    del ids, gv, gk, gouts, gscr
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(S, torch, args, dev, rank):
@@ -690,13 +790,22 @@ def run_configs(S, torch, dev, rank):
     for dom in (100_000, 10_000_000):
         keys = torch.randint(0, dom, (n,), dtype=torch.int32, device=dev, generator=gen)
         res = {}
-        for name, fn in (("hash", lambda: S.sirius_groupby_agg(keys, vals, group_cap_hint=dom, stream=stream)),
+        # the hash group-by through the C ABI with its outputs and scratch allocated once and no
+        # host synchronisation inside the timed call (G stays on the device)
+        gouts = S.groupby_outputs(S.lib().sirius_groupby_capacity(dom) + 1, dev)
+        gscr = torch.empty(S.lib().sirius_groupby_scratch_bytes(dom), dtype=torch.uint8, device=dev)
+        for name, fn in (("hash", lambda: S.sirius_groupby_agg(keys, vals, group_cap_hint=dom, stream=stream,
+                                                               outputs=gouts, scratch=gscr, sync=False)),
                          ("sort", lambda: S.sirius_groupby_sort(keys, vals, out_cap=dom, stream=stream))):
-            g_ = int(fn()["key"].numel())
+            fn()
             torch.cuda.synchronize()
-            res[name] = {"ms": median_us(fn, 1, 3) / 1e3, "groups": g_}
+            g_ = int(gouts["groups"].item()) if name == "hash" else int(fn()["key"].numel())
+            res[name] = {"ms": median_us(fn, 2, 5) / 1e3, "groups": g_}
+        res["hash"]["rows_per_s"] = n / (res["hash"]["ms"] / 1e3)
+        res["hash"]["hbm_frac_12B_per_row"] = n * 12 / (res["hash"]["ms"] / 1e3) / 1e9 / float(
+            measured_peaks()[0].get("hbm_gbs", 6800.0))
         gb[f"keys_{dom}"] = res
-        del keys
+        del keys, gouts, gscr
     out["groupby_hash_vs_sort_100M"] = gb
     del vals
     torch.cuda.empty_cache()

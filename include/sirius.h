@@ -93,6 +93,15 @@ sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t op, int32_t
                             uint32_t* d_row_ids, int64_t* d_count, int64_t* h_count,
                             void* d_scratch, size_t scratch_bytes, sirius_stream stream);
 
+/* Failure injection for tests of callers' error handling (Sec. 3.2.3's buffer manager sizes
+ * and acquires the processing region; this exercises the path where that acquisition fails):
+ * the next `count` scratch allocations the library itself makes -- calls given d_scratch NULL
+ * -- fail with SIRIUS_ERR_OOM and a message, without calling the allocator and before any
+ * device work; calls given caller scratch are unaffected.  count 0 cancels pending failures.
+ * Process-wide and thread-safe; returns the number of failures still pending before the call.
+ * No device memory is touched, so the GPU and every later call stay usable. */
+int32_t sirius_inject_alloc_failures(int32_t count);
+
 /* sirius_filter_static: sirius_filter for callers that cannot allocate device memory at all.
  * The paper has no counterpart; it exists for code that must not call cudaMalloc or
  * cudaMallocAsync -- a host callback or another latency-critical path where an allocation
@@ -174,9 +183,13 @@ sirius_status sirius_gather_group_key(const int32_t* d_grp, const int8_t* d_flag
 /* ------------------------------------------------------------------ A5 / A6: group-by
  * Hash group-by aggregation (Sec. 3.2.2; Sec. 4.2: few groups contend on memory).  Keys are
  * int32 (key_width 4) or int64 (key_width 8); values int64.  For each distinct key: SUM,
- * COUNT(*), MIN, MAX (those selected by `aggs`; COUNT is always computed).  Small tables are
- * pre-aggregated per thread block in shared memory; large ones aggregate with global atomics
- * after a warp-level combine of equal keys.  The table holds sirius_groupby_capacity(hint)
+ * COUNT(*), MIN, MAX (those selected by `aggs`; COUNT is always computed).  A first pass
+ * records the key range; when it spans at most the table's limit of distinct keys (7/8 of its
+ * slots), a key's slot is its offset from the smallest key (no hashing; only those slots are
+ * cleared and scanned), else keys are hashed.  Small tables are pre-aggregated per thread block
+ * in shared memory; large ones aggregate with global atomics, behind a per-block cache of hot
+ * groups (direct slots) or after a warp-level combine of equal keys (hashed keys).  The table
+ * holds sirius_groupby_capacity(hint)
  * slots; more distinct keys than it can take -> TABLE_FULL (retry with a larger hint).
  * Outputs (device, out_cap each, NULL for aggregates not requested): keys, sums, counts, mins,
  * maxs, in unspecified order; the group count G goes to *d_groups / *h_groups

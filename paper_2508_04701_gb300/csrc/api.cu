@@ -33,6 +33,18 @@ int sm_count() {
   return n;
 }
 
+// Injected allocation failures (sirius_inject_alloc_failures): how many of the next
+// library-owned scratch allocations fail as if the device were out of memory.
+static std::atomic<int32_t> g_inject_oom{0};
+
+static bool take_injected_failure() {
+  int32_t k = g_inject_oom.load(std::memory_order_relaxed);
+  while (k > 0) {
+    if (g_inject_oom.compare_exchange_weak(k, k - 1, std::memory_order_relaxed)) return true;
+  }
+  return false;
+}
+
 sirius_status Scratch::acquire(void* d_scratch, size_t have, size_t need, cudaStream_t s) {
   stream = s;
   if (d_scratch) {
@@ -49,6 +61,10 @@ sirius_status Scratch::acquire(void* d_scratch, size_t have, size_t need, cudaSt
     return SIRIUS_OK;
   }
   if (need == 0) return SIRIUS_OK;
+  if (take_injected_failure()) {
+    set_error("scratch allocation of %zu bytes failed (injected failure)", need);
+    return SIRIUS_ERR_OOM;
+  }
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, need, s);
   if (e != cudaSuccess) {
@@ -155,3 +171,7 @@ sirius_status sirius_profile_stop(double* ms, int64_t* launches, int32_t nphases
 }
 
 }  // extern "C"
+
+extern "C" int32_t sirius_inject_alloc_failures(int32_t count) {
+  return sirius::g_inject_oom.exchange(count < 0 ? 0 : count, std::memory_order_relaxed);
+}

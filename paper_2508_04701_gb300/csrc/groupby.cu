@@ -3,12 +3,21 @@
 //
 // Group table (scratch): a 256-byte header, keys[cap + 1] (int64, kEmptyKey = empty; slot cap
 // holds the one key equal to kEmptyKey) and Agg[cap + 1] {sum, count, min, max}.
+//
+// A first pass over the keys records their range.  When the range spans at most the table's
+// limit of distinct keys (a dense key domain: dictionary codes, surrogate keys, small integer
+// attributes), a key's slot is its offset from the smallest key -- no hashing, no
+// compare-and-swap, no key array to clear or read -- and only the range's slots are cleared and
+// finalized.  Such a table can never hold more keys than the hash table would, so TABLE_FULL
+// is unchanged.  Otherwise keys are hashed into the table as before.
 // Small tables (cap <= kSmemMaxCap): every block first aggregates its rows into a private copy
 // of the table in shared memory (shared-memory atomics), then merges its occupied slots into
-// the global table -- the contention of few groups stays on chip.  Large tables: rows go
-// straight to the global table; lanes of a warp holding the same key are combined first
-// (match_any), so a hot key costs one global atomic per warp instead of one per row.
-#include "tables.cuh"
+// the global table -- the contention of few groups stays on chip.  Large tables: with direct
+// slots, four rows per thread (16-byte loads) go to the global table behind a per-block cache
+// of hot groups in shared memory (skewed keys aggregate on chip); hashed keys go straight to the
+// global table, lanes of a warp holding the same key combined first (match_any), so a hot key
+// costs one global atomic per warp instead of one per row.
+#include "pipeline.cuh"
 
 namespace sirius {
 namespace {
@@ -21,20 +30,72 @@ struct GroupHeader {
   int32_t pad0;
   unsigned long long distinct;
   unsigned long long groups;
-  unsigned long long pad[29];
+  // key range, order-preserving unsigned images (key ^ sign bit): the largest in kmax_enc, the
+  // complement of the smallest in kmin_inv, so that the cleared header (zeros) is the identity
+  // of both atomicMax reductions
+  unsigned long long kmax_enc;
+  unsigned long long kmin_inv;
+  unsigned long long pad[27];
 };
 static_assert(sizeof(GroupHeader) == 256, "group header is 256 bytes");
 
-__global__ void group_init_kernel(int64_t* keys, Agg* aggs, int64_t slots) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < slots;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    keys[i] = kEmptyKey;
-    agg_identity(&aggs[i]);
-  }
+constexpr unsigned long long kSign = 0x8000000000000000ull;
+
+// The key range as the range pass recorded it, and whether direct slots apply: n > 0 and
+// kmax - kmin < limit (so range = kmax - kmin + 1 <= limit slots).
+struct KeyRange {
+  int64_t kmin;
+  uint64_t range;  // kmax - kmin + 1 when direct, else 0
+  bool direct;
+};
+__device__ __forceinline__ KeyRange key_range(const GroupHeader* hdr, int64_t n, unsigned long long limit) {
+  KeyRange r;
+  const unsigned long long mx = hdr->kmax_enc, mn = ~hdr->kmin_inv;
+  r.kmin = (int64_t)(mn ^ kSign);
+  const uint64_t span = (mx ^ kSign) - (mn ^ kSign);  // two's-complement difference, exact
+  r.direct = n > 0 && mx >= mn && span < limit;
+  r.range = r.direct ? span + 1 : 0;
+  return r;
 }
 
 __device__ __forceinline__ int64_t load_key(const void* keys, int key_width, int64_t i) {
   return key_width == 4 ? (int64_t)((const int32_t*)keys)[i] : ((const int64_t*)keys)[i];
+}
+
+// Range pass: the smallest and largest key (warp reductions, one pair of atomics per warp).
+__global__ void __launch_bounds__(256)
+group_range_kernel(const void* __restrict__ keys, int key_width, int64_t n, GroupHeader* hdr) {
+  unsigned long long hi = 0, lo_inv = 0;  // identities of max(enc) and max(~enc)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long e = (unsigned long long)load_key(keys, key_width, i) ^ kSign;
+    hi = e > hi ? e : hi;
+    lo_inv = ~e > lo_inv ? ~e : lo_inv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, hi, o);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, lo_inv, o);
+    hi = a > hi ? a : hi;
+    lo_inv = b > lo_inv ? b : lo_inv;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&hdr->kmax_enc, hi);
+    atomicMax(&hdr->kmin_inv, lo_inv);
+  }
+}
+
+// Clears the slots the aggregation will use: the range's aggregates (direct slots), or every
+// key and aggregate of the hash table.
+__global__ void group_init_kernel(int64_t* keys, Agg* aggs, int64_t slots, const GroupHeader* hdr, int64_t n,
+                                  unsigned long long limit) {
+  const KeyRange kr = key_range(hdr, n, limit);
+  const int64_t use = kr.direct ? (int64_t)kr.range : slots;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < use;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!kr.direct) keys[i] = kEmptyKey;
+    agg_identity(&aggs[i]);
+  }
 }
 
 // Combine the lanes of a warp that hold the same key; returns true in the one lane per key
@@ -73,6 +134,7 @@ __global__ void __launch_bounds__(kThreads)
 group_global_kernel(const void* __restrict__ keys_in, int key_width, const int64_t* __restrict__ vals,
                     int64_t n, uint32_t aggs, int64_t* keys, Agg* tab, uint32_t cap,
                     GroupHeader* hdr, unsigned long long limit) {
+  if (key_range(hdr, n, limit).direct) return;  // group_direct_kernel aggregates these keys
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t i = base + threadIdx.x;
@@ -93,6 +155,59 @@ group_global_kernel(const void* __restrict__ keys_in, int key_width, const int64
   }
 }
 
+// Direct slots, large table: four rows per thread (16-byte loads when the columns are 16-byte
+// aligned), every row's aggregates behind the block's cache of hot groups.
+template <int kKeyWidth, bool kVec>
+__global__ void __launch_bounds__(512)
+group_direct_kernel(const void* __restrict__ keys_in, const int64_t* __restrict__ vals, int64_t n, uint32_t aggs,
+                    Agg* tab, const GroupHeader* hdr, unsigned long long limit) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  const KeyRange kr = key_range(hdr, n, limit);
+  if (!kr.direct) return;  // hashed keys: group_global_kernel
+  ProbeArgs a{};
+  a.tab = tab;
+  a.aggs = aggs;
+  const SmemAggs T = smem_aggs(smem_raw, kHotEntries);
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kHotEntries; i += blockDim.x) {
+    smem_identity(T, i);
+    T.tag[i] = kEmpty32;
+  }
+  __syncthreads();
+  const int64_t nq = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += stride) {
+    int64_t k[4], v[4];
+    if (kVec) {
+      if (kKeyWidth == 4) {
+        const int4 k4 = __ldcs(reinterpret_cast<const int4*>(keys_in) + q);
+        k[0] = k4.x, k[1] = k4.y, k[2] = k4.z, k[3] = k4.w;
+      } else {
+        const longlong2 a0 = __ldcs(reinterpret_cast<const longlong2*>(keys_in) + 2 * q);
+        const longlong2 a1 = __ldcs(reinterpret_cast<const longlong2*>(keys_in) + 2 * q + 1);
+        k[0] = a0.x, k[1] = a0.y, k[2] = a1.x, k[3] = a1.y;
+      }
+      const longlong2 v0 = __ldcs(reinterpret_cast<const longlong2*>(vals) + 2 * q);
+      const longlong2 v1 = __ldcs(reinterpret_cast<const longlong2*>(vals) + 2 * q + 1);
+      v[0] = v0.x, v[1] = v0.y, v[2] = v1.x, v[3] = v1.y;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        k[r] = load_key(keys_in, kKeyWidth, 4 * q + r);
+        v[r] = vals[4 * q + r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) aggregate<kAggHot>(a, T, (uint32_t)(uint64_t)(k[r] - kr.kmin), v[r]);
+  }
+  if (blockIdx.x == 0 && (int64_t)threadIdx.x < n - (nq << 2)) {
+    const int64_t i = (nq << 2) + threadIdx.x;
+    aggregate<kAggHot>(a, T, (uint32_t)(uint64_t)(load_key(keys_in, kKeyWidth, i) - kr.kmin), vals[i]);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < (uint32_t)kHotEntries; i += blockDim.x)
+    if (T.tag[i] != kEmpty32) smem_merge(T, i, &tab[T.tag[i]], aggs);
+}
+
 __global__ void __launch_bounds__(kThreads)
 group_smem_kernel(const void* __restrict__ keys_in, int key_width, const int64_t* __restrict__ vals,
                   int64_t n, uint32_t aggs, int64_t* keys, Agg* tab, uint32_t cap,
@@ -107,12 +222,15 @@ group_smem_kernel(const void* __restrict__ keys_in, int key_width, const int64_t
   }
   if (threadIdx.x == 0) s_distinct = 0;
   __syncthreads();
+  const KeyRange kr = key_range(hdr, n, limit);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int64_t key = load_key(keys_in, key_width, i);
     const long long v = vals[i];
     int64_t slot;
-    if (key == kEmptyKey) {
+    if (kr.direct) {
+      slot = (int64_t)(uint64_t)(key - kr.kmin);  // < range <= limit < cap
+    } else if (key == kEmptyKey) {
       slot = cap;
     } else {
       slot = -1;
@@ -151,8 +269,8 @@ group_smem_kernel(const void* __restrict__ keys_in, int key_width, const int64_t
   for (uint32_t i = threadIdx.x; i <= cap; i += blockDim.x) {
     const Agg a = s_tab[i];
     if (a.count == 0) continue;
-    const int64_t g = (i == cap) ? (int64_t)cap
-                                 : group_find_or_insert(keys, cap, s_keys[i], &hdr->distinct, limit);
+    const int64_t g = (kr.direct || i == cap) ? (int64_t)i
+                                               : group_find_or_insert(keys, cap, s_keys[i], &hdr->distinct, limit);
     if (g < 0) set_status(&hdr->status, SIRIUS_ERR_TABLE_FULL);
     else agg_merge_global(&tab[g], a.sum, a.count, a.min, a.max, aggs);
   }
@@ -162,7 +280,9 @@ __global__ void group_finalize_kernel(const int64_t* __restrict__ keys, const Ag
                                       int64_t slots, uint32_t cap, uint32_t aggs, int64_t* out_keys,
                                       int64_t* out_sum, int64_t* out_count, int64_t* out_min,
                                       int64_t* out_max, int64_t out_cap, GroupHeader* hdr,
-                                      int64_t* d_groups) {
+                                      int64_t n, unsigned long long limit) {
+  const KeyRange kr = key_range(hdr, n, limit);
+  if (kr.direct) slots = (int64_t)kr.range;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t rounds = (slots + stride - 1) / stride;
   for (int64_t r = 0; r < rounds; ++r) {
@@ -171,7 +291,7 @@ __global__ void group_finalize_kernel(const int64_t* __restrict__ keys, const Ag
     const uint64_t pos = warp_append(&hdr->groups, occ);
     if (occ && (int64_t)pos < out_cap) {
       const Agg a = tab[i];
-      if (out_keys) out_keys[pos] = (i == cap) ? kEmptyKey : keys[i];
+      if (out_keys) out_keys[pos] = kr.direct ? kr.kmin + i : ((i == cap) ? kEmptyKey : keys[i]);
       if (out_sum) out_sum[pos] = (int64_t)a.sum;
       if (out_count) out_count[pos] = (int64_t)a.count;
       if (out_min) out_min[pos] = a.min;
@@ -219,10 +339,15 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
   GroupHeader* hdr = (GroupHeader*)sc.take(256);
   int64_t* keys = (int64_t*)sc.take((size_t)(cap + 1) * 8);
   Agg* tab = (Agg*)sc.take((size_t)(cap + 1) * sizeof(Agg));
-  SIRIUS_CUDA_TRY(cudaMemsetAsync(hdr, 0, 256, s));
-  group_init_kernel<<<grid_for(cap + 1, kThreads), kThreads, 0, s>>>(keys, tab, cap + 1);
-  SIRIUS_LAUNCH_CHECK();
   const unsigned long long limit = group_limit_for(cap);
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(hdr, 0, 256, s));
+  if (n > 0) {
+    group_range_kernel<<<grid_for(n, 256) < sm_count() * 8 ? grid_for(n, 256) : sm_count() * 8, 256, 0, s>>>(
+        d_keys, key_width, n, hdr);
+    SIRIUS_LAUNCH_CHECK();
+  }
+  group_init_kernel<<<grid_for(cap + 1, kThreads), kThreads, 0, s>>>(keys, tab, cap + 1, hdr, n, limit);
+  SIRIUS_LAUNCH_CHECK();
   PhaseTimer pt(s, SIRIUS_PHASE_GROUPBY);
   if (n > 0) {
     if (cap <= kSmemMaxCap) {
@@ -239,6 +364,17 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
       group_smem_kernel<<<g, kThreads, smem, s>>>(d_keys, key_width, d_vals, n, aggs, keys, tab,
                                                   (uint32_t)cap, hdr, limit);
     } else {
+      // direct slots (decided on the device from the key range) or the hash table: each kernel
+      // returns at once when the other applies
+      const bool vec = ((uintptr_t)d_keys & 15) == 0 && ((uintptr_t)d_vals & 15) == 0;
+      auto kd = key_width == 4 ? (vec ? group_direct_kernel<4, true> : group_direct_kernel<4, false>)
+                               : (vec ? group_direct_kernel<8, true> : group_direct_kernel<8, false>);
+      SIRIUS_CUDA_TRY(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHotSmemBytes));
+      int64_t gd = ((n >> 2) + 511) / 512;
+      const int64_t most = (int64_t)sm_count() * 3;  // three 64 KB caches per SM
+      gd = gd < 1 ? 1 : (gd > most ? most : gd);
+      kd<<<(unsigned)gd, 512, kHotSmemBytes, s>>>(d_keys, d_vals, n, aggs, tab, hdr, limit);
+      SIRIUS_LAUNCH_CHECK();
       group_global_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(d_keys, key_width, d_vals, n, aggs,
                                                                      keys, tab, (uint32_t)cap, hdr, limit);
     }
@@ -246,7 +382,7 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
   }
   group_finalize_kernel<<<grid_for(cap + 1, kThreads), kThreads, 0, s>>>(
       keys, tab, cap + 1, (uint32_t)cap, aggs, d_out_keys, d_sum, d_count, d_min, d_max, out_cap, hdr,
-      d_groups);
+      n, limit);
   SIRIUS_LAUNCH_CHECK();
   if (d_groups) {
     copy_groups_kernel<<<1, 1, 0, s>>>(hdr, d_groups);

@@ -93,6 +93,7 @@ SIGNATURES = {
     "sirius_filter_scratch_bytes": (_SZ, [_I64]),
     "sirius_filter": (_I32, [_VP, _I64, _I32, _I32, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "sirius_filter_static_max_rows": (_I64, []),
+    "sirius_inject_alloc_failures": (_I32, [_I32]),
     "sirius_filter_static": (_I32, [_VP, _I64, _I32, _I32, _VP, _VP, _VP, _VP]),
     "sirius_join_table_capacity": (_I64, [_I64, _F64]),
     "sirius_join_table_bytes": (_SZ, [_I64, _I32]),
@@ -337,28 +338,47 @@ def _agg_mask(aggs) -> int:
     return m
 
 
+def groupby_outputs(out_cap: int, device="cuda") -> Dict[str, torch.Tensor]:
+    """Output arrays for sirius_groupby_agg / sirius_groupby_sort (out_cap groups each) and the
+    device group count ("groups", one int64)."""
+    outs = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, device=device)
+            for c in ("key", "sum", "count", "min", "max")}
+    outs["groups"] = torch.zeros(1, dtype=torch.int64, device=device)
+    return outs
+
+
 def sirius_groupby_agg(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,min,max",
                        group_cap_hint: int = 1024, out_cap: Optional[int] = None,
-                       stream=None) -> Dict[str, torch.Tensor]:
+                       stream=None, outputs: Optional[Dict[str, torch.Tensor]] = None,
+                       scratch: Optional[torch.Tensor] = None, sync: bool = True):
+    """Hash group-by.  sync=True: returns the trimmed group arrays (reads G back); sync=False:
+    returns nothing and leaves G in outputs["groups"] (no host synchronisation).  outputs /
+    scratch: preallocated (groupby_outputs, sirius_groupby_scratch_bytes) to avoid allocating
+    per call."""
     n = keys.numel()
     kw = {torch.int32: 4, torch.int64: 8}[keys.dtype]
     mask = _agg_mask(aggs)
-    if out_cap is None:
-        out_cap = lib().sirius_groupby_capacity(group_cap_hint) + 1
     dev = keys.device
-    outs = {c: torch.empty(max(out_cap, 1), dtype=torch.int64, device=dev)
-            for c in ("key", "sum", "count", "min", "max")}
-    scratch = _scratch(lib().sirius_groupby_scratch_bytes(group_cap_hint), dev)
+    if outputs is None:
+        if out_cap is None:
+            out_cap = lib().sirius_groupby_capacity(group_cap_hint) + 1
+        outputs = groupby_outputs(out_cap, dev)
+    outs = outputs
+    out_cap = outs["key"].numel()
+    if scratch is None:
+        scratch = _scratch(lib().sirius_groupby_scratch_bytes(group_cap_hint), dev)
     h = ctypes.c_int64(0)
     st = lib().sirius_groupby_agg(
         _ptr(keys), kw, _ptr(vals), n, mask, group_cap_hint, _ptr(outs["key"]),
         _ptr(outs["sum"]) if mask & AGG_SUM else None, _ptr(outs["count"]),
         _ptr(outs["min"]) if mask & AGG_MIN else None,
-        _ptr(outs["max"]) if mask & AGG_MAX else None, out_cap, None, ctypes.byref(h),
-        _ptr(scratch), scratch.numel(), _stream(stream))
+        _ptr(outs["max"]) if mask & AGG_MAX else None, out_cap, _ptr(outs.get("groups")),
+        ctypes.byref(h) if sync else None, _ptr(scratch), scratch.numel(), _stream(stream))
     _check(st, h.value)
+    if not sync:
+        return None
     g = h.value
-    return {c: t[:g] for c, t in outs.items()}
+    return {c: outs[c][:g] for c in ("key", "sum", "count", "min", "max")}
 
 
 def sirius_groupby_sort(keys: torch.Tensor, vals: torch.Tensor, aggs="sum,count,min,max",

@@ -149,3 +149,15 @@ def test_wait_selftests_reject_bad_arguments_on_the_host(lib):
     assert "blocks" in S.last_error()
     assert lib.sirius_selftest_lookback_timeout(None, 0, ctypes.byref(st), None) == S.ERR_INVALID
     assert "256 bytes" in S.last_error()
+
+
+def test_injected_allocation_failure_host_side(lib):
+    """The failure-injection hook fails the next library-owned scratch allocation with OOM before
+    any device work (here: a group-by over no rows with no caller scratch), and counts down."""
+    from paper_2508_04701_gb300 import sirius as S
+    assert lib.sirius_inject_alloc_failures(2) == 0
+    st = lib.sirius_groupby_agg(None, 4, None, 0, 15, 10, None, None, None, None, None, 0, None, None,
+                                None, 0, None)
+    assert st == S.ERR_OOM and "injected" in S.last_error()
+    assert lib.sirius_inject_alloc_failures(0) == 1      # one was used, one still pending; cancelled
+    assert lib.sirius_inject_alloc_failures(0) == 0

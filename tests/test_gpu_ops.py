@@ -11,6 +11,7 @@ import oracle as O
 from paper_2508_04701_gb300 import datagen as dg
 
 pytestmark = pytest.mark.gpu
+COLS = ("key", "sum", "count", "min", "max")
 
 
 @pytest.fixture(scope="module")
@@ -185,6 +186,46 @@ def test_groupby_subsets_and_single_group(S):
     vals = rng.integers(0, 10**8, size=123_457)
     check_groupby(S, np.zeros(vals.size, np.int32), vals, 1, "sum,count")
     check_groupby(S, rng.integers(0, 50, size=vals.size).astype(np.int32), vals, 64, "min")
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+@pytest.mark.parametrize("n,dom", [(5, 3), (3_000_003, 1_000_000), (2_000_001, 4000)])
+def test_groupby_direct_slots_large_tables(S, n, dom, offset):
+    """Dense keys of a table too large for shared memory: direct slots (key - min) behind the
+    hot-group cache, 16-byte loads (offset 0) or scalar loads (columns one element off)."""
+    rng = np.random.default_rng(n + dom + offset)
+    keys = (rng.integers(0, dom, size=n + offset) - dom // 3).astype(np.int32)
+    vals = rng.integers(-10**12, 10**12, size=n + offset)
+    dk, dvals = dev(keys)[offset:], dev(vals)[offset:]
+    got = S.sirius_groupby_agg(dk, dvals, group_cap_hint=max(dom, 3000))
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in got.items()})
+    want = O.groupby_agg(keys[offset:], vals[offset:])
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
+
+
+def test_groupby_direct_slots_int64_edges(S):
+    """Dense int64 keys far from zero, at INT64_MIN and at INT64_MAX; a range of exactly the
+    table's limit (direct) and one past it with two keys (hashed)."""
+    rng = np.random.default_rng(14)
+    vals = rng.integers(-10**8, 10**8, size=400_003)
+    for base in (1 << 40, np.iinfo(np.int64).min, np.iinfo(np.int64).max - 4999):
+        keys = (np.int64(base) + rng.integers(0, 5000, size=vals.size)).astype(np.int64)
+        check_groupby(S, keys, vals, 5000)
+    cap = S.lib().sirius_groupby_capacity(3000)
+    limit = cap - cap // 8
+    keys = np.arange(limit, dtype=np.int64).repeat(3)
+    check_groupby(S, keys, np.arange(keys.size, dtype=np.int64), 3000)
+    keys = np.array([0, limit] * 5000, dtype=np.int64)
+    check_groupby(S, keys, np.arange(keys.size, dtype=np.int64), 3000)
+
+
+def test_groupby_direct_slots_skewed(S):
+    """Zipf(1.1) ranks over 1e6 dense keys: hot groups aggregate in the per-block cache."""
+    rng = np.random.default_rng(15)
+    keys = np.minimum(rng.zipf(1.1, size=2_000_003), 1_000_000).astype(np.int32) - 1
+    vals = rng.integers(0, 10**8, size=keys.size)
+    check_groupby(S, keys, vals, 1_000_000)
 
 
 def test_groupby_table_full_then_retry(S):
