@@ -445,6 +445,22 @@ def run_operators(S, torch, spec, fact, dim, dev, stream, fused_ms):
     out["join_probe"] = line(p_ms, n_sel, n_sel * (4 + 4 + 32) + pairs * 8,
                              "4 B row id + 4 B key + one 32 B bucket sector per probe, 8 B per pair out")
     out["join_probe"]["pairs"] = pairs
+    # A/B: four rows per thread (variant 1) against four lanes per key (variant 2, warp-
+    # cooperative), at load factors 1/2 and 0.9 (the same probes; pairs must agree)
+    ab = {}
+    for lf in (0.5, 0.9):
+        for var in (1, 2):
+            t2 = S.HashJoinTable(m, 4, lf, dev, probe_variant=var)
+            ok(L.sirius_hash_join_build(dim["pk"].data_ptr(), None, m, ctypes.byref(t2.struct), None, st))
+            ms2 = timed(lambda: ok(L.sirius_hash_join_probe(ctypes.byref(t2.struct), fact["fk"].data_ptr(), None,
+                                                            ids.data_ptr(), n_sel, pp.data_ptr(), pb.data_ptr(),
+                                                            n_sel, pc.data_ptr(), None, st)))
+            ab[f"lf{lf}_variant{var}"] = {"ms": ms2, "pairs_agree": int(pc.item()) == pairs,
+                                          "table_mb": t2.mem.numel() / 1e6}
+            del t2
+    out["join_probe"]["variants"] = ab
+    ok(L.sirius_hash_join_probe(ctypes.byref(tab.struct), fact["fk"].data_ptr(), None, ids.data_ptr(), n_sel,
+                                pp.data_ptr(), pb.data_ptr(), n_sel, pc.data_ptr(), None, st))
     del tab
     # ---- A4 gathers: values by probe row, group keys by build row
     gv = torch.empty(pairs, dtype=torch.int64, device=dev)
@@ -724,6 +740,42 @@ def run_configs(S, torch, dev, rank):
                                    "rows_per_s": spec.n / (ms / 1e3), "phase_ms": ph,
                                    "join": "hash table (two-column keys), 20 B/row of fact columns"}
     del fact, dim, desc, scr, o
+    torch.cuda.empty_cache()
+
+    # ---- the 600M-row query forced through the hash-table join, its load factor swept (the
+    # autotuner's knob: a fuller table is smaller, 0.95 -> 126 MB against the 129 MB L2)
+    spec = dg.plain_scale(seed=rank)
+    dim = dg.gen_dim_device(spec, dev)
+    fact = dg.gen_fact_device(spec, dim, dev)
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    sweep = {}
+    for lf in (0.5, 0.7, 0.9, 0.95):
+        desc = S.make_desc(fact, dim, "lt", spec.t, spec.aggs, 100_000, load_factor=lf, join_mode="hash")
+        o = S.PipelineOutputs(100_001, dev)
+        scr = torch.empty(S.pipeline_scratch_bytes(desc), dtype=torch.uint8, device=dev)
+        g = S.sirius_run_pipeline(desc, o, scr, stream, sync=True)
+        S.profile_start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            S.sirius_run_pipeline(desc, o, scr, stream, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ph = {k: v[0] / max(v[1], 1) for k, v in S.profile_stop().items()}
+        ms = e0.elapsed_time(e1) / 3
+        pr = ph.get("pipe_probe", 0.0)
+        sweep[f"lf_{lf}"] = {"groups": g, "ms_per_query": ms, "rows_per_s": spec.n / (ms / 1e3), "phase_ms": ph,
+                             "probe_roofline_frac": (spec.n * 16 / (pr / 1e3) / 1e9 / peak) if pr > 0 else None,
+                             "table_mb": S.lib().sirius_join_table_bytes(
+                                 S.lib().sirius_join_table_capacity(spec.m, lf), 4) / 1e6}
+        del desc, o, scr
+    best = min(sweep, key=lambda k: sweep[k]["ms_per_query"])
+    out["plain_600M_hash_join"] = {"rows": spec.n, "join": "hash table forced (join_mode 1), one-column keys",
+                                   "load_factor_sweep": sweep, "best": best,
+                                   "roofline": {"bound": "hbm", "kernel": "probe_kernel (hash-table join)",
+                                                "frac": sweep[best]["probe_roofline_frac"], "peak": peak,
+                                                "unit": "GB/s", "bytes_per_row": 16}}
+    del fact, dim
     torch.cuda.empty_cache()
 
     # ---- the 600M-row query with a dim-side predicate (dattr < 10: a tenth of the dim rows take

@@ -141,7 +141,11 @@ typedef struct {
   void* d_mem;         /* caller-owned device memory */
   int64_t capacity;    /* slots; must exceed the number of build rows */
   int32_t key_width;   /* 4 or 8 */
-  int32_t reserved;
+  int32_t probe_variant; /* how sirius_hash_join_probe walks the table when it holds no duplicate
+                            keys: 0 or 1, four probe rows per thread, each reading its key's
+                            32-byte home bucket (all four requested together); 2, warp-cooperative,
+                            four lanes per probe key reading four consecutive buckets per step.
+                            A table with duplicate keys is walked one row per lane. */
 } sirius_join_table;
 
 int64_t sirius_join_table_capacity(int64_t m, double load_factor); /* load_factor in (0, 0.95] */

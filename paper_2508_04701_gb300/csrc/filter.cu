@@ -1,12 +1,15 @@
 // A2: predicate filter with stable stream compaction (Sec. 3.2.2 predicate pushdown; Sec. 4.2).
 //
-// One pass over the column.  A thread block owns a tile of 4096 rows (8 warps x 512 rows; a
-// lane reads four 16-byte vectors, rows 4*(lane + 32k) .. +3 of its warp's slice).  Each warp
-// ranks its selected rows with 16 ballots and popcounts; the block scans its 8 warp totals;
-// the tile's output offset comes from a decoupled look-back over the tiles before it
-// (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA
-// technical report NVR-2016-002).  Tiles take tickets from an atomic counter, so every tile a
-// look-back waits on has already started; each wait is still bounded and reports TIMEOUT.
+// One pass over the column.  A thread block owns a tile of 8192 rows (8 warps x 1024 rows; a
+// lane reads eight 16-byte vectors, rows 4*(lane + 32k) .. +3 of its warp's slice, all eight in
+// flight together).  Each warp ranks its selected rows with ballots and popcounts; the block
+// scans its 8 warp totals and publishes the tile's count at once; the selected row ids are
+// placed in shared memory in row order while warp 0 finds the tile's output offset with a
+// decoupled look-back over the tiles before it (Merrill & Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", NVIDIA technical report NVR-2016-002); then the block copies
+// its ids out as one contiguous, coalesced run.  Tiles take tickets from an atomic counter, so
+// every tile a look-back waits on has already started; each wait is still bounded and reports
+// TIMEOUT.
 #include <mutex>
 
 #include "common.cuh"
@@ -15,9 +18,9 @@ namespace sirius {
 namespace {
 
 constexpr int kFilterThreads = 256;
-constexpr int kFilterK = 4;                                  // 16-byte vectors per lane
-constexpr int kWarpRows = 32 * 4 * kFilterK;                 // 512
-constexpr int kTileRows = kWarpRows * (kFilterThreads / 32);  // 4096
+constexpr int kFilterK = 8;                                  // 16-byte vectors per lane
+constexpr int kWarpRows = 32 * 4 * kFilterK;                 // 1024
+constexpr int kTileRows = kWarpRows * (kFilterThreads / 32);  // 8192
 constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
 constexpr int kSpinLimit = 1 << 21;
 
@@ -27,15 +30,17 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
   return v;
 }
 
-// Exclusive prefix of this tile: the sum of all earlier tiles' selected counts.  Run by one
-// whole warp; returns the same value in every lane.
-__device__ uint64_t look_back(uint64_t* status, int64_t tile, uint64_t total, int32_t* err) {
+// Publishes this tile's selected count: as its inclusive prefix for tile 0, else as an
+// aggregate that successors can add up before this tile's own prefix is known.
+__device__ __forceinline__ void publish_count(uint64_t* status, int64_t tile, uint64_t total) {
+  st_relaxed_u64(&status[tile], (total << 2) | (tile == 0 ? kFlagPrefix : kFlagAgg));
+}
+
+// Exclusive prefix of this tile (its count already published): the sum of all earlier tiles'
+// selected counts.  Run by one whole warp; returns the same value in every lane.
+__device__ uint64_t look_back_published(uint64_t* status, int64_t tile, uint64_t total, int32_t* err) {
   const int lane = threadIdx.x & 31;
-  if (tile == 0) {
-    if (lane == 0) st_relaxed_u64(&status[0], (total << 2) | kFlagPrefix);
-    return 0;
-  }
-  if (lane == 0) st_relaxed_u64(&status[tile], (total << 2) | kFlagAgg);
+  if (tile == 0) return 0;
   uint64_t excl = 0;
   int64_t j0 = tile - 1;
   bool timed_out = false;
@@ -65,6 +70,11 @@ __device__ uint64_t look_back(uint64_t* status, int64_t tile, uint64_t total, in
   return excl;
 }
 
+__device__ uint64_t look_back(uint64_t* status, int64_t tile, uint64_t total, int32_t* err) {
+  if ((threadIdx.x & 31) == 0) publish_count(status, tile, total);
+  return look_back_published(status, tile, total, err);
+}
+
 // Self-test of the look-back's bounded wait: one warp plays tile 1, whose predecessor (tile 0)
 // never publishes, so the wait runs out and records SIRIUS_ERR_TIMEOUT in *err.
 __global__ void lookback_selftest_kernel(uint64_t* status, int32_t* err) { look_back(status, 1, 7, err); }
@@ -76,8 +86,10 @@ filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_
                       DevHeader* hdr, uint64_t* status, int64_t num_tiles) {
   __shared__ int64_t s_tile;
   __shared__ uint32_t s_warp_total[kFilterThreads / 32];
-  __shared__ uint64_t s_warp_excl[kFilterThreads / 32];
+  __shared__ uint32_t s_warp_excl[kFilterThreads / 32];
+  __shared__ uint32_t s_total;
   __shared__ uint64_t s_tile_excl;
+  __shared__ uint32_t s_ids[kTileRows];   // the tile's selected row ids, in row order
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -130,18 +142,39 @@ filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_
   if (lane == 0) s_warp_total[warp] = running;
   __syncthreads();
 
-  // ---- block scan of warp totals, then the look-back for the tile's offset
+  // ---- block scan of warp totals; the tile's count is published at once
   if (warp == 0) {
-    uint64_t v = lane < kFilterThreads / 32 ? s_warp_total[lane] : 0;
-    uint64_t incl = v;
+    const uint32_t v = lane < kFilterThreads / 32 ? s_warp_total[lane] : 0;
+    uint32_t incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += u;
     }
     if (lane < kFilterThreads / 32) s_warp_excl[lane] = incl - v;
-    const uint64_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const uint64_t excl = look_back(status, tile, total, &hdr->status);
+    if (lane == 31) {
+      s_total = incl;
+      publish_count(status, tile, incl);
+    }
+  }
+  __syncthreads();
+
+  // ---- the selected row ids into shared memory in row order (tile-local positions)
+  const uint32_t wbase = s_warp_excl[warp];
+#pragma unroll
+  for (int k = 0; k < kFilterK; ++k) {
+    uint32_t b = bits[k];
+    uint32_t pos = wbase + before[k];
+    const uint32_t row0 = (uint32_t)(warp_row0 + 4 * (lane + 32 * k));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((b >> j) & 1u) s_ids[pos++] = row0 + j;
+    }
+  }
+  // ---- the tile's output offset (warp 0)
+  const uint32_t total = s_total;
+  if (warp == 0) {
+    const uint64_t excl = look_back_published(status, tile, total, &hdr->status);
     if (lane == 0) {
       s_tile_excl = excl;
       if (tile == num_tiles - 1) {
@@ -152,18 +185,9 @@ filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_
   }
   __syncthreads();
 
-  // ---- scatter the selected row ids in row order
-  const uint64_t base = s_tile_excl + s_warp_excl[warp];
-#pragma unroll
-  for (int k = 0; k < kFilterK; ++k) {
-    uint32_t b = bits[k];
-    uint32_t pos = before[k];
-    const uint32_t row0 = (uint32_t)(warp_row0 + 4 * (lane + 32 * k));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if ((b >> j) & 1u) out[base + pos++] = row0 + j;
-    }
-  }
+  // ---- one contiguous run of ids out
+  uint32_t* dst = out + s_tile_excl;
+  for (uint32_t i = threadIdx.x; i < total; i += kFilterThreads) dst[i] = s_ids[i];
 }
 
 }  // namespace

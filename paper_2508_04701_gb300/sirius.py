@@ -69,7 +69,7 @@ class Result(ctypes.Structure):
 
 class JoinTable(ctypes.Structure):
     _fields_ = [("d_mem", ctypes.c_void_p), ("capacity", ctypes.c_int64),
-                ("key_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("key_width", ctypes.c_int32), ("probe_variant", ctypes.c_int32)]
 
 
 class DimIndex(ctypes.Structure):
@@ -241,11 +241,12 @@ def sirius_filter(col: torch.Tensor, op="lt", literal: int = 0, out: Optional[to
 class HashJoinTable:
     """A join table in a torch-owned device buffer."""
 
-    def __init__(self, m: int, key_width: int = 4, load_factor: float = 0.5, device="cuda"):
+    def __init__(self, m: int, key_width: int = 4, load_factor: float = 0.5, device="cuda",
+                 probe_variant: int = 0):
         cap = lib().sirius_join_table_capacity(m, load_factor)
         nbytes = lib().sirius_join_table_bytes(cap, key_width)
         self.mem = torch.empty(nbytes, dtype=torch.uint8, device=device)
-        self.struct = JoinTable(self.mem.data_ptr(), cap, key_width, 0)
+        self.struct = JoinTable(self.mem.data_ptr(), cap, key_width, int(probe_variant))
         self.has_dups = None
 
     @property

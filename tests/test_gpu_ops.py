@@ -67,8 +67,9 @@ def test_filter_async_count(S):
 
 
 # ------------------------------------------------------------------------- join
-def check_join(S, probe, build, sel=None, probe_hi=None, build_hi=None, lf=0.5):
-    tab = S.sirius_hash_join_build(dev(build), dev(build_hi) if build_hi is not None else None, lf)
+def check_join(S, probe, build, sel=None, probe_hi=None, build_hi=None, lf=0.5, variant=0):
+    tab = S.HashJoinTable(build.size, 8 if build_hi is not None else 4, lf, probe_variant=variant)
+    tab = S.sirius_hash_join_build(dev(build), dev(build_hi) if build_hi is not None else None, lf, table=tab)
     p, b = S.sirius_hash_join_probe(tab, dev(probe), dev(probe_hi) if probe_hi is not None else None,
                                     dev(sel.view(np.int32)) if sel is not None else None)
     got = O.sort_pairs(u32(p), u32(b))
@@ -129,6 +130,30 @@ def test_join_composite_keys(S):
     check_join(S, p_lo, b_lo, probe_hi=p_hi, build_hi=b_hi)
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("lf", [0.5, 0.95])
+def test_join_probe_variants(S, variant, lf):
+    """Four rows per thread (1) and four lanes per key (2): unique keys at two load factors (long
+    walks at 0.95), a selection vector starting off a 16-byte boundary, ragged counts, two-column
+    keys, and a table with duplicates (walked one row per lane by either)."""
+    rng = np.random.default_rng(20 + variant)
+    m = 50_001
+    build = rng.permutation(3 * m)[:m].astype(np.int32) - m
+    probe = rng.integers(-m - 100, 2 * m + 100, size=400_003).astype(np.int32)
+    assert check_join(S, probe, build, lf=lf, variant=variant) > 0
+    sel = O.filter_rows(rng.integers(0, 100, size=probe.size).astype(np.int32), "lt", 37)
+    check_join(S, probe, build, sel=sel[1:], lf=lf, variant=variant)
+    for n in (1, 3, 5, 33):
+        check_join(S, probe[:n], build, lf=lf, variant=variant)
+    pool = rng.integers(-2**31, 2**31, size=(20_000, 2)).astype(np.int64)
+    bi = rng.permutation(20_000)[:15_000]
+    pi = rng.integers(0, 20_000, size=100_001)
+    check_join(S, pool[pi, 1].astype(np.int32), pool[bi, 1].astype(np.int32), probe_hi=pool[pi, 0].astype(np.int32),
+               build_hi=pool[bi, 0].astype(np.int32), lf=lf, variant=variant)
+    dups = np.concatenate([build[:5000], build[:3000]])
+    check_join(S, probe, dups, lf=lf, variant=variant)
+
+
 def test_join_capacity_retry(S):
     build = np.concatenate([np.arange(100, dtype=np.int32)] * 4)
     probe = np.arange(100, dtype=np.int32)
@@ -145,6 +170,10 @@ def test_gather(S):
     idx = rng.integers(0, 100_000, size=333_333).astype(np.uint32)
     assert np.array_equal(S.sirius_gather(dev(src64), dev(idx.view(np.int32))).cpu().numpy(), src64[idx])
     assert np.array_equal(S.sirius_gather(dev(src32), dev(idx.view(np.int32))).cpu().numpy(), src32[idx])
+    for n, off in ((1, 0), (3, 1), (7, 1), (1001, 2)):   # ragged counts, indexes off 16-byte boundaries
+        di = dev(idx.view(np.int32))[off:off + n]
+        assert np.array_equal(S.sirius_gather(dev(src64), di).cpu().numpy(), src64[idx[off:off + n]])
+        assert np.array_equal(S.sirius_gather(dev(src32), di).cpu().numpy(), src32[idx[off:off + n]])
     grp = rng.integers(-1000, 1000, size=100_000).astype(np.int32)
     flag = rng.integers(-128, 128, size=100_000).astype(np.int8)
     got = S.sirius_gather_group_key(dev(grp), dev(flag), dev(idx.view(np.int32))).cpu().numpy()
