@@ -6,9 +6,13 @@
     python -m paper_2508_04701_gb300.profile_case --workload plain_1M --variant single
     python -m paper_2508_04701_gb300.profile_case --op sort --n ROWS --m DISTINCT_KEYS
     python -m paper_2508_04701_gb300.profile_case --op strings --n ROWS --m DISTINCT_STRINGS
+    python -m paper_2508_04701_gb300.profile_case --op operators [--n ROWS] [--m DIM_ROWS]
 
 --op sort runs the sort-based group-by on int32 keys U[0, m) with int64 values; --op strings
-dictionary-encodes a seeded string column of n rows over m distinct strings.
+dictionary-encodes a seeded string column of n rows over m distinct strings; --op operators
+runs the query's unfused C-ABI operators on the 600M-row query's distributions at n rows:
+filter (pred < 30), join build over the dim keys, probe of the selected rows, gathers of their
+values and group keys, hash group-by.
 
 Builds the 600M-row query's distributions at a reduced fact size (default 100M rows, 1.6 GB of
 columns, above the L2 size) against the full 15M-row dim table, and runs the pipeline R times.
@@ -33,7 +37,7 @@ def main():
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
     p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot", "routed"])
     p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
-    p.add_argument("--op", default="pipeline", choices=["pipeline", "sort", "strings"])
+    p.add_argument("--op", default="pipeline", choices=["pipeline", "sort", "strings", "operators"])
     a = p.parse_args()
     import torch
 
@@ -55,6 +59,21 @@ def main():
             codes, rows = S.sirius_dict_encode(col["offsets"], col["chars"], distinct_hint=a.m)
         torch.cuda.synchronize()
         print(f"profile case ok: dictionary of {a.n} strings ({col['chars'].numel()} bytes), {rows.numel()} distinct")
+        return
+    if a.op == "operators":
+        spec = dg.plain_scale(n=a.n, m=a.m)
+        dim = dg.gen_dim_device(spec)
+        fact = dg.gen_fact_device(spec, dim)
+        for _ in range(a.runs):
+            ids = S.sirius_filter(fact["pred"], "lt", spec.t)
+            tab = S.sirius_hash_join_build(dim["pk"], load_factor=0.5)
+            pp, pb = S.sirius_hash_join_probe(tab, fact["fk"], sel=ids)
+            vals = S.sirius_gather(fact["val"], pp)
+            keys = S.sirius_gather_group_key(dim["grp"], None, pb)
+            g = S.sirius_groupby_agg(keys, vals, group_cap_hint=100_000)
+        torch.cuda.synchronize()
+        print(f"profile case ok: operators over n={spec.n} m={spec.m}: {ids.numel()} selected, "
+              f"{pp.numel()} pairs, {g['key'].numel()} groups")
         return
     if a.batch > 0:
         specs = [dg.batch_query(q) for q in range(a.batch)]
