@@ -309,9 +309,9 @@ __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T,
       if (t == kEmpty32) t = gs;
     }
     if (t == gs) agg_update_smem(T, e, v, a.aggs);
-    else agg_update_global(&a.tab[gs], v, a.aggs);
+    else agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
   } else {
-    agg_update_global(&a.tab[gs], v, a.aggs);
+    agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
   }
 }
 
@@ -322,6 +322,14 @@ __device__ __forceinline__ void load_bucket(const void* slots, uint32_t s, uint6
   const char* p = reinterpret_cast<const char*>(slots) + (size_t)s * (kWide ? 16 : 8);
   if (kFresh) ldcg_bucket(p, w[0], w[1], w[2], w[3]);
   else ldg_bucket(p, w[0], w[1], w[2], w[3]);
+}
+
+// A read-only 4-byte load that asks L2 to keep the line (the direct array stays resident while
+// the fact columns stream past it).
+__device__ __forceinline__ uint32_t ldg_keep(const uint32_t* p) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_keep_policy()));
+  return v;
 }
 
 // Probe up to four rows (bit r of `bits` set = row r selected) and hand every (row, group slot,
@@ -339,7 +347,7 @@ __device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const uint32_t k = (uint32_t)key[r] - (uint32_t)L.kmin;
-      gs[r] = (((bits >> r) & 1u) && k < L.range) ? (kFresh ? __ldcg(a.dslot + k) : __ldg(a.dslot + k))
+      gs[r] = (((bits >> r) & 1u) && k < L.range) ? (kFresh ? __ldcg(a.dslot + k) : ldg_keep(a.dslot + k))
                                                    : kEmpty32;
     }
 #pragma unroll

@@ -139,6 +139,23 @@ __device__ __forceinline__ void agg_update_global(Agg* a, int64_t v, uint32_t ag
   if (aggs & SIRIUS_AGG_MAX) atomicMax(&a->max, (long long)v);
 }
 
+// The same four reductions with an L2 policy that keeps the aggregate lines resident while the
+// fact columns stream past them (createpolicy evict_last).
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void agg_update_global_keep(Agg* a, int64_t v, uint32_t aggs, uint64_t pol) {
+  if (aggs & SIRIUS_AGG_SUM)
+    asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(&a->sum), "l"(v), "l"(pol) : "memory");
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(&a->count), "l"(1ull), "l"(pol) : "memory");
+  if (aggs & SIRIUS_AGG_MIN)
+    asm volatile("red.global.min.L2::cache_hint.s64 [%0], %1, %2;" ::"l"(&a->min), "l"(v), "l"(pol) : "memory");
+  if (aggs & SIRIUS_AGG_MAX)
+    asm volatile("red.global.max.L2::cache_hint.s64 [%0], %1, %2;" ::"l"(&a->max), "l"(v), "l"(pol) : "memory");
+}
+
 __device__ __forceinline__ void agg_merge_global(Agg* a, unsigned long long sum, unsigned long long cnt,
                                                  long long mn, long long mx, uint32_t aggs) {
   if (aggs & SIRIUS_AGG_SUM) atomicAdd(&a->sum, sum);
