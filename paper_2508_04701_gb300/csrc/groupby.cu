@@ -157,13 +157,23 @@ group_global_kernel(const void* __restrict__ keys_in, int key_width, const int64
 
 // Direct slots, large table: four rows per thread (16-byte loads when the columns are 16-byte
 // aligned), every row's aggregates behind the block's cache of hot groups.
+// One launch per pass over the rows when the range's aggregates exceed what L2 keeps: pass p
+// aggregates only the slots [p * kPassSlots, (p + 1) * kPassSlots), so its reductions hit a
+// 48 MB window of the table that stays in L2 instead of fetching and writing back random DRAM
+// sectors; every pass reads the keys, and a value only where its quad has a row in the window.
+constexpr uint64_t kPassSlots = (48ull << 20) / sizeof(Agg);
+
 template <int kKeyWidth, bool kVec>
 __global__ void __launch_bounds__(512)
 group_direct_kernel(const void* __restrict__ keys_in, const int64_t* __restrict__ vals, int64_t n, uint32_t aggs,
-                    Agg* tab, const GroupHeader* hdr, unsigned long long limit) {
+                    Agg* tab, const GroupHeader* hdr, unsigned long long limit, int pass) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   const KeyRange kr = key_range(hdr, n, limit);
   if (!kr.direct) return;  // hashed keys: group_global_kernel
+  const uint64_t lo = (uint64_t)pass * kPassSlots;
+  if (lo >= kr.range) return;  // the range ends before this pass's window
+  const uint64_t width = kr.range - lo < kPassSlots ? kr.range - lo : kPassSlots;  // window [lo, lo + width)
+  const bool whole = lo == 0 && width == kr.range;  // one pass covers every slot
   ProbeArgs a{};
   a.tab = tab;
   a.aggs = aggs;
@@ -186,22 +196,30 @@ group_direct_kernel(const void* __restrict__ keys_in, const int64_t* __restrict_
         const longlong2 a1 = __ldcs(reinterpret_cast<const longlong2*>(keys_in) + 2 * q + 1);
         k[0] = a0.x, k[1] = a0.y, k[2] = a1.x, k[3] = a1.y;
       }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) k[r] = load_key(keys_in, kKeyWidth, 4 * q + r);
+    }
+    uint32_t in = 0;  // rows whose slot is in this pass's window
+#pragma unroll
+    for (int r = 0; r < 4; ++r) in |= (uint32_t)(whole || (uint64_t)(k[r] - kr.kmin) - lo < width) << r;
+    if (!in) continue;
+    if (kVec) {
       const longlong2 v0 = __ldcs(reinterpret_cast<const longlong2*>(vals) + 2 * q);
       const longlong2 v1 = __ldcs(reinterpret_cast<const longlong2*>(vals) + 2 * q + 1);
       v[0] = v0.x, v[1] = v0.y, v[2] = v1.x, v[3] = v1.y;
     } else {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        k[r] = load_key(keys_in, kKeyWidth, 4 * q + r);
-        v[r] = vals[4 * q + r];
-      }
+      for (int r = 0; r < 4; ++r) v[r] = ((in >> r) & 1u) ? vals[4 * q + r] : 0;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) aggregate<kAggHot>(a, T, (uint32_t)(uint64_t)(k[r] - kr.kmin), v[r]);
+    for (int r = 0; r < 4; ++r)
+      if ((in >> r) & 1u) aggregate<kAggHot>(a, T, (uint32_t)(uint64_t)(k[r] - kr.kmin), v[r]);
   }
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < n - (nq << 2)) {
     const int64_t i = (nq << 2) + threadIdx.x;
-    aggregate<kAggHot>(a, T, (uint32_t)(uint64_t)(load_key(keys_in, kKeyWidth, i) - kr.kmin), vals[i]);
+    const uint64_t slot = (uint64_t)(load_key(keys_in, kKeyWidth, i) - kr.kmin);
+    if (slot - lo < width) aggregate<kAggHot>(a, T, (uint32_t)slot, vals[i]);
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < (uint32_t)kHotEntries; i += blockDim.x)
@@ -373,8 +391,13 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
       int64_t gd = ((n >> 2) + 511) / 512;
       const int64_t most = (int64_t)sm_count() * 3;  // three 64 KB caches per SM
       gd = gd < 1 ? 1 : (gd > most ? most : gd);
-      kd<<<(unsigned)gd, 512, kHotSmemBytes, s>>>(d_keys, d_vals, n, aggs, tab, hdr, limit);
-      SIRIUS_LAUNCH_CHECK();
+      // passes over windows of the direct slots (the range is known on the device only: a pass
+      // whose window starts past it returns at once)
+      const int passes = (int)((group_limit_for(cap) + kPassSlots - 1) / kPassSlots);
+      for (int p = 0; p < passes; ++p) {
+        kd<<<(unsigned)gd, 512, kHotSmemBytes, s>>>(d_keys, d_vals, n, aggs, tab, hdr, limit, p);
+        SIRIUS_LAUNCH_CHECK();
+      }
       group_global_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(d_keys, key_width, d_vals, n, aggs,
                                                                      keys, tab, (uint32_t)cap, hdr, limit);
     }

@@ -303,9 +303,12 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
   }
 }
 
-// The fused probe pass: filter, probe and aggregate every fact row.
+// The fused probe pass: filter, probe and aggregate every fact row.  Held to 64 registers, so
+// that two 512-thread blocks share an SM: the pass needs the resident warps to cover its
+// memory latency (a 76-register build of the two-column-key variant ran one block per SM and
+// took 15.0 ms instead of 8.4 on the 600M-row query).
 template <bool kWide, int kMode, bool kVec, bool kSemi>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
 probe_kernel(ProbeArgs a, SemiArgs sa) {
   probe_body<kWide, kMode, kVec, kSemi>(a, sa);
 }

@@ -297,7 +297,10 @@ constexpr int kHotBits = 11;
 constexpr int kHotEntries = 1 << kHotBits;
 constexpr size_t kHotSmemBytes = smem_aggs_bytes(kHotEntries, true);
 
-template <int kMode>
+// kKeep: the global reductions carry an L2 evict_last hint (measured faster for star queries,
+// whose filter structures and aggregates compete with the streamed columns for L2; slower for
+// the others, which therefore go without it).
+template <int kMode, bool kKeep = false>
 __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T, uint32_t gs, int64_t v) {
   if (kMode == kAggSmem) {
     agg_update_smem(T, gs, v, a.aggs);
@@ -309,9 +312,12 @@ __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T,
       if (t == kEmpty32) t = gs;
     }
     if (t == gs) agg_update_smem(T, e, v, a.aggs);
-    else agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
-  } else {
+    else if (kKeep) agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
+    else agg_update_global(&a.tab[gs], v, a.aggs);
+  } else if (kKeep) {
     agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
+  } else {
+    agg_update_global(&a.tab[gs], v, a.aggs);
   }
 }
 
@@ -338,7 +344,7 @@ __device__ __forceinline__ uint32_t ldg_keep(const uint32_t* p) {
 // bucket only past full buckets.  kFresh: the join structures were built earlier in the same
 // launch (read through L2 only).  Without duplicate build keys a row matches at most once.
 // kRows < 4: the hash-table walk covers rows 0 .. kRows-1 only (fewer buckets held at once).
-template <bool kWide, bool kFresh, int kRows = 4, class Emit>
+template <bool kWide, bool kFresh, int kRows = 4, bool kKeep = false, class Emit>
 __device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup& L, uint32_t bits,
                                                 const uint64_t (&key)[4], const int64_t (&v)[4], Emit&& emit) {
   if (!kWide && L.direct) {
@@ -347,7 +353,7 @@ __device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const uint32_t k = (uint32_t)key[r] - (uint32_t)L.kmin;
-      gs[r] = (((bits >> r) & 1u) && k < L.range) ? (kFresh ? __ldcg(a.dslot + k) : ldg_keep(a.dslot + k))
+      gs[r] = (((bits >> r) & 1u) && k < L.range) ? (kFresh ? __ldcg(a.dslot + k) : (kKeep ? ldg_keep(a.dslot + k) : __ldg(a.dslot + k)))
                                                    : kEmpty32;
     }
 #pragma unroll
@@ -400,12 +406,13 @@ __device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup
   }
 }
 
-// The same, aggregating every match into the group table (kMode: where the aggregates live).
-template <bool kWide, int kMode, bool kFresh = false>
+// The same, aggregating every match into the group table (kMode: where the aggregates live;
+// kKeep: L2 keep hints on the direct-array reads and the reductions).
+template <bool kWide, int kMode, bool kFresh = false, bool kKeep = false>
 __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, uint32_t bits,
                                            const uint64_t (&key)[4], const int64_t (&v)[4]) {
-  probe_rows_emit<kWide, kFresh>(a, L, bits, key, v,
-                                 [&](int, uint32_t gs, int64_t val) { aggregate<kMode>(a, T, gs, val); });
+  probe_rows_emit<kWide, kFresh, 4, kKeep>(a, L, bits, key, v,
+                                           [&](int, uint32_t gs, int64_t val) { aggregate<kMode, kKeep>(a, T, gs, val); });
 }
 
 // Filter, probe and aggregate the four rows of quad q (rows 4q .. 4q+3, all < n).
@@ -531,7 +538,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
     key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? vv[r] : 0;
-    probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
+    probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, bits, key, v);
     return;
   }
   if (kVec) {
@@ -552,7 +559,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
       key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
 #pragma unroll
       for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-      probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
+      probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, bits, key, v);
       return;
     }
     if (!bits) return;
@@ -581,7 +588,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-  probe_rows<kWide, kMode, kFresh>(a, T, L, bits, key, v);
+  probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, bits, key, v);
 }
 
 // Two quads (qa, qb, both below n/4; 16-byte loads; one-column keys joined through the direct
@@ -632,7 +639,7 @@ __device__ __forceinline__ void probe_one(const ProbeArgs& a, const SmemAggs& T,
   int64_t v[4] = {0, 0, 0, 0};
   key[0] = kWide ? pack_key64(a.fk_hi[r], a.fk[r]) : (uint64_t)(uint32_t)a.fk[r];
   v[0] = a.val[r];
-  probe_rows<kWide, kMode, kFresh>(a, T, L, 1u, key, v);
+  probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, 1u, key, v);
 }
 
 // The dim-side predicate of a build (col == nullptr: every dim row takes part).

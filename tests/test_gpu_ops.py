@@ -218,10 +218,11 @@ def test_groupby_subsets_and_single_group(S):
 
 
 @pytest.mark.parametrize("offset", [0, 1])
-@pytest.mark.parametrize("n,dom", [(5, 3), (3_000_003, 1_000_000), (2_000_001, 4000)])
+@pytest.mark.parametrize("n,dom", [(5, 3), (3_000_003, 1_000_000), (2_000_001, 4000), (6_000_001, 4_000_000)])
 def test_groupby_direct_slots_large_tables(S, n, dom, offset):
     """Dense keys of a table too large for shared memory: direct slots (key - min) behind the
-    hot-group cache, 16-byte loads (offset 0) or scalar loads (columns one element off)."""
+    hot-group cache, 16-byte loads (offset 0) or scalar loads (columns one element off); a range of
+    4M slots is aggregated in three passes over L2-sized windows of the table."""
     rng = np.random.default_rng(n + dom + offset)
     keys = (rng.integers(0, dom, size=n + offset) - dom // 3).astype(np.int32)
     vals = rng.integers(-10**12, 10**12, size=n + offset)
