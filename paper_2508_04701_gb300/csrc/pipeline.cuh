@@ -379,26 +379,35 @@ __device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup
       load_bucket<kWide, kFresh>(a.jslots, s[r], w[r]);
     }
   }
+  // Each bucket is scanned branch-free into a mask of matching slots before its first empty slot;
+  // the matches are then emitted from one site per row (the first one only without duplicate
+  // keys), which keeps the unrolled code -- and the instruction cache -- small.
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
     if (!((bits >> r) & 1u)) continue;
     uint32_t slot = s[r];
     for (uint32_t step = 0; step < a.jcap; step += kPer) {
-      bool stop = false;
+      uint32_t mm = 0, em = 0;
+      uint32_t pay[kPer];
 #pragma unroll
-      for (int j = 0; j < kPer; ++j) {  // fully unrolled: bucket words stay in registers
+      for (int j = 0; j < kPer; ++j) {
         const uint64_t k = kWide ? w[r][2 * j] : (uint64_t)(uint32_t)w[r][j];
-        const uint32_t p = kWide ? (uint32_t)w[r][2 * j + 1] : (uint32_t)(w[r][j] >> 32);
-        if (!stop) {
-          if (p == kEmpty32) {
-            stop = true;
-          } else if (k == key[r]) {
-            emit(r, p, v[r]);
-            stop = !dups;
-          }
-        }
+        pay[j] = kWide ? (uint32_t)w[r][2 * j + 1] : (uint32_t)(w[r][j] >> 32);
+        em |= (uint32_t)(pay[j] == kEmpty32) << j;
+        mm |= (uint32_t)(pay[j] != kEmpty32 && k == key[r]) << j;
       }
-      if (stop) break;
+      if (em) mm &= (em & (0u - em)) - 1;  // only slots before the first empty one
+      if (!dups) mm &= 0u - mm;             // unique keys: the first match only
+      const bool done = em != 0 || (!dups && mm != 0);
+      while (mm) {
+        const int j = __ffs(mm) - 1;
+        uint32_t p = pay[0];
+#pragma unroll
+        for (int t = 1; t < kPer; ++t) p = j == t ? pay[t] : p;
+        emit(r, p, v[r]);
+        mm &= mm - 1;
+      }
+      if (done) break;
       slot += kPer;
       if (slot >= a.jcap) slot = 0;
       load_bucket<kWide, kFresh>(a.jslots, slot, w[r]);
