@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda/atomic>
+#include <atomic>
 #include <stdint.h>
 #include <string.h>
 
@@ -61,6 +62,20 @@ constexpr uint64_t kEmpty64 = 0xFFFFFFFFFFFFFFFFull;
 constexpr int64_t kEmptyKey = INT64_MIN;     // empty slot of a group table
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Raises a kernel's dynamic shared-memory limit once per device (one bit per device ordinal in
+// `done`; two threads racing on a device's first call both set it, which is harmless).
+template <typename K>
+inline cudaError_t ensure_smem_limit(K kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // Scratch handed to a call: either the caller's buffer or one allocated stream-ordered.
 struct Scratch {

@@ -370,12 +370,8 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
   if (n > 0) {
     if (cap <= kSmemMaxCap) {
       const size_t smem = (size_t)(cap + 1) * (sizeof(Agg) + 8);
-      static bool attr_set = false;
-      if (!attr_set) {
-        SIRIUS_CUDA_TRY(cudaFuncSetAttribute(group_smem_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-        attr_set = true;
-      }
+      static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
+      SIRIUS_CUDA_TRY(ensure_smem_limit(group_smem_kernel, 100 * 1024, smem_set));
       int64_t want = (n + kThreads * 16 - 1) / (kThreads * 16);
       int64_t maxg = (int64_t)sm_count() * 2;
       int g = (int)(want < maxg ? (want > 0 ? want : 1) : maxg);

@@ -462,11 +462,8 @@ sirius_status launch_probe(const ProbeArgs& a, const SemiArgs& sa, int threads, 
   if constexpr (kSemi) k = probe_star_kernel<kWide, kMode, kVec>;
   else k = probe_kernel<kWide, kMode, kVec, false>;
   if (kMode == kAggSmem || kMode == kAggHot) {
-    static bool attr = false;
-    if (!attr) {
-      SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
+    SIRIUS_CUDA_TRY(ensure_smem_limit(k, 200 * 1024, smem_set));
   }
   int per_sm = blocks_per_sm;
   if (per_sm <= 0) {
@@ -505,11 +502,8 @@ sirius_status launch_part(const ProbeArgs& a, const part::PartArgs& pa, bool vec
   }
   PhaseTimer pt2(s, SIRIUS_PHASE_PIPE_AGGREGATE);
   const size_t smem = (size_t)part::kPartSlots * sizeof(Agg);
-  static bool attr = false;
-  if (!attr) {
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(part::part_agg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(part::part_agg_kernel, (int)smem, smem_set));
   // about three waves of one block per SM over all partitions
   int64_t kb = ((int64_t)sm_count() * 3 + pa.parts - 1) / pa.parts;
   if (kb < 1) kb = 1;
@@ -526,11 +520,8 @@ template <bool kWide>
 sirius_status launch_staged(const ProbeArgs& a, PipeHeader* phdr, cudaStream_t s) {
   auto k = staged::probe_staged_kernel<kWide>;
   const size_t smem = staged::smem_bytes(kWide);
-  static bool attr = false;
-  if (!attr) {
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(k, (int)smem, smem_set));
   const int64_t tiles = (((a.n >> 2) << 2) + staged::kTile - 1) / staged::kTile;
   int64_t g = sm_count();
   if (g > tiles) g = tiles;
@@ -606,11 +597,8 @@ sirius_status dispatch_probe(const ProbeArgs& a, const SemiArgs& sa, int mode, b
 template <bool kWide, int kMode, bool kVec>
 sirius_status launch_single(const SingleArgs& g, int threads, int per_sm, size_t smem, cudaStream_t s) {
   auto k = single_query_kernel<kWide, kMode, kVec>;
-  static bool attr = false;
-  if (!attr) {
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(k, 200 * 1024, smem_set));
   // One block per SM (the default) always fits: 512 threads at the 128 registers the launch
   // bound allows, and the shared memory raised above; only a larger request asks the runtime
   // (a query per call would add its host time to every small query).

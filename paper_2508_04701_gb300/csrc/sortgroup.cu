@@ -569,16 +569,12 @@ __global__ void sg_copy_groups_kernel(const SgHeader* h, int64_t* d_groups) {
 template <typename K>
 sirius_status sg_run(const void* d_keys, const int64_t* d_vals, int64_t n, const SgOut& o, char* base,
                      const SgLayout& L, SgHeader* hdr, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(sg_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sg_scatter_smem<K>()));
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(sg_reduce_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSgReduceSmem(sizeof(K))));
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(sg_upfront_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(K) * sg_copies<K>() * 256 * 4)));
-    attr = true;
-  }
+  static std::atomic<uint64_t> smem_set0{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(sg_scatter_kernel<K>, (int)sg_scatter_smem<K>(), smem_set0));
+  static std::atomic<uint64_t> smem_set1{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(sg_reduce_kernel<K>, (int)kSgReduceSmem(sizeof(K)), smem_set1));
+  static std::atomic<uint64_t> smem_set2{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(sg_upfront_kernel<K>, (int)(sizeof(K) * sg_copies<K>() * 256 * 4), smem_set2));
   SgBufs<K> b;
   b.in_k = reinterpret_cast<const K*>(d_keys);
   b.in_v = d_vals;

@@ -213,12 +213,8 @@ extern "C" sirius_status sirius_topn_groups(const int64_t* d_keys, const int64_t
   int64_t p2 = 1;
   while (p2 < rank) p2 <<= 1;
   const size_t smem = (size_t)p2 * sizeof(Word);
-  static bool attr = false;
-  if (!attr) {
-    SIRIUS_CUDA_TRY(cudaFuncSetAttribute(top_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kTopMax * sizeof(Word))));
-    attr = true;
-  }
+  static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(top_sort_kernel, (int)(kTopMax * sizeof(Word)), smem_set));
   top_sort_kernel<<<1, 1024, smem, s>>>(words, state, rank, d_out_idx, d_count);
   SIRIUS_LAUNCH_CHECK();
   if (h_count) {
