@@ -22,6 +22,10 @@ constexpr int kFilterK = 8;                                  // 16-byte vectors 
 constexpr int kWarpRows = 32 * 4 * kFilterK;                 // 1024
 constexpr int kTileRows = kWarpRows * (kFilterThreads / 32);  // 8192
 constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
+// Bound of one look-back wait: 2^21 polls, the later ones 256 ns apart (about half a second).
+// A predecessor tile that is running publishes its count within microseconds, so only a
+// predecessor that cannot run -- its GPU time-sliced away to another context for longer than the
+// bound, or a fault -- turns into SIRIUS_ERR_TIMEOUT; the caller may then simply retry the call.
 constexpr int kSpinLimit = 1 << 21;
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {

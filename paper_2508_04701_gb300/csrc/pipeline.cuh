@@ -743,7 +743,11 @@ __device__ __forceinline__ bool direct_applies(const DimView& d, int64_t m) {
 }
 
 // ------------------------------------------------------------------ grid-wide barrier
-// Spins of one barrier wait (64 ns sleeps: about half a second) before it gives up.
+// Spins of one barrier wait (64 ns sleeps: about half a second) before it gives up.  Every block
+// of a cooperative launch is resident, so a barrier normally completes within microseconds; the
+// bound is reached only when blocks cannot run (the GPU time-sliced to another context for longer
+// than the bound, or a fault), and the call then reports SIRIUS_ERR_TIMEOUT, which a caller may
+// retry.
 constexpr uint32_t kGridBarrierSpins = 1u << 23;
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {

@@ -30,11 +30,14 @@ def encode(S, off, chars, **kw):
     return codes.cpu().numpy(), rows.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,d", [(1, 1), (1000, 7), (4099, 4099), (100_003, 5000), (300_000, 200_000)])
-@pytest.mark.parametrize("weak", [False, True])
+# the 8-bit test hash forces collisions: every distinct string shares its hash with ~d/256
+# others, so the weak-hash cases stop at sizes where those chains stay short
+GENERATED = [(n, d, False) for n, d in [(1, 1), (1000, 7), (4099, 4099), (100_003, 5000), (300_000, 200_000)]] + \
+            [(n, d, True) for n, d in [(1, 1), (1000, 7), (4099, 4099), (100_003, 5000)]]
+
+
+@pytest.mark.parametrize("n,d,weak", GENERATED)
 def test_dict_encode_generated(S, n, d, weak):
-    if weak and n > 100_003:
-        pytest.skip("the 8-bit hash makes long probe chains at this size")
     col = dg.gen_strings_host(dg.StringSpec(n=n, d=d, seed=n % 97))
     want_codes, want_rows = O.dict_encode(col["offsets"], col["chars"])
     codes, rows = encode(S, col["offsets"], col["chars"], distinct_hint=d, weak_hash=weak)
