@@ -332,14 +332,8 @@ typedef struct {
                                buffer in scratch, one grid-wide barrier per round of rows
                                (group tables up to 256 x 2000 slots; larger tables and star
                                queries use 4; duplicate build keys make the launch use global
-                               reductions); 6 bound filter: a 512-entry hot-group cache, and
-                               for each of the first 102 400 group slots two bytes of shared
-                               memory bounding the slot's MAX from below and MIN from above by
-                               values the block already reduced, so that a row which cannot
-                               move an extreme skips that reduction (one block per SM; exact
-                               whatever the values; star queries, the single launch and
-                               queries without MIN and MAX use 4).  Auto: 1 when it fits,
-                               else 4 from 1Mi fact rows, else 2 */
+                               reductions).  Auto: 1 when it fits, else 4 from 1Mi fact rows,
+                               else 2 */
   int64_t group_cap_hint;   /* expected distinct group keys in the dim; 0 -> m */
   float load_factor;        /* join table load factor; 0 -> default 0.5 */
   int32_t block_threads;    /* probe kernel block size; 0 -> default */

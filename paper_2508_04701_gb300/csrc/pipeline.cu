@@ -257,46 +257,6 @@ __global__ void semi_build_kernel(SemiInput in, SemiView v) {
   }
 }
 
-// The bound filter's state for this block (kAggFilt): bound bytes cleared (0 = no bound) and
-// the code scale taken from the values of the block's first rows (the rows of each thread's
-// first quad): base = their minimum, and a shift that maps their range onto about 256 codes.
-// Ends with a block barrier.
-__device__ __noinline__ void filt_setup(const ProbeArgs& a, SmemAggs& T, unsigned char* code) {
-  __shared__ long long s_lo, s_hi;
-  T.code = code;
-  T.fslots = filt_slots(a.gslots);
-  const uint32_t words = (T.fslots * 2 + 15) / 16;
-  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) reinterpret_cast<uint4*>(code)[i] = make_uint4(0, 0, 0, 0);
-  if (threadIdx.x == 0) {
-    s_lo = LLONG_MAX;
-    s_hi = LLONG_MIN;
-  }
-  __syncthreads();
-  long long lo = LLONG_MAX, hi = LLONG_MIN;
-  const int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  for (int r = 0; r < 4; ++r) {
-    if (r0 + r < a.n) {
-      const long long v = a.val[r0 + r];
-      lo = v < lo ? v : lo;
-      hi = v > hi ? v : hi;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    lo = l2 < lo ? l2 : lo;
-    hi = h2 > hi ? h2 : hi;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(&s_lo, lo);
-    atomicMax(&s_hi, hi);
-  }
-  __syncthreads();
-  const long long base = s_lo;
-  const uint64_t range = s_hi > base ? (uint64_t)s_hi - (uint64_t)base : 0;
-  T.qbase = base;
-  T.qshift = range < 256 ? 0u : (uint32_t)(56 - __clzll((long long)range));
-}
-
 // kFresh: the build ran earlier in the same launch (the single-launch kernel): its headers and
 // tables are read through L2 only.  Every thread of the block takes part.
 template <bool kWide, int kMode, bool kVec, bool kSemi, bool kFresh = false>
@@ -313,24 +273,20 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
     __syncthreads();
     SLp = &s_sl;
   }
-  constexpr bool kHotCache = kMode == kAggHot || kMode == kAggFilt;
-  const uint32_t slots = kMode == kAggSmem ? a.gslots
-                         : (kMode == kAggHot ? (uint32_t)kHotEntries : (kMode == kAggFilt ? (uint32_t)kFiltHotEntries : 0u));
-  SmemAggs T = smem_aggs(smem_raw, slots);
-  if (kMode == kAggFilt) filt_setup(a, T, smem_raw + smem_aggs_bytes(kFiltHotEntries, true));
-  if (kMode == kAggSmem || kHotCache) {
+  const uint32_t slots = kMode == kAggSmem ? a.gslots : (kMode == kAggHot ? (uint32_t)kHotEntries : 0u);
+  const SmemAggs T = smem_aggs(smem_raw, slots);
+  if (kMode == kAggSmem || kMode == kAggHot) {
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
       smem_identity(T, i);
-      if (kHotCache) T.tag[i] = kEmpty32;
+      if (kMode == kAggHot) T.tag[i] = kEmpty32;
     }
     __syncthreads();
   }
   const int64_t nq = a.n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if constexpr ((kFresh || kMode == kAggFilt) && kVec && !kWide && !kSemi) {
-    // one block per SM (the single launch, the bound filter), registers to spare: two quads in
-    // flight per thread
+  if constexpr (kFresh && kVec && !kWide && !kSemi) {
+    // the single launch (one block per SM, registers to spare): two quads in flight per thread
     if (L.direct)
       for (; q + stride < nq; q += 2 * stride) probe_quad_pair_direct<kMode, true>(a, T, L, q, q + stride);
   }
@@ -338,7 +294,7 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
     probe_one<kWide, kMode, kSemi, kFresh>(a, T, L, (nq << 2) + threadIdx.x, SLp);
-  if (kMode == kAggSmem || kHotCache) {
+  if (kMode == kAggSmem || kMode == kAggHot) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
       if (kMode == kAggSmem) smem_merge(T, i, &a.tab[i], a.aggs);
@@ -350,10 +306,9 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
 // The fused probe pass: filter, probe and aggregate every fact row.  Held to 64 registers, so
 // that two 512-thread blocks share an SM: the pass needs the resident warps to cover its
 // memory latency (a 76-register build of the two-column-key variant ran one block per SM and
-// took 15.0 ms instead of 8.4 on the 600M-row query).  The bound filter's shared memory leaves
-// room for one block per SM, which may then use 128 registers.
+// took 15.0 ms instead of 8.4 on the 600M-row query).
 template <bool kWide, int kMode, bool kVec, bool kSemi>
-__global__ void __launch_bounds__(512, kMode == kAggFilt ? 1 : 2)
+__global__ void __launch_bounds__(512, 2)
 probe_kernel(ProbeArgs a, SemiArgs sa) {
   probe_body<kWide, kMode, kVec, kSemi>(a, sa);
 }
@@ -506,15 +461,15 @@ sirius_status launch_probe(const ProbeArgs& a, const SemiArgs& sa, int threads, 
   void (*k)(ProbeArgs, SemiArgs);
   if constexpr (kSemi) k = probe_star_kernel<kWide, kMode, kVec>;
   else k = probe_kernel<kWide, kMode, kVec, false>;
-  if (kMode == kAggSmem || kMode == kAggHot || kMode == kAggFilt) {
+  if (kMode == kAggSmem || kMode == kAggHot) {
     static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
-    SIRIUS_CUDA_TRY(ensure_smem_limit(k, kMode == kAggFilt ? (int)filt_smem_bytes(kFiltMaxSlots) : 200 * 1024, smem_set));
+    SIRIUS_CUDA_TRY(ensure_smem_limit(k, 200 * 1024, smem_set));
   }
   int per_sm = blocks_per_sm;
   if (per_sm <= 0) {
     // residency depends on the block size (and on the shared-memory table when there is one)
     static int occ_by_warps[17] = {};
-    if (kMode == kAggSmem || kMode == kAggHot || kMode == kAggFilt) {
+    if (kMode == kAggSmem || kMode == kAggHot) {
       per_sm = occupancy_blocks(k, threads, smem);
     } else {
       int& c = occ_by_warps[(threads / 32) & 15];
@@ -629,14 +584,9 @@ sirius_status dispatch_probe(const ProbeArgs& a, const SemiArgs& sa, int mode, b
   if (mode == kAggSmem)
     return vec ? launch_probe<kWide, kAggSmem, true, kSemi>(a, sa, threads, bps, smem, s)
                : launch_probe<kWide, kAggSmem, false, kSemi>(a, sa, threads, bps, smem, s);
-  if (mode == kAggHot || (kSemi && mode == kAggFilt))
+  if (mode == kAggHot)
     return vec ? launch_probe<kWide, kAggHot, true, kSemi>(a, sa, threads, bps, kHotSmemBytes, s)
                : launch_probe<kWide, kAggHot, false, kSemi>(a, sa, threads, bps, kHotSmemBytes, s);
-  if constexpr (!kSemi) {
-    if (mode == kAggFilt)
-      return vec ? launch_probe<kWide, kAggFilt, true, false>(a, sa, threads, bps, filt_smem_bytes(a.gslots), s)
-                 : launch_probe<kWide, kAggFilt, false, false>(a, sa, threads, bps, filt_smem_bytes(a.gslots), s);
-  }
   return vec ? launch_probe<kWide, kAggGlobal, true, kSemi>(a, sa, threads, bps, 0, s)
              : launch_probe<kWide, kAggGlobal, false, kSemi>(a, sa, threads, bps, 0, s);
 }
@@ -686,7 +636,7 @@ sirius_status dispatch_single(const SingleArgs& g, int mode, bool vec, int threa
   if (mode == kAggSmem)
     return vec ? launch_single<kWide, kAggSmem, true>(g, threads, per_sm, smem, s)
                : launch_single<kWide, kAggSmem, false>(g, threads, per_sm, smem, s);
-  if (mode == kAggHot || mode == kAggFilt)  // the single launch keeps the plain hot-group cache
+  if (mode == kAggHot)
     return vec ? launch_single<kWide, kAggHot, true>(g, threads, per_sm, kHotSmemBytes, s)
                : launch_single<kWide, kAggHot, false>(g, threads, per_sm, kHotSmemBytes, s);
   return vec ? launch_single<kWide, kAggGlobal, true>(g, threads, per_sm, 0, s)
@@ -830,7 +780,7 @@ sirius_status validate_fact(const sirius_pipeline_desc* q) {
   SIRIUS_REQUIRE(q->n == 0 || (q->fk && q->pred && q->val), "pipeline: NULL fact column");
   SIRIUS_REQUIRE(q->op >= SIRIUS_LT && q->op <= SIRIUS_NE, "pipeline: bad comparison %d", q->op);
   SIRIUS_REQUIRE(q->aggs <= SIRIUS_AGG_ALL, "pipeline: bad aggregate mask");
-  SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= kAggFilt, "pipeline: bad agg_mode %d", q->agg_mode);
+  SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= kAggRouted, "pipeline: bad agg_mode %d", q->agg_mode);
   SIRIUS_REQUIRE(q->block_threads == 0 || (q->block_threads % 32 == 0 && q->block_threads >= 64 &&
                                            q->block_threads <= 512),
                  "pipeline: block_threads must be a multiple of 32 in [64, 512]");
@@ -878,7 +828,6 @@ int choose_mode(int agg_mode, int64_t gslots, int64_t n) {
   if (agg_mode == kAggPart) return part_ok ? kAggPart : kAggGlobal;
   if (agg_mode == kAggHot) return n > 0 ? kAggHot : kAggGlobal;
   if (agg_mode == kAggRouted) return (n > 0 && route_plan(gslots).R > 0) ? kAggRouted : (n > 0 ? kAggHot : kAggGlobal);
-  if (agg_mode == kAggFilt) return n > 0 ? kAggFilt : kAggGlobal;
   if (fits) return kAggSmem;
   // large group tables: the hot-group cache (measured: skewed 300M-row query 38.5 -> 3.3 ms,
   // uniform 600M-row query 5.31 -> 5.15 ms against plain reductions)
@@ -980,13 +929,7 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   SemiArgs sa;
   sa.nsemi = nsemi;
   for (int i = 0; i < kMaxSemi; ++i) sa.semi[i] = i < nsemi ? semi[i] : SemiView{};
-  // star queries take neither the routed probe nor the bound filter; nor do queries without
-  // MIN or MAX (nothing to filter): those run with the plain hot-group cache
-  const bool extremes = (q->aggs & (SIRIUS_AGG_MIN | SIRIUS_AGG_MAX)) != 0;
-  const int mode = ((r.mode == kAggRouted || r.mode == kAggFilt) && nsemi > 0) ||
-                           (r.mode == kAggFilt && !extremes)
-                       ? kAggHot
-                       : r.mode;
+  const int mode = (r.mode == kAggRouted && nsemi > 0) ? kAggHot : r.mode;
   bool vec = vec_columns(q);
   for (int i = 0; i < nsemi; ++i)  // a star query's key columns take the vector loads too
     vec = vec && ((uintptr_t)semi[i].fk & 15) == 0 && (!semi[i].fk_hi || ((uintptr_t)semi[i].fk_hi & 15) == 0);
@@ -1003,8 +946,7 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
     PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
     return d.key_width == 8 ? launch_staged<true>(a, r.phdr, s) : launch_staged<false>(a, r.phdr, s);
   }
-  const int threads =
-      q->block_threads > 0 ? q->block_threads : (mode == kAggSmem || mode == kAggHot || mode == kAggFilt ? 512 : 256);
+  const int threads = q->block_threads > 0 ? q->block_threads : (mode == kAggSmem || mode == kAggHot ? 512 : 256);
   const size_t smem = mode == kAggSmem ? smem_aggs_bytes((uint32_t)gslots, false) : 0;  // hot cache: fixed size
   PhaseTimer pt(s, SIRIUS_PHASE_PIPE_PROBE);
   if (nsemi > 0)
@@ -1171,7 +1113,7 @@ static sirius_status semi_build(const sirius_pipeline_desc* q, char* base, SemiV
 static int star_agg_mode(const sirius_pipeline_desc* q) {
   if (q->nsemi <= 0) return q->agg_mode;
   if (q->agg_mode == kAggPart) return kAggGlobal;
-  if (q->agg_mode == kAggRouted || q->agg_mode == kAggFilt) return kAggHot;
+  if (q->agg_mode == kAggRouted) return kAggHot;
   return q->agg_mode;
 }
 

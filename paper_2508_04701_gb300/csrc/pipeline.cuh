@@ -8,7 +8,7 @@
 
 namespace sirius {
 
-enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2, kAggPart = 3, kAggHot = 4, kAggRouted = 5, kAggFilt = 6 };
+enum { kAggAuto = 0, kAggSmem = 1, kAggGlobal = 2, kAggPart = 3, kAggHot = 4, kAggRouted = 5 };
 constexpr int64_t kSmemAggMaxBytes = 96 * 1024;  // shared-memory aggregates up to 3510 slots
 
 // Build side ("dim index"): [DimHeader | JoinHeader + join slots | group keys[gcap + 1]].
@@ -258,12 +258,6 @@ struct SmemAggs {
   long long* mx = nullptr;
   uint32_t* cnt = nullptr;
   uint32_t* tag = nullptr;  // hot-group cache only
-  // bound filter (kAggFilt only): two bytes per group slot below fslots, and the scale of the
-  // block's value codes
-  unsigned char* code = nullptr;
-  uint32_t fslots = 0;
-  uint32_t qshift = 0;
-  long long qbase = 0;
 };
 __host__ __device__ constexpr size_t smem_aggs_bytes(uint32_t slots, bool tags) {
   return (size_t)slots * (tags ? 32 : 28);
@@ -303,71 +297,6 @@ constexpr int kHotBits = 11;
 constexpr int kHotEntries = 1 << kHotBits;
 constexpr size_t kHotSmemBytes = smem_aggs_bytes(kHotEntries, true);
 
-// Bound filter (kAggFilt): the hot-group cache (kFiltHotEntries entries) plus, for every group
-// slot below kFiltMaxSlots, two bytes in shared memory that bound the slot's MAX from below and
-// its MIN from above by values this block has already sent to the global aggregates.  A row
-// whose value cannot move a bound skips that reduction, so a uniform key distribution costs
-// about two L2 reductions per joined row (SUM, COUNT) instead of four.
-//
-// Codes.  q(v) in [0, 254] is monotone in v: 0 up to the block's base value, then the distance
-// to it shifted right by qshift bits, capped at 254 (base and shift come from the values of the
-// block's first rows: they only decide how well the filter works, never what it computes).  The
-// MAX byte of a slot is 0 (no bound) or q(v0) + 1 for a value v0 this block reduced into the
-// slot's MAX; the MIN byte is 0 or 255 - q(v0) for a value v0 reduced into its MIN.  A row with
-// value v skips the MAX reduction when q(v) < q(v0), which implies v < v0 <= the final MAX (the
-// block's own reduction of v0 lands before the launch ends); likewise for MIN.  The bytes are
-// updated with plain byte stores: a store lost to a race leaves an older byte, which still comes
-// from a reduced value, so every state of the bytes is a valid bound and the results are exact.
-constexpr int kFiltHotBits = 9;
-constexpr int kFiltHotEntries = 1 << kFiltHotBits;
-constexpr uint32_t kFiltMaxSlots = 102400;  // 200 KB of bound bytes
-__host__ __device__ constexpr uint32_t filt_slots(uint32_t gslots) {
-  return gslots < kFiltMaxSlots ? gslots : kFiltMaxSlots;
-}
-__host__ __device__ constexpr size_t filt_smem_bytes(uint32_t gslots) {
-  return smem_aggs_bytes(kFiltHotEntries, true) + (((size_t)filt_slots(gslots) * 2 + 15) & ~(size_t)15);
-}
-__device__ __forceinline__ uint32_t filt_code(int64_t v, long long base, uint32_t shift) {
-  if (v <= base) return 0;
-  const uint64_t d = ((uint64_t)v - (uint64_t)base) >> shift;
-  return d < 254 ? (uint32_t)d : 254u;
-}
-// The four global reductions of one joined row, MIN and MAX behind the slot's bounds.
-__device__ __forceinline__ void agg_update_filtered(Agg* g, const SmemAggs& T, uint32_t gs, int64_t v, uint32_t aggs) {
-  if (aggs & SIRIUS_AGG_SUM) atomicAdd(&g->sum, (unsigned long long)v);
-  atomicAdd(&g->count, 1ull);
-  if (gs >= T.fslots) {
-    if (aggs & SIRIUS_AGG_MIN) atomicMin(&g->min, (long long)v);
-    if (aggs & SIRIUS_AGG_MAX) atomicMax(&g->max, (long long)v);
-    return;
-  }
-  const uint32_t q = filt_code(v, T.qbase, T.qshift);
-  volatile unsigned char* c = T.code + 2 * (size_t)gs;
-  const uint32_t both = *reinterpret_cast<volatile uint16_t*>(c);
-  const uint32_t hi = q + 1, lo = 255 - q;
-  if ((aggs & SIRIUS_AGG_MAX) && hi >= (both & 0xffu)) {
-    atomicMax(&g->max, (long long)v);
-    if (hi > (both & 0xffu)) c[0] = (unsigned char)hi;
-  }
-  if ((aggs & SIRIUS_AGG_MIN) && lo >= (both >> 8)) {
-    atomicMin(&g->min, (long long)v);
-    if (lo > (both >> 8)) c[1] = (unsigned char)lo;
-  }
-}
-
-// A direct-mapped hot-group cache of 2^kBits entries: the entry of group slot gs, claimed for gs
-// when free; true when the entry is gs's.
-template <int kBits>
-__device__ __forceinline__ bool hot_entry(const SmemAggs& T, uint32_t gs, uint32_t& e) {
-  e = (gs * 2654435761u) >> (32 - kBits);
-  uint32_t t = *(volatile uint32_t*)&T.tag[e];
-  if (t == kEmpty32) {
-    t = atomicCAS(&T.tag[e], kEmpty32, gs);
-    if (t == kEmpty32) t = gs;
-  }
-  return t == gs;
-}
-
 // kKeep: the global reductions carry an L2 evict_last hint (measured faster for star queries,
 // whose filter structures and aggregates compete with the streamed columns for L2; slower for
 // the others, which therefore go without it).
@@ -376,14 +305,15 @@ __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T,
   if (kMode == kAggSmem) {
     agg_update_smem(T, gs, v, a.aggs);
   } else if (kMode == kAggHot) {
-    uint32_t e;
-    if (hot_entry<kHotBits>(T, gs, e)) agg_update_smem(T, e, v, a.aggs);
+    const uint32_t e = (gs * 2654435761u) >> (32 - kHotBits);
+    uint32_t t = *(volatile uint32_t*)&T.tag[e];
+    if (t == kEmpty32) {
+      t = atomicCAS(&T.tag[e], kEmpty32, gs);
+      if (t == kEmpty32) t = gs;
+    }
+    if (t == gs) agg_update_smem(T, e, v, a.aggs);
     else if (kKeep) agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
     else agg_update_global(&a.tab[gs], v, a.aggs);
-  } else if (kMode == kAggFilt) {
-    uint32_t e;
-    if (hot_entry<kFiltHotBits>(T, gs, e)) agg_update_smem(T, e, v, a.aggs);
-    else agg_update_filtered(&a.tab[gs], T, gs, v, a.aggs);
   } else if (kKeep) {
     agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
   } else {

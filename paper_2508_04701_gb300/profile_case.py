@@ -35,7 +35,7 @@ def main():
     p.add_argument("--runs", type=int, default=2)
     p.add_argument("--workload", default="plain", choices=["plain", "composite", "skewed", "star", "plain_1M"])
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
-    p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot", "routed", "bounds"])
+    p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot", "routed"])
     p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
     p.add_argument("--op", default="pipeline", choices=["pipeline", "sort", "strings", "operators"])
     a = p.parse_args()

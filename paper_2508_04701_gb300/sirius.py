@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CAPACITY", 4: "TABLE_FULL",
 LT, LE, GT, GE, EQ, NE = range(6)
 OPS = {"lt": LT, "le": LE, "gt": GT, "ge": GE, "eq": EQ, "ne": NE}
 AGG_SUM, AGG_COUNT, AGG_MIN, AGG_MAX, AGG_ALL = 1, 2, 4, 8, 15
-AGG_MODES = {"auto": 0, "smem": 1, "global": 2, "part": 3, "hot": 4, "routed": 5, "bounds": 6}
+AGG_MODES = {"auto": 0, "smem": 1, "global": 2, "part": 3, "hot": 4, "routed": 5}
 PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2, "single": 3}
 BLOOM_MODES = {"auto": 0, "off": 1, "on": 2}
 JOIN_MODES = {"auto": 0, "hash": 1}
