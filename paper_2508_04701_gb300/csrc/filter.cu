@@ -1,15 +1,18 @@
 // A2: predicate filter with stable stream compaction (Sec. 3.2.2 predicate pushdown; Sec. 4.2).
 //
-// One pass over the column.  A thread block owns a tile of 8192 rows (8 warps x 1024 rows; a
-// lane reads eight 16-byte vectors, rows 4*(lane + 32k) .. +3 of its warp's slice, all eight in
-// flight together).  Each warp ranks its selected rows with ballots and popcounts; the block
-// scans its 8 warp totals and publishes the tile's count at once; the selected row ids are
-// placed in shared memory in row order while warp 0 finds the tile's output offset with a
-// decoupled look-back over the tiles before it (Merrill & Garland, "Single-pass Parallel Prefix
-// Scan with Decoupled Look-back", NVIDIA technical report NVR-2016-002); then the block copies
-// its ids out as one contiguous, coalesced run.  Tiles take tickets from an atomic counter, so
-// every tile a look-back waits on has already started; each wait is still bounded and reports
-// TIMEOUT.
+// One pass over the column.  A thread block owns a tile of 32768 rows (8 warps x 4096 rows; a
+// lane reads thirty-two 16-byte vectors, rows 4*(lane + 32k) .. +3 of its warp's slice, in two
+// phases of sixteen loads in flight together).  Each warp counts its selected rows; the block
+// scans its 8 warp totals and publishes the tile's count at once; ballots and popcounts rank
+// the selected rows, whose offsets in the tile (16-bit) are placed in shared memory in row
+// order while warp 0 finds the tile's output offset with a decoupled look-back over the tiles
+// before it (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back",
+// NVIDIA technical report NVR-2016-002); then the block writes its ids out as one contiguous,
+// coalesced run.  Large tiles spread each block's fixed costs (two barriers, the look-back's
+// L2 round trip) over 128 KB of input; 8192-row tiles ran at 0.52 of the copy rate, these at
+// 0.79 (600M rows, 30 % selected).  The tile is the block index: blocks are dispatched in index
+// order, so every tile a look-back waits on has been dispatched; each wait is still bounded and
+// reports TIMEOUT.
 #include <mutex>
 
 #include "common.cuh"
@@ -18,9 +21,11 @@ namespace sirius {
 namespace {
 
 constexpr int kFilterThreads = 256;
-constexpr int kFilterK = 8;                                  // 16-byte vectors per lane
-constexpr int kWarpRows = 32 * 4 * kFilterK;                 // 1024
-constexpr int kTileRows = kWarpRows * (kFilterThreads / 32);  // 8192
+constexpr int kFilterK = 32;                                 // 16-byte vectors per lane
+constexpr int kFilterPhase = 16;                             // vectors per load phase
+constexpr int kWarpRows = 32 * 4 * kFilterK;                 // 4096
+constexpr int kTileRows = kWarpRows * (kFilterThreads / 32);  // 32768 (offsets fit 16 bits)
+static_assert(kTileRows <= 65536, "tile offsets are 16-bit");
 constexpr uint64_t kFlagAgg = 1, kFlagPrefix = 2;
 // Bound of one look-back wait: 2^21 polls, the later ones 256 ns apart (about half a second).
 // A predecessor tile that is running publishes its count within microseconds, so only a
@@ -41,7 +46,10 @@ __device__ __forceinline__ void publish_count(uint64_t* status, int64_t tile, ui
 }
 
 // Exclusive prefix of this tile (its count already published): the sum of all earlier tiles'
-// selected counts.  Run by one whole warp; returns the same value in every lane.
+// selected counts.  Run by one whole warp, which reads the status words of the 32 tiles before
+// the current position and adds their counts back to the nearest published inclusive prefix
+// (only the words nearer than that prefix need to be ready); returns the same value in every
+// lane.
 __device__ uint64_t look_back_published(uint64_t* status, int64_t tile, uint64_t total, int32_t* err) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) return 0;
@@ -54,8 +62,10 @@ __device__ uint64_t look_back_published(uint64_t* status, int64_t tile, uint64_t
     int spins = 0;
     while (true) {
       w = (j >= 0) ? ld_relaxed_u64(&status[j]) : kFlagPrefix;
-      const bool not_ready = (w & 3) == 0;
-      if (!__any_sync(0xffffffffu, not_ready)) break;
+      // done when every word nearer than the nearest published prefix is ready
+      const unsigned nr = __ballot_sync(0xffffffffu, (w & 3) == 0);
+      const unsigned pr = __ballot_sync(0xffffffffu, (w & 3) == kFlagPrefix);
+      if (nr == 0 || (pr != 0 && (pr & (0u - pr)) < (nr & (0u - nr)))) break;
       if (++spins > kSpinLimit) {
         timed_out = true;
         break;
@@ -83,66 +93,57 @@ __device__ uint64_t look_back(uint64_t* status, int64_t tile, uint64_t total, in
 // never publishes, so the wait runs out and records SIRIUS_ERR_TIMEOUT in *err.
 __global__ void lookback_selftest_kernel(uint64_t* status, int32_t* err) { look_back(status, 1, 7, err); }
 
+// Three blocks per SM (64 KB of shared memory and up to 85 registers each).
 template <bool kVec>
-__global__ void __launch_bounds__(kFilterThreads)
+__global__ void __launch_bounds__(kFilterThreads, 3)
 filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_t lit,
                       uint32_t* __restrict__ out, int64_t* __restrict__ d_count,
                       DevHeader* hdr, uint64_t* status, int64_t num_tiles) {
-  __shared__ int64_t s_tile;
   __shared__ uint32_t s_warp_total[kFilterThreads / 32];
   __shared__ uint32_t s_warp_excl[kFilterThreads / 32];
   __shared__ uint32_t s_total;
   __shared__ uint64_t s_tile_excl;
-  __shared__ uint32_t s_ids[kTileRows];   // the tile's selected row ids, in row order
+  extern __shared__ uint16_t s_ids[];   // [kTileRows] the tile's selected rows (offsets in the tile), in row order
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd((unsigned long long*)&hdr->counter, 1ull);
-  __syncthreads();
-  const int64_t tile = s_tile;
+  const int64_t tile = blockIdx.x;
   const int64_t warp_row0 = tile * kTileRows + (int64_t)warp * kWarpRows;
 
-  // ---- load + evaluate: bits[k] holds the 4 predicate results of vector k of this lane
-  uint32_t bits[kFilterK];
+  // ---- load + evaluate: bits of vector k of this lane at 4k .. 4k+3 (two phases of loads)
+  uint32_t bits[kFilterK / 8] = {};  // vector k at bits[k / 8], bits 4 (k % 8) .. +3
   const bool full_tile = (tile + 1) * (int64_t)kTileRows <= n;
   if (kVec && full_tile) {
     const int4* p = reinterpret_cast<const int4*>(col + warp_row0);
-    int4 v[kFilterK];
 #pragma unroll
-    for (int k = 0; k < kFilterK; ++k) v[k] = __ldcs(p + lane + 32 * k);
+    for (int h = 0; h < kFilterK; h += kFilterPhase) {
+      int4 v[kFilterPhase];
 #pragma unroll
-    for (int k = 0; k < kFilterK; ++k)
-      bits[k] = (uint32_t)cmp_op(v[k].x, lit, op) | ((uint32_t)cmp_op(v[k].y, lit, op) << 1) |
-                ((uint32_t)cmp_op(v[k].z, lit, op) << 2) | ((uint32_t)cmp_op(v[k].w, lit, op) << 3);
+      for (int k = 0; k < kFilterPhase; ++k) v[k] = __ldcs(p + lane + 32 * (h + k));
+#pragma unroll
+      for (int k = 0; k < kFilterPhase; ++k)
+        bits[(h + k) / 8] |= ((uint32_t)cmp_op(v[k].x, lit, op) | ((uint32_t)cmp_op(v[k].y, lit, op) << 1) |
+                              ((uint32_t)cmp_op(v[k].z, lit, op) << 2) | ((uint32_t)cmp_op(v[k].w, lit, op) << 3))
+                             << (4 * ((h + k) % 8));
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < kFilterK; ++k) {
-      uint32_t b = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int64_t r = warp_row0 + 4 * (lane + 32 * k) + j;
-        if (r < n && cmp_op(col[r], lit, op)) b |= 1u << j;
+        if (r < n && cmp_op(col[r], lit, op)) bits[k / 8] |= 1u << (4 * (k % 8) + j);
       }
-      bits[k] = b;
     }
   }
 
-  // ---- warp-level ranks: ballots per (k, j), popcounts below this lane
+  // ---- warp total of selected rows
   const unsigned lt = lanemask_lt();
-  uint32_t before[kFilterK];  // selected items of this warp ordered before (k, lane, 0)
   uint32_t running = 0;
 #pragma unroll
-  for (int k = 0; k < kFilterK; ++k) {
-    uint32_t below = 0, tot = 0;
+  for (int i = 0; i < kFilterK / 8; ++i) running += __popc(bits[i]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const unsigned m = __ballot_sync(0xffffffffu, (bits[k] >> j) & 1u);
-      below += __popc(m & lt);
-      tot += __popc(m);
-    }
-    before[k] = running + below;
-    running += tot;
-  }
+  for (int o = 16; o > 0; o >>= 1) running += __shfl_xor_sync(0xffffffffu, running, o);
   if (lane == 0) s_warp_total[warp] = running;
   __syncthreads();
 
@@ -163,17 +164,25 @@ filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_
   }
   __syncthreads();
 
-  // ---- the selected row ids into shared memory in row order (tile-local positions)
-  const uint32_t wbase = s_warp_excl[warp];
+  // ---- the selected row ids into shared memory in row order (tile-local positions): per
+  // vector k the ballots rank this lane's rows among the warp's
+  uint32_t pos = s_warp_excl[warp];
 #pragma unroll
   for (int k = 0; k < kFilterK; ++k) {
-    uint32_t b = bits[k];
-    uint32_t pos = wbase + before[k];
-    const uint32_t row0 = (uint32_t)(warp_row0 + 4 * (lane + 32 * k));
+    const uint32_t b = (bits[k / 8] >> (4 * (k % 8))) & 15u;
+    const uint32_t off0 = (uint32_t)(warp * kWarpRows + 4 * (lane + 32 * k));
+    uint32_t m[4], below = 0, tot = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      if ((b >> j) & 1u) s_ids[pos++] = row0 + j;
+      m[j] = __ballot_sync(0xffffffffu, (b >> j) & 1u);
+      below += __popc(m[j] & lt);
+      tot += __popc(m[j]);
     }
+    uint32_t q = pos + below;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((b >> j) & 1u) s_ids[q++] = (uint16_t)(off0 + j);
+    pos += tot;
   }
   // ---- the tile's output offset (warp 0)
   const uint32_t total = s_total;
@@ -191,7 +200,8 @@ filter_compact_kernel(const int32_t* __restrict__ col, int64_t n, int op, int32_
 
   // ---- one contiguous run of ids out
   uint32_t* dst = out + s_tile_excl;
-  for (uint32_t i = threadIdx.x; i < total; i += kFilterThreads) dst[i] = s_ids[i];
+  const uint32_t tile_row0 = (uint32_t)(tile * kTileRows);
+  for (uint32_t i = threadIdx.x; i < total; i += kFilterThreads) dst[i] = tile_row0 + s_ids[i];
 }
 
 }  // namespace
@@ -208,11 +218,14 @@ sirius_status filter_launch(const int32_t* d_col, int64_t n, int32_t op, int32_t
   SIRIUS_CUDA_TRY(cudaMemsetAsync(hdr, 0, 256 + (size_t)tiles * 8, s));
   const bool vec = ((uintptr_t)d_col & 15) == 0;
   PhaseTimer pt(s, SIRIUS_PHASE_FILTER);
+  static std::atomic<uint64_t> smem_set[2] = {};  // per kernel: devices with the limit raised
+  SIRIUS_CUDA_TRY(ensure_smem_limit(filter_compact_kernel<true>, kTileRows * 2, smem_set[0]));
+  SIRIUS_CUDA_TRY(ensure_smem_limit(filter_compact_kernel<false>, kTileRows * 2, smem_set[1]));
   if (vec)
-    filter_compact_kernel<true><<<(unsigned)tiles, kFilterThreads, 0, s>>>(
+    filter_compact_kernel<true><<<(unsigned)tiles, kFilterThreads, kTileRows * 2, s>>>(
         d_col, n, op, literal, d_row_ids, d_count, hdr, status, tiles);
   else
-    filter_compact_kernel<false><<<(unsigned)tiles, kFilterThreads, 0, s>>>(
+    filter_compact_kernel<false><<<(unsigned)tiles, kFilterThreads, kTileRows * 2, s>>>(
         d_col, n, op, literal, d_row_ids, d_count, hdr, status, tiles);
   SIRIUS_LAUNCH_CHECK();
   return SIRIUS_OK;
@@ -264,7 +277,7 @@ extern "C" sirius_status sirius_filter(const int32_t* d_col, int64_t n, int32_t 
 // (a host callback or another latency-critical path where an allocation could block the
 // device or fail, or a process whose device memory is entirely owned by another allocator and
 // that passes only its own inputs and outputs).  Its look-back scratch (the 256-byte header and
-// one status word per 4096-row tile) lives in the file-scope device array below, which every
+// one status word per 32768-row tile) lives in the file-scope device array below, which every
 // GPU that loads this library holds until the process exits.
 namespace {
 constexpr int64_t kStaticFilterMaxRows = 1ll << 28;  // 268 435 456 rows

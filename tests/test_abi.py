@@ -50,7 +50,7 @@ def test_host_side_queries(lib):
     assert lib.sirius_join_table_bytes(10, 3) == 0
     assert lib.sirius_groupby_capacity(1000) >= 2000
     assert lib.sirius_filter_scratch_bytes(0) >= 256
-    assert lib.sirius_filter_scratch_bytes(10**9) >= 8 * (10**9 // 8192)   # a status word per 8192-row tile
+    assert lib.sirius_filter_scratch_bytes(10**9) >= 8 * (10**9 // 32768)   # a status word per 32768-row tile
 
 
 def test_invalid_arguments_rejected_before_any_device_work(lib):

@@ -32,7 +32,8 @@ def u32(t):
 
 
 # ------------------------------------------------------------------------- filter
-@pytest.mark.parametrize("n", [1, 5, 4095, 4096, 4097, 12289, 100_003, 3_000_001])
+@pytest.mark.parametrize("n", [1, 5, 4095, 4096, 4097, 12289, 32767, 32768, 32769, 65537, 98305, 100_003,
+                               1_048_577, 3_000_001, 40_000_003])
 def test_filter_sizes(S, n):
     col = np.random.default_rng(n).integers(0, 100, size=n).astype(np.int32)
     for t in (0, 37, 100):
@@ -55,6 +56,9 @@ def test_filter_empty_and_unaligned(S):
     d = dev(col)
     got = u32(S.sirius_filter(d[1:], "ge", 42))   # 4-byte offset: scalar path
     assert np.array_equal(got, O.filter_rows(col[1:], "ge", 42))
+    col = np.random.default_rng(4).integers(0, 100, size=1_000_003).astype(np.int32)
+    got = u32(S.sirius_filter(dev(col)[3:], "lt", 61))   # scalar path over 31 tiles and a ragged one
+    assert np.array_equal(got, O.filter_rows(col[3:], "lt", 61))
 
 
 def test_filter_async_count(S):
