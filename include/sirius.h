@@ -110,7 +110,7 @@ int32_t sirius_inject_alloc_failures(int32_t count);
  * input column and the outputs (d_row_ids with room for n ids; d_count / h_count as in
  * sirius_filter, same results).  The look-back scratch lives instead in one file-scope device
  * array of the library, sized for at most sirius_filter_static_max_rows() = 2^28 rows (about
- * 512 KB); every GPU that loads the library holds that array until the process exits.  Larger
+ * 64 KB: one word per 32768-row tile); every GPU that loads the library holds that array until the process exits.  Larger
  * n is rejected with SIRIUS_ERR_INVALID and a message.  The call allocates nothing: it clears
  * the part of the array it uses (stream-ordered) before its kernel.  The first call on each
  * device looks up the array's device address (with that device current) and caches it; make
