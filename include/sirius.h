@@ -350,7 +350,15 @@ typedef struct {
   int32_t join_mode;        /* 0 auto: one-column build keys that are unique and span a range
                                of at most 2m values are joined through a direct-address array
                                (decided on the device during the build); 1 hash table always */
-  int32_t reserved;
+  int32_t split_probe;      /* queries with one-column keys asking for MIN or MAX, aggregated with
+                               agg_mode 2 or 4: 0 auto, 1 one probe pass, 2 split pass -- the
+                               first 1/16 of the fact rows aggregate in full, then the smallest
+                               MAX and the largest MIN over the groups seen so far (with a bitmap
+                               of those among the first 2^17 group slots) let the other rows
+                               skip the MIN / MAX reductions they cannot change (direct-address
+                               join only; exact).  Auto: 2 when n >= 2^26, n >= 256 x the group
+                               slots (sirius_groupby_capacity(group_cap_hint) + 1), dpred is
+                               NULL and join_mode is 0; else 1 */
   /* dim-side predicate (predicate transfer, Sec. 3.4): NULL, or a dim column of m values; only
      the dim rows with dpred[j] <dop> dliteral take part in the join (a filter on the build
      side, so the probe pass finds no partner for the other rows' keys) */

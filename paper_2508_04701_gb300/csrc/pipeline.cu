@@ -259,7 +259,9 @@ __global__ void semi_build_kernel(SemiInput in, SemiView v) {
 
 // kFresh: the build ran earlier in the same launch (the single-launch kernel): its headers and
 // tables are read through L2 only.  Every thread of the block takes part.
-template <bool kWide, int kMode, bool kVec, bool kSemi, bool kFresh = false>
+// kBounded: the second phase of a split pass (one-column keys, hot-group cache or plain
+// reductions; a.bounds set).
+template <bool kWide, int kMode, bool kVec, bool kSemi, bool kFresh = false, bool kBounded = false>
 __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& sa) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   const int32_t dstatus = kFresh ? *(const volatile int32_t*)&a.dhdr->status : a.dhdr->status;
@@ -275,6 +277,18 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
   }
   const uint32_t slots = kMode == kAggSmem ? a.gslots : (kMode == kAggHot ? (uint32_t)kHotEntries : 0u);
   const SmemAggs T = smem_aggs(smem_raw, slots);
+  if constexpr (kBounded) {
+    // second phase of a split pass: the bounds into shared memory after the hot-group cache,
+    // the extremes decoded (the hot-group cache's barrier below, or this one, publishes them)
+    const uint4* src = reinterpret_cast<const uint4*>(a.bounds);
+    uint4* dst = reinterpret_cast<uint4*>(smem_raw + (kMode == kAggHot ? kHotSmemBytes : 0));
+    for (uint32_t i = threadIdx.x; i < kBoundsSmemBytes / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+      s_bound_floor = bound_decode(a.bounds->max_floor_enc);
+      s_bound_ceil = bound_decode(~a.bounds->min_ceil_inv);
+    }
+    if (kMode == kAggGlobal) __syncthreads();
+  }
   if (kMode == kAggSmem || kMode == kAggHot) {
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
       smem_identity(T, i);
@@ -290,7 +304,7 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
     if (L.direct)
       for (; q + stride < nq; q += 2 * stride) probe_quad_pair_direct<kMode, true>(a, T, L, q, q + stride);
   }
-  for (; q < nq; q += stride) probe_quad<kWide, kMode, kVec, kSemi, false, kFresh>(a, T, L, q, SLp);
+  for (; q < nq; q += stride) probe_quad<kWide, kMode, kVec, kSemi, false, kFresh, kBounded>(a, T, L, q, SLp);
   // ragged tail: the last n % 4 rows, one per thread of block 0
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < a.n - (nq << 2))
     probe_one<kWide, kMode, kSemi, kFresh>(a, T, L, (nq << 2) + threadIdx.x, SLp);
@@ -303,14 +317,55 @@ __device__ __forceinline__ void probe_body(const ProbeArgs& a, const SemiArgs& s
   }
 }
 
+// The extreme bounds after the first phase of a split probe pass: one thread per group slot
+// below kBoundSlots (a bit per slot that has joined rows, by ballot), the smallest MAX and the
+// largest MIN over those slots by block reductions and one atomicMin per block on their
+// encodings (set to all-ones before the launch).
+__global__ void __launch_bounds__(256) extreme_bounds_kernel(const Agg* __restrict__ tab, uint32_t gslots,
+                                                           ExtremeBounds* b) {
+  __shared__ unsigned long long s_floor, s_ceil;  // encoded MAX floor, complemented MIN ceiling
+  if (threadIdx.x == 0) {
+    s_floor = ~0ull;
+    s_ceil = ~0ull;
+  }
+  __syncthreads();
+  const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;  // < kBoundSlots (grid covers it exactly)
+  unsigned long long fl = ~0ull, ce = ~0ull;
+  bool seen = false;
+  if (slot < gslots) {
+    const Agg g = tab[slot];
+    seen = g.count != 0;
+    if (seen) {
+      fl = bound_encode(g.max);
+      ce = ~bound_encode(g.min);
+    }
+  }
+  const unsigned bits = __ballot_sync(0xffffffffu, seen);
+  if ((threadIdx.x & 31) == 0) b->seen[slot >> 5] = bits;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long f2 = __shfl_xor_sync(0xffffffffu, fl, o), c2 = __shfl_xor_sync(0xffffffffu, ce, o);
+    fl = f2 < fl ? f2 : fl;
+    ce = c2 < ce ? c2 : ce;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&s_floor, fl);
+    atomicMin(&s_ceil, ce);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMin(&b->max_floor_enc, s_floor);
+    atomicMin(&b->min_ceil_inv, s_ceil);
+  }
+}
+
 // The fused probe pass: filter, probe and aggregate every fact row.  Held to 64 registers, so
 // that two 512-thread blocks share an SM: the pass needs the resident warps to cover its
 // memory latency (a 76-register build of the two-column-key variant ran one block per SM and
 // took 15.0 ms instead of 8.4 on the 600M-row query).
-template <bool kWide, int kMode, bool kVec, bool kSemi>
+template <bool kWide, int kMode, bool kVec, bool kSemi, bool kBounded = false>
 __global__ void __launch_bounds__(512, 2)
 probe_kernel(ProbeArgs a, SemiArgs sa) {
-  probe_body<kWide, kMode, kVec, kSemi>(a, sa);
+  probe_body<kWide, kMode, kVec, kSemi, false, kBounded>(a, sa);
 }
 
 // The same pass for a star query, held to 64 registers so that two 512-thread blocks share an
@@ -455,12 +510,12 @@ int occupancy_blocks(K kernel, int threads, size_t smem) {
   return b > 0 ? b : 1;
 }
 
-template <bool kWide, int kMode, bool kVec, bool kSemi>
+template <bool kWide, int kMode, bool kVec, bool kSemi, bool kBounded = false>
 sirius_status launch_probe(const ProbeArgs& a, const SemiArgs& sa, int threads, int blocks_per_sm, size_t smem,
                            cudaStream_t s) {
   void (*k)(ProbeArgs, SemiArgs);
   if constexpr (kSemi) k = probe_star_kernel<kWide, kMode, kVec>;
-  else k = probe_kernel<kWide, kMode, kVec, false>;
+  else k = probe_kernel<kWide, kMode, kVec, false, kBounded>;
   if (kMode == kAggSmem || kMode == kAggHot) {
     static std::atomic<uint64_t> smem_set{0};  // devices with the limit raised
     SIRIUS_CUDA_TRY(ensure_smem_limit(k, 200 * 1024, smem_set));
@@ -584,6 +639,16 @@ sirius_status dispatch_probe(const ProbeArgs& a, const SemiArgs& sa, int mode, b
   if (mode == kAggSmem)
     return vec ? launch_probe<kWide, kAggSmem, true, kSemi>(a, sa, threads, bps, smem, s)
                : launch_probe<kWide, kAggSmem, false, kSemi>(a, sa, threads, bps, smem, s);
+  if constexpr (!kWide && !kSemi) {
+    if (a.bounds) {  // second phase of a split pass: the bounds' copy follows the hot-group cache
+      constexpr size_t bb = kBoundsSmemBytes;
+      if (mode == kAggHot)
+        return vec ? launch_probe<false, kAggHot, true, false, true>(a, sa, threads, bps, kHotSmemBytes + bb, s)
+                   : launch_probe<false, kAggHot, false, false, true>(a, sa, threads, bps, kHotSmemBytes + bb, s);
+      return vec ? launch_probe<false, kAggGlobal, true, false, true>(a, sa, threads, bps, bb, s)
+                 : launch_probe<false, kAggGlobal, false, false, true>(a, sa, threads, bps, bb, s);
+    }
+  }
   if (mode == kAggHot)
     return vec ? launch_probe<kWide, kAggHot, true, kSemi>(a, sa, threads, bps, kHotSmemBytes, s)
                : launch_probe<kWide, kAggHot, false, kSemi>(a, sa, threads, bps, kHotSmemBytes, s);
@@ -720,6 +785,10 @@ RunLayout run_layout(int64_t gcap, int64_t n, int agg_mode) {
     R.off_prefix = align_up(R.off_tval + tuples * 8, 256);
     end = align_up(R.off_prefix + (size_t)R.ntiles * (R.parts + 1) * 4, 256);
   }
+  if (R.mode == kAggHot || R.mode == kAggGlobal) {
+    R.off_bounds = end;
+    end = align_up(end + sizeof(ExtremeBounds), 256);
+  }
   R.total = end;
   return R;
 }
@@ -758,6 +827,7 @@ RunView run_view(const RunLayout& R, char* base) {
   r.tgs = R.mode == kAggPart ? (uint32_t*)(base + R.off_tgs) : nullptr;
   r.tval = R.mode == kAggPart ? (int64_t*)(base + R.off_tval) : nullptr;
   r.prefix = R.mode == kAggPart ? (int32_t*)(base + R.off_prefix) : nullptr;
+  r.bounds = R.off_bounds ? (ExtremeBounds*)(base + R.off_bounds) : nullptr;
   return r;
 }
 
@@ -781,6 +851,7 @@ sirius_status validate_fact(const sirius_pipeline_desc* q) {
   SIRIUS_REQUIRE(q->op >= SIRIUS_LT && q->op <= SIRIUS_NE, "pipeline: bad comparison %d", q->op);
   SIRIUS_REQUIRE(q->aggs <= SIRIUS_AGG_ALL, "pipeline: bad aggregate mask");
   SIRIUS_REQUIRE(q->agg_mode >= 0 && q->agg_mode <= kAggRouted, "pipeline: bad agg_mode %d", q->agg_mode);
+  SIRIUS_REQUIRE(q->split_probe >= 0 && q->split_probe <= 2, "pipeline: bad split_probe %d", q->split_probe);
   SIRIUS_REQUIRE(q->block_threads == 0 || (q->block_threads % 32 == 0 && q->block_threads >= 64 &&
                                            q->block_threads <= 512),
                  "pipeline: block_threads must be a multiple of 32 in [64, 512]");
@@ -917,6 +988,28 @@ static ProbeArgs probe_args(const sirius_pipeline_desc* q, const DimView& d, con
 }
 
 // 16-byte loads of the probe columns need every one 16-byte aligned.
+// The split probe pass, for queries with one-column keys that ask for MIN or MAX, aggregated
+// with the hot-group cache or plain reductions (not the star kernel: its probe keeps one pass):
+// when the descriptor's split_probe asks for it, or by default for large queries with many rows
+// per group slot and no dim-side predicate.  The first 1/kSplitFirstDiv of the rows give every
+// frequent group enough rows that the bounds rule out most later MIN / MAX reductions.  Only the
+// direct-array join takes the bounds in the second phase; a hash-table join runs it with plain
+// reductions.
+constexpr int64_t kSplitMinRows = 1ll << 26;
+constexpr int64_t kSplitRowsPerSlot = 256;
+constexpr int64_t kSplitFirstDiv = 16;
+static bool split_applies(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int mode,
+                          int64_t gslots) {
+  if (q->split_probe == 1 || r.bounds == nullptr || d.key_width != 4 || (mode != kAggHot && mode != kAggGlobal) ||
+      (q->aggs & (SIRIUS_AGG_MIN | SIRIUS_AGG_MAX)) == 0 || q->n < 64)
+    return false;
+  if (q->split_probe == 2) return true;
+  // auto: large queries with many rows per group slot, whose pass is bound by the reductions (a
+  // dim-side predicate leaves few joined rows: the column stream bounds those passes; a forced
+  // hash-table join takes no bounds)
+  return q->n >= kSplitMinRows && q->n >= kSplitRowsPerSlot * gslots && q->dpred == nullptr && q->join_mode == 0;
+}
+
 static bool vec_columns(const sirius_pipeline_desc* q) {
   return ((uintptr_t)q->pred & 15) == 0 && ((uintptr_t)q->fk & 15) == 0 &&
          (!q->fk_hi || ((uintptr_t)q->fk_hi & 15) == 0);
@@ -952,8 +1045,29 @@ sirius_status run_probe(const sirius_pipeline_desc* q, const DimView& d, const R
   if (nsemi > 0)
     return d.key_width == 8 ? dispatch_probe<true, true>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s)
                             : dispatch_probe<false, true>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s);
-  return d.key_width == 8 ? dispatch_probe<true, false>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s)
-                          : dispatch_probe<false, false>(a, sa, mode, vec, threads, q->blocks_per_sm, smem, s);
+  auto probe = [&](const ProbeArgs& x) {
+    return d.key_width == 8 ? dispatch_probe<true, false>(x, sa, mode, vec, threads, q->blocks_per_sm, smem, s)
+                            : dispatch_probe<false, false>(x, sa, mode, vec, threads, q->blocks_per_sm, smem, s);
+  };
+  if (!split_applies(q, d, r, mode, gslots)) return probe(a);
+  // Split pass: the first rows aggregate in full; then the extreme bounds over the group table
+  // so far; then the other rows skip the MIN / MAX reductions those bounds rule out.
+  const int64_t n0 = ((q->n / kSplitFirstDiv) >> 2) << 2;  // a multiple of 4: column alignment kept
+  ProbeArgs a1 = a;
+  a1.n = n0;
+  sirius_status st = probe(a1);
+  if (st != SIRIUS_OK) return st;
+  SIRIUS_CUDA_TRY(cudaMemsetAsync(r.bounds, 0xFF, 2 * sizeof(unsigned long long), s));
+  extreme_bounds_kernel<<<kBoundSlots / 256, 256, 0, s>>>(r.aggs, (uint32_t)gslots, r.bounds);
+  SIRIUS_LAUNCH_CHECK();
+  ProbeArgs a2 = a;
+  a2.fk = q->fk + n0;
+  a2.fk_hi = q->fk_hi ? q->fk_hi + n0 : nullptr;
+  a2.pred = q->pred + n0;
+  a2.val = q->val + n0;
+  a2.n = q->n - n0;
+  a2.bounds = r.bounds;
+  return probe(a2);
 }
 
 sirius_status run_finalize(const sirius_pipeline_desc* q, const DimView& d, const RunView& r, int64_t gslots,

@@ -54,6 +54,7 @@ struct RunLayout {
   int parts = 0;          // partitioned mode: partitions and pass-1 tiles
   int64_t ntiles = 0;
   size_t off_aggs = 256, off_tgs = 0, off_tval = 0, off_prefix = 0, total = 0;
+  size_t off_bounds = 0;  // extreme bounds of a split probe pass (0: none)
   // routed mode: blocks of the launch the exchange is sized for, owners (2^logP), slots per
   // owner, run capacity; exchange values, local slots, run lengths
   int route_blocks = 0, route_logP = 0;
@@ -75,6 +76,8 @@ struct DimView {
   int key_width;
 };
 
+struct ExtremeBounds;
+
 struct RunView {
   PipeHeader* phdr;
   Agg* aggs;
@@ -89,6 +92,7 @@ struct RunView {
   uint32_t* rfill;
   int route_blocks, route_logP;
   uint32_t route_R, route_C;
+  ExtremeBounds* bounds;  // nullptr: the run has no room for a split probe pass
 };
 
 struct PipeOut {
@@ -138,6 +142,29 @@ struct SemiView {
 };
 
 // Everything the probe pass reads for one query.
+// Extreme bounds for the second phase of a split probe pass (taken after the first phase over
+// the group table): every slot whose bit is set had joined rows, its MAX at least max_floor and
+// its MIN at most min_ceil -- and both only move outwards, so a later row of such a slot whose
+// value is below max_floor cannot change the slot's MAX, nor one above min_ceil its MIN.
+constexpr uint32_t kBoundSlots = 1u << 17;          // group slots the bitmap covers
+constexpr uint32_t kBoundWords = kBoundSlots / 32;  // 16 KB
+struct __align__(16) ExtremeBounds {
+  // both taken with atomicMin from all-ones (one memset clears them): the order-preserving
+  // encoding (value ^ sign bit) of max_floor, and its complement for min_ceil
+  unsigned long long max_floor_enc;
+  unsigned long long min_ceil_inv;
+  unsigned long long pad[2];
+  uint32_t seen[kBoundWords];    // bit s: slot s had joined rows when the bounds were taken
+};
+__host__ __device__ __forceinline__ unsigned long long bound_encode(long long v) {
+  return (unsigned long long)v ^ 0x8000000000000000ull;
+}
+__host__ __device__ __forceinline__ long long bound_decode(unsigned long long e) {
+  return (long long)(e ^ 0x8000000000000000ull);
+}
+// The decoded bounds of the running block (set at the start of a second-phase launch).
+__shared__ long long s_bound_floor, s_bound_ceil;
+
 struct ProbeArgs {
   const int32_t* fk;
   const int32_t* fk_hi;
@@ -156,6 +183,7 @@ struct ProbeArgs {
   uint32_t gslots;
   const uint64_t* bloom;  // nullptr: no Bloom filter
   uint32_t bloom_mask;
+  const ExtremeBounds* bounds = nullptr;  // second phase of a split probe pass (hot / global modes)
 };
 
 // The semi-join dims of a star query: a kernel parameter of its own, read only by the kSemi
@@ -297,10 +325,28 @@ constexpr int kHotBits = 11;
 constexpr int kHotEntries = 1 << kHotBits;
 constexpr size_t kHotSmemBytes = smem_aggs_bytes(kHotEntries, true);
 
+// The global reductions of one joined row in the second phase of a split probe pass: MIN and
+// MAX are skipped where the bounds show that the value cannot move them.
+constexpr size_t kBoundsSmemBytes = sizeof(ExtremeBounds);
+template <int kMode>
+__device__ __forceinline__ void agg_update_global_bounded(const ProbeArgs& a, uint32_t gs, int64_t v) {
+  uint32_t aggs = a.aggs;
+  // the bounds' copy in shared memory follows the hot-group cache; the bitmap and the decoded
+  // extremes are read where used (no registers held for them)
+  extern __shared__ __align__(32) unsigned char probe_dyn_smem[];
+  const volatile uint32_t* seen = reinterpret_cast<const volatile ExtremeBounds*>(
+                                      probe_dyn_smem + (kMode == kAggHot ? kHotSmemBytes : 0))->seen;
+  if (gs < kBoundSlots && ((seen[gs >> 5] >> (gs & 31)) & 1u)) {
+    if (v < *(volatile long long*)&s_bound_floor) aggs &= ~(uint32_t)SIRIUS_AGG_MAX;
+    if (v > *(volatile long long*)&s_bound_ceil) aggs &= ~(uint32_t)SIRIUS_AGG_MIN;
+  }
+  agg_update_global(&a.tab[gs], v, aggs);
+}
+
 // kKeep: the global reductions carry an L2 evict_last hint (measured faster for star queries,
 // whose filter structures and aggregates compete with the streamed columns for L2; slower for
 // the others, which therefore go without it).
-template <int kMode, bool kKeep = false>
+template <int kMode, bool kKeep = false, bool kBounded = false>
 __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T, uint32_t gs, int64_t v) {
   if (kMode == kAggSmem) {
     agg_update_smem(T, gs, v, a.aggs);
@@ -313,9 +359,12 @@ __device__ __forceinline__ void aggregate(const ProbeArgs& a, const SmemAggs& T,
     }
     if (t == gs) agg_update_smem(T, e, v, a.aggs);
     else if (kKeep) agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
+    else if (kBounded) agg_update_global_bounded<kAggHot>(a, gs, v);
     else agg_update_global(&a.tab[gs], v, a.aggs);
   } else if (kKeep) {
     agg_update_global_keep(&a.tab[gs], v, a.aggs, l2_keep_policy());
+  } else if (kBounded && kMode == kAggGlobal) {
+    agg_update_global_bounded<kAggGlobal>(a, gs, v);
   } else {
     agg_update_global(&a.tab[gs], v, a.aggs);
   }
@@ -417,9 +466,25 @@ __device__ __forceinline__ void probe_rows_emit(const ProbeArgs& a, const Lookup
 
 // The same, aggregating every match into the group table (kMode: where the aggregates live;
 // kKeep: L2 keep hints on the direct-array reads and the reductions).
-template <bool kWide, int kMode, bool kFresh = false, bool kKeep = false>
+// kBounded (one-column keys): the direct-array join aggregates behind the extreme bounds of a
+// split pass; the hash-table walk keeps the plain reductions.
+template <bool kWide, int kMode, bool kFresh = false, bool kKeep = false, bool kBounded = false>
 __device__ __forceinline__ void probe_rows(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, uint32_t bits,
                                            const uint64_t (&key)[4], const int64_t (&v)[4]) {
+  if constexpr (kBounded && !kWide) {
+    if (L.direct) {
+      uint32_t gs[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t k = (uint32_t)key[r] - (uint32_t)L.kmin;
+        gs[r] = (((bits >> r) & 1u) && k < L.range) ? __ldg(a.dslot + k) : kEmpty32;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (gs[r] != kEmpty32) aggregate<kMode, false, true>(a, T, gs[r], v[r]);
+      return;
+    }
+  }
   probe_rows_emit<kWide, kFresh, 4, kKeep>(a, L, bits, key, v,
                                            [&](int, uint32_t gs, int64_t val) { aggregate<kMode, kKeep>(a, T, gs, val); });
 }
@@ -523,7 +588,8 @@ __device__ __forceinline__ uint32_t semi_filter_vec(const SemiLookups& SL, int64
 // before any of them is used -- three column reads in flight per thread instead of one after
 // another -- at the cost of reading the values of unselected rows (a quad's values are one
 // 32-byte sector, needed whenever any of its rows is selected).
-template <bool kWide, int kMode, bool kVec, bool kSemi = false, bool kPreload = false, bool kFresh = false>
+template <bool kWide, int kMode, bool kVec, bool kSemi = false, bool kPreload = false, bool kFresh = false,
+          bool kBounded = false>
 __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T, const Lookup& L, int64_t q,
                                            const SemiLookups* SLp = nullptr) {
   const int64_t row0 = q << 2;
@@ -547,7 +613,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
     key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? vv[r] : 0;
-    probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, bits, key, v);
+    probe_rows<kWide, kMode, kFresh, kSemi, kBounded>(a, T, L, bits, key, v);
     return;
   }
   if (kVec) {
@@ -568,7 +634,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
       key[3] = kWide ? pack_key64(h4.w, k4.w) : (uint64_t)(uint32_t)k4.w;
 #pragma unroll
       for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-      probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, bits, key, v);
+      probe_rows<kWide, kMode, kFresh, kSemi, kBounded>(a, T, L, bits, key, v);
       return;
     }
     if (!bits) return;
@@ -597,7 +663,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = ((bits >> r) & 1u) ? __ldcs(a.val + row0 + r) : 0;
-  probe_rows<kWide, kMode, kFresh, kSemi>(a, T, L, bits, key, v);
+  probe_rows<kWide, kMode, kFresh, kSemi, kBounded>(a, T, L, bits, key, v);
 }
 
 // Two quads (qa, qb, both below n/4; 16-byte loads; one-column keys joined through the direct

@@ -27,6 +27,7 @@ AGG_MODES = {"auto": 0, "smem": 1, "global": 2, "part": 3, "hot": 4, "routed": 5
 PROBE_VARIANTS = {"auto": 0, "direct": 1, "staged": 2, "single": 3}
 BLOOM_MODES = {"auto": 0, "off": 1, "on": 2}
 JOIN_MODES = {"auto": 0, "hash": 1}
+SPLIT_MODES = {"auto": 0, "off": 1, "on": 2}
 
 
 class SiriusError(RuntimeError):
@@ -54,7 +55,7 @@ class PipelineDesc(ctypes.Structure):
                 ("agg_mode", ctypes.c_int32), ("group_cap_hint", ctypes.c_int64),
                 ("load_factor", ctypes.c_float), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("probe_variant", ctypes.c_int32),
-                ("join_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("join_mode", ctypes.c_int32), ("split_probe", ctypes.c_int32),
                 ("dpred", ctypes.c_void_p), ("dop", ctypes.c_int32), ("dliteral", ctypes.c_int32),
                 ("bloom", ctypes.c_int32), ("nsemi", ctypes.c_int32),
                 ("semi", Semijoin * MAX_SEMIJOINS)]
@@ -476,7 +477,7 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
               load_factor: float = 0.0, agg_mode="auto", block_threads: int = 0,
               blocks_per_sm: int = 0, host: bool = False, probe_variant="auto",
               join_mode="auto", dim_op=None, dim_literal: int = 0, bloom="auto",
-              semi=None) -> PipelineDesc:
+              semi=None, split_probe="auto") -> PipelineDesc:
     """A pipeline descriptor over device columns (host=True: over host columns, for
     sirius_run_pipeline_host).  fact: fk, fk_hi?, pred, val; dim: pk, pk_hi?, grp, flag?, and
     dattr when dim_op is given (the dim-side predicate dattr <dim_op> dim_literal).
@@ -491,7 +492,8 @@ def make_desc(fact: Dict[str, torch.Tensor], dim: Dict[str, torch.Tensor], op="l
         AGG_MODES[agg_mode] if isinstance(agg_mode, str) else int(agg_mode), int(group_cap_hint),
         float(load_factor), int(block_threads), int(blocks_per_sm),
         PROBE_VARIANTS[probe_variant] if isinstance(probe_variant, str) else int(probe_variant),
-        JOIN_MODES[join_mode] if isinstance(join_mode, str) else int(join_mode), 0,
+        JOIN_MODES[join_mode] if isinstance(join_mode, str) else int(join_mode),
+        SPLIT_MODES[split_probe] if isinstance(split_probe, str) else int(split_probe),
         g(dim, "dattr") if dim_op is not None else None,
         (OPS[dim_op] if isinstance(dim_op, str) else int(dim_op)) if dim_op is not None else 0,
         int(dim_literal), BLOOM_MODES[bloom] if isinstance(bloom, str) else int(bloom), 0)

@@ -78,6 +78,10 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     d.op = 0
     d.load_factor = 0.99
     assert lib.sirius_run_pipeline(ctypes.byref(d), ctypes.byref(r), None, 0, None) == S.ERR_INVALID
+    d.load_factor = 0
+    d.split_probe = 3
+    assert lib.sirius_run_pipeline(ctypes.byref(d), ctypes.byref(r), None, 0, None) == S.ERR_INVALID
+    assert "split_probe" in S.last_error()
 
 
 def test_scratch_size_query_grows_with_inputs(lib):
