@@ -416,7 +416,7 @@ extern "C" size_t sirius_pipeline_batch_scratch_bytes(const sirius_pipeline_desc
       off += L.total;
       gcap = L.gcap;
     }
-    off += run_layout(gcap).total;
+    off += run_layout(gcap, 0, kAggGlobal, false).total;
   }
   return off;
 }
@@ -583,7 +583,7 @@ extern "C" sirius_status sirius_batch_plan_run(sirius_batch_plan p, const sirius
       dbase = sc.base + off;
       off += L.total;
     }
-    const RunLayout R = run_layout(L.gcap);
+    const RunLayout R = run_layout(L.gcap, 0, kAggGlobal, false);
     char* rbase = sc.base + off;
     off += R.total;
     b.d = dim_view(L, dbase);

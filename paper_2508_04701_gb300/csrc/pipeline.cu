@@ -758,7 +758,7 @@ DimLayout dim_layout_of_index(const sirius_dim_index* idx) {
   return L;
 }
 
-RunLayout run_layout(int64_t gcap, int64_t n, int agg_mode) {
+RunLayout run_layout(int64_t gcap, int64_t n, int agg_mode, bool bounds) {
   RunLayout R;
   R.gslots = gcap + 1;
   R.mode = choose_mode(agg_mode, R.gslots, n);
@@ -785,7 +785,7 @@ RunLayout run_layout(int64_t gcap, int64_t n, int agg_mode) {
     R.off_prefix = align_up(R.off_tval + tuples * 8, 256);
     end = align_up(R.off_prefix + (size_t)R.ntiles * (R.parts + 1) * 4, 256);
   }
-  if (R.mode == kAggHot || R.mode == kAggGlobal) {
+  if (bounds && (R.mode == kAggHot || R.mode == kAggGlobal)) {
     R.off_bounds = end;
     end = align_up(end + sizeof(ExtremeBounds), 256);
   }

@@ -856,7 +856,9 @@ DimLayout dim_layout(int64_t m, bool wide, int64_t group_cap_hint, float load_fa
 DimLayout dim_layout_for(const sirius_pipeline_desc* q);
 DimLayout dim_layout_of_index(const sirius_dim_index* idx);
 // n: fact rows of the run (sizes the partitioned-mode buffers); agg_mode as in the descriptor.
-RunLayout run_layout(int64_t gcap, int64_t n = 0, int agg_mode = kAggGlobal);
+// bounds: room for the extreme bounds of a split probe pass (hot-group or global modes; the
+// batched calls, which never split, leave it out)
+RunLayout run_layout(int64_t gcap, int64_t n = 0, int agg_mode = kAggGlobal, bool bounds = true);
 DimView dim_view(const DimLayout& L, char* base);
 RunView run_view(const RunLayout& R, char* base);
 sirius_status validate_dim(const sirius_pipeline_desc* q);
