@@ -162,11 +162,20 @@ group_global_kernel(const void* __restrict__ keys_in, int key_width, const int64
 // 48 MB window of the table that stays in L2 instead of fetching and writing back random DRAM
 // sectors; every pass reads the keys, and a value only where its quad has a row in the window.
 constexpr uint64_t kPassSlots = (48ull << 20) / sizeof(Agg);
+// Split pass of the direct-slot group-by: for inputs with many rows per group slot that ask for
+// MIN or MAX and fit one window (the same technique as the fused probe's split pass).
+constexpr int64_t kGroupSplitMinRows = 1ll << 24;
+constexpr int64_t kGroupSplitRowsPerSlot = 256;
 
-template <int kKeyWidth, bool kVec>
+//
+// kBounded: the second phase of a split pass (one window covers every slot; `bounds` set):
+// the rows skip the MIN / MAX reductions that the extreme bounds taken after the first phase
+// rule out, as in the fused probe's split pass.
+template <int kKeyWidth, bool kVec, bool kBounded = false>
 __global__ void __launch_bounds__(512)
 group_direct_kernel(const void* __restrict__ keys_in, const int64_t* __restrict__ vals, int64_t n, uint32_t aggs,
-                    Agg* tab, const GroupHeader* hdr, unsigned long long limit, int pass) {
+                    Agg* tab, const GroupHeader* hdr, unsigned long long limit, int pass,
+                    const ExtremeBounds* bounds) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   const KeyRange kr = key_range(hdr, n, limit);
   if (!kr.direct) return;  // hashed keys: group_global_kernel
@@ -177,7 +186,19 @@ group_direct_kernel(const void* __restrict__ keys_in, const int64_t* __restrict_
   ProbeArgs a{};
   a.tab = tab;
   a.aggs = aggs;
+  a.bounds = bounds;
   const SmemAggs T = smem_aggs(smem_raw, kHotEntries);
+  if constexpr (kBounded) {
+    // the bounds into shared memory after the hot-group cache, the extremes decoded (published
+    // by the barrier below)
+    const uint4* src = reinterpret_cast<const uint4*>(bounds);
+    uint4* dst = reinterpret_cast<uint4*>(smem_raw + kHotSmemBytes);
+    for (uint32_t i = threadIdx.x; i < kBoundsSmemBytes / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+      s_bound_floor = bound_decode(bounds->max_floor_enc);
+      s_bound_ceil = bound_decode(~bounds->min_ceil_inv);
+    }
+  }
   for (uint32_t i = threadIdx.x; i < (uint32_t)kHotEntries; i += blockDim.x) {
     smem_identity(T, i);
     T.tag[i] = kEmpty32;
@@ -214,7 +235,7 @@ group_direct_kernel(const void* __restrict__ keys_in, const int64_t* __restrict_
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if ((in >> r) & 1u) aggregate<kAggHot>(a, T, (uint32_t)(uint64_t)(k[r] - kr.kmin), v[r]);
+      if ((in >> r) & 1u) aggregate<kAggHot, false, kBounded>(a, T, (uint32_t)(uint64_t)(k[r] - kr.kmin), v[r]);
   }
   if (blockIdx.x == 0 && (int64_t)threadIdx.x < n - (nq << 2)) {
     const int64_t i = (nq << 2) + threadIdx.x;
@@ -326,7 +347,8 @@ __global__ void copy_groups_kernel(const GroupHeader* hdr, int64_t* d_groups) {
 
 size_t groupby_scratch_bytes(int64_t hint) {
   const int64_t cap = group_capacity_for(hint);
-  return 256 + align_up((size_t)(cap + 1) * 8, 256) + (size_t)(cap + 1) * sizeof(Agg) + 256;
+  return 256 + align_up((size_t)(cap + 1) * 8, 256) + align_up((size_t)(cap + 1) * sizeof(Agg), 256) +
+         align_up(sizeof(ExtremeBounds), 256) + 256;
 }
 
 }  // namespace sirius
@@ -357,6 +379,7 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
   GroupHeader* hdr = (GroupHeader*)sc.take(256);
   int64_t* keys = (int64_t*)sc.take((size_t)(cap + 1) * 8);
   Agg* tab = (Agg*)sc.take((size_t)(cap + 1) * sizeof(Agg));
+  ExtremeBounds* bounds = (ExtremeBounds*)sc.take(sizeof(ExtremeBounds));
   const unsigned long long limit = group_limit_for(cap);
   SIRIUS_CUDA_TRY(cudaMemsetAsync(hdr, 0, 256, s));
   if (n > 0) {
@@ -390,9 +413,31 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
       // passes over windows of the direct slots (the range is known on the device only: a pass
       // whose window starts past it returns at once)
       const int passes = (int)((group_limit_for(cap) + kPassSlots - 1) / kPassSlots);
-      for (int p = 0; p < passes; ++p) {
-        kd<<<(unsigned)gd, 512, kHotSmemBytes, s>>>(d_keys, d_vals, n, aggs, tab, hdr, limit, p);
+      if (passes == 1 && (aggs & (SIRIUS_AGG_MIN | SIRIUS_AGG_MAX)) && n >= kGroupSplitMinRows &&
+          n >= kGroupSplitRowsPerSlot * (cap + 1)) {
+        // split pass: the first 1/16 of the rows in full, the extreme bounds, then the rest
+        // behind them (one block fewer per SM: the bounds' copy follows each 64 KB cache)
+        const int64_t n0 = ((n / 16) >> 2) << 2;
+        const size_t kw = (size_t)key_width;
+        kd<<<(unsigned)gd, 512, kHotSmemBytes, s>>>(d_keys, d_vals, n0, aggs, tab, hdr, limit, 0, nullptr);
         SIRIUS_LAUNCH_CHECK();
+        SIRIUS_CUDA_TRY(cudaMemsetAsync(bounds, 0xFF, 2 * sizeof(unsigned long long), s));
+        extreme_bounds_kernel<<<kBoundSlots / 256, 256, 0, s>>>(tab, (uint32_t)(cap + 1), bounds);
+        SIRIUS_LAUNCH_CHECK();
+        auto kb = key_width == 4 ? (vec ? group_direct_kernel<4, true, true> : group_direct_kernel<4, false, true>)
+                                 : (vec ? group_direct_kernel<8, true, true> : group_direct_kernel<8, false, true>);
+        const size_t smem = kHotSmemBytes + kBoundsSmemBytes;
+        SIRIUS_CUDA_TRY(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t most2 = (int64_t)sm_count() * 2;
+        const int64_t gd2 = gd > most2 ? most2 : gd;
+        kb<<<(unsigned)gd2, 512, smem, s>>>(static_cast<const char*>(d_keys) + n0 * kw, d_vals + n0, n - n0, aggs,
+                                           tab, hdr, limit, 0, bounds);
+        SIRIUS_LAUNCH_CHECK();
+      } else {
+        for (int p = 0; p < passes; ++p) {
+          kd<<<(unsigned)gd, 512, kHotSmemBytes, s>>>(d_keys, d_vals, n, aggs, tab, hdr, limit, p, nullptr);
+          SIRIUS_LAUNCH_CHECK();
+        }
       }
       group_global_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(d_keys, key_width, d_vals, n, aggs,
                                                                      keys, tab, (uint32_t)cap, hdr, limit);

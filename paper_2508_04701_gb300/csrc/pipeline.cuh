@@ -343,6 +343,47 @@ __device__ __forceinline__ void agg_update_global_bounded(const ProbeArgs& a, ui
   agg_update_global(&a.tab[gs], v, aggs);
 }
 
+// The extreme bounds after the first phase of a split pass (the fused probe, the group-by): one thread per group slot
+// below kBoundSlots (a bit per slot that has joined rows, by ballot), the smallest MAX and the
+// largest MIN over those slots by block reductions and one atomicMin per block on their
+// encodings (set to all-ones before the launch).
+static __global__ void __launch_bounds__(256) extreme_bounds_kernel(const Agg* __restrict__ tab, uint32_t gslots,
+                                                           ExtremeBounds* b) {
+  __shared__ unsigned long long s_floor, s_ceil;  // encoded MAX floor, complemented MIN ceiling
+  if (threadIdx.x == 0) {
+    s_floor = ~0ull;
+    s_ceil = ~0ull;
+  }
+  __syncthreads();
+  const uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x;  // < kBoundSlots (grid covers it exactly)
+  unsigned long long fl = ~0ull, ce = ~0ull;
+  bool seen = false;
+  if (slot < gslots) {
+    const Agg g = tab[slot];
+    seen = g.count != 0;
+    if (seen) {
+      fl = bound_encode(g.max);
+      ce = ~bound_encode(g.min);
+    }
+  }
+  const unsigned bits = __ballot_sync(0xffffffffu, seen);
+  if ((threadIdx.x & 31) == 0) b->seen[slot >> 5] = bits;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long f2 = __shfl_xor_sync(0xffffffffu, fl, o), c2 = __shfl_xor_sync(0xffffffffu, ce, o);
+    fl = f2 < fl ? f2 : fl;
+    ce = c2 < ce ? c2 : ce;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&s_floor, fl);
+    atomicMin(&s_ceil, ce);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMin(&b->max_floor_enc, s_floor);
+    atomicMin(&b->min_ceil_inv, s_ceil);
+  }
+}
+
 // kKeep: the global reductions carry an L2 evict_last hint (measured faster for star queries,
 // whose filter structures and aggregates compete with the streamed columns for L2; slower for
 // the others, which therefore go without it).

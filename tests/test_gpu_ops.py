@@ -262,6 +262,47 @@ def test_groupby_direct_slots_skewed(S):
     check_groupby(S, keys, vals, 1_000_000)
 
 
+SPLIT_N = 20_000_003   # at least 2^24 rows and 256 per group slot (hint 30 000: 65 537 slots)
+
+
+@pytest.mark.parametrize("order", ["uniform", "ascending", "descending"])
+@pytest.mark.parametrize("key_dtype", [np.int32, np.int64])
+def test_groupby_split_pass(S, order, key_dtype):
+    """Inputs with many rows per direct slot take the split pass (the first 1/16 of the rows in
+    full, then the rest behind the extreme bounds of the groups seen): value orders that make
+    the bounds decisive or useless, int32 and int64 keys far from zero."""
+    rng = np.random.default_rng(40 + (key_dtype == np.int64))
+    keys = rng.integers(0, 30_000, size=SPLIT_N).astype(key_dtype)
+    if key_dtype == np.int64:
+        keys = keys + np.int64(10**15)
+    vals = {"uniform": rng.integers(-10**12, 10**12, size=SPLIT_N),
+            "ascending": np.arange(SPLIT_N, dtype=np.int64) * 7 - 10**8,
+            "descending": 10**8 - np.arange(SPLIT_N, dtype=np.int64) * 7}[order]
+    check_groupby(S, keys, vals, 30_000)
+
+
+def test_groupby_split_pass_late_keys_subsets_and_unaligned(S):
+    """Half the keys appear only after the split (no bound applies to them; values beyond the
+    first phase's extremes), each subset of MIN and MAX, and columns one element off (scalar
+    loads)."""
+    rng = np.random.default_rng(43)
+    n0 = ((SPLIT_N // 16) >> 2) << 2
+    keys = rng.integers(0, 30_000, size=SPLIT_N).astype(np.int32)
+    keys[:n0] = rng.integers(0, 15_000, size=n0)
+    vals = rng.integers(-10**9, 10**9, size=SPLIT_N)
+    vals[n0:n0 + 2000] = rng.choice([-3 * 10**9, 3 * 10**9], size=2000)
+    check_groupby(S, keys, vals, 30_000)
+    for aggs in ("min", "max", "min,max", "sum,count"):
+        check_groupby(S, keys, vals, 30_000, aggs)
+    keys1 = np.concatenate([[7], keys]).astype(np.int32)
+    vals1 = np.concatenate([[5], vals]).astype(np.int64)
+    got = S.sirius_groupby_agg(dev(keys1)[1:], dev(vals1)[1:], group_cap_hint=30_000)
+    got = O.sort_groups({k: v.cpu().numpy() for k, v in got.items()})
+    want = O.groupby_agg(keys, vals)
+    for c in COLS:
+        assert np.array_equal(got[c], want[c]), c
+
+
 def test_groupby_table_full_then_retry(S):
     keys = np.arange(10_000, dtype=np.int64)
     vals = np.ones(10_000, dtype=np.int64)
