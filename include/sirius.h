@@ -351,7 +351,8 @@ typedef struct {
                                of at most 2m values are joined through a direct-address array
                                (decided on the device during the build); 1 hash table always */
   int32_t split_probe;      /* queries with one-column keys asking for MIN or MAX, aggregated with
-                               agg_mode 2 or 4: 0 auto, 1 one probe pass, 2 split pass -- the
+                               agg_mode 2 or 4 (not star queries, whose probe keeps one pass):
+                               0 auto, 1 one probe pass, 2 split pass -- the
                                first 1/16 of the fact rows aggregate in full, then the smallest
                                MAX and the largest MIN over the groups seen so far (with a bitmap
                                of those among the first 2^17 group slots) let the other rows
