@@ -19,6 +19,7 @@ is bracketed by barriers and the max over ranks is taken.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -114,6 +115,25 @@ def measured_peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cudart():
+    """The CUDA runtime library (for plain copies that measure the host link), or None."""
+    import ctypes
+    import glob
+    cands = []
+    for d in ("/usr/local/cuda/lib64", "/usr/local/cuda/targets/sbsa-linux/lib", "/usr/local/cuda/targets/x86_64-linux/lib"):
+        cands += sorted(glob.glob(os.path.join(d, "libcudart.so*")))
+    for c in cands:
+        try:
+            lib = ctypes.CDLL(c)
+            lib.cudaMemcpyAsync.restype = ctypes.c_int
+            lib.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                            ctypes.c_void_p]
+            return lib
+        except OSError:
+            continue
+    return None
 
 
 def source_hash(paths):
@@ -958,21 +978,34 @@ def run_e2e(S, torch, spec, fact, dim, hint, aggs, args, dev, stream, world):
         sum(v.numel() * v.element_size() for v in hd.values())
     d2h = g * 8 * 5 + 256
     # the link's ceiling on this machine: plain copies of the same pinned columns to the device,
-    # one cudaMemcpyAsync per column on a stream of its own (all columns in flight together, as
-    # the library's staged copies are; one stream alone has measured well below the link on
-    # some boxes), timed with CUDA events from the launching stream
+    # each column in 16M-element pieces on a stream of its own (all columns in flight together,
+    # as the library's staged chunks are), by cudaMemcpyAsync from the CUDA runtime itself (torch's
+    # copy_ of pinned views has measured well below the link on some boxes), timed with CUDA events
+    # from the launching stream
     dst = {k: torch.empty_like(v, device=dev) for k, v in list(hf.items()) + [("d_" + k, v) for k, v in hd.items()]}
     src = dict(list(hf.items()) + [("d_" + k, v) for k, v in hd.items()])
     side = {k: torch.cuda.Stream(device=dev) for k in src}
     main = torch.cuda.current_stream(dev)
+    rt = cudart()
+    piece = 1 << 24
 
     def copy_all():
         start = torch.cuda.Event()
         start.record(main)
         for k, v in src.items():
             side[k].wait_event(start)
-            with torch.cuda.stream(side[k]):
-                dst[k].copy_(v, non_blocking=True)
+            es = v.element_size()
+            for i in range(0, v.numel(), piece):
+                m = min(piece, v.numel() - i)
+                if rt is not None:
+                    rc = rt.cudaMemcpyAsync(ctypes.c_void_p(dst[k].data_ptr() + i * es),
+                                            ctypes.c_void_p(v.data_ptr() + i * es), ctypes.c_size_t(m * es),
+                                            1, ctypes.c_void_p(side[k].cuda_stream))
+                    if rc != 0:
+                        raise RuntimeError(f"cudaMemcpyAsync failed: {rc}")
+                else:
+                    with torch.cuda.stream(side[k]):
+                        dst[k][i:i + m].copy_(v[i:i + m], non_blocking=True)
         for k in src:
             done = torch.cuda.Event()
             done.record(side[k])
