@@ -406,7 +406,11 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
       const bool vec = ((uintptr_t)d_keys & 15) == 0 && ((uintptr_t)d_vals & 15) == 0;
       auto kd = key_width == 4 ? (vec ? group_direct_kernel<4, true> : group_direct_kernel<4, false>)
                                : (vec ? group_direct_kernel<8, true> : group_direct_kernel<8, false>);
-      SIRIUS_CUDA_TRY(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHotSmemBytes));
+      {
+        static std::atomic<uint64_t> smem_set[4] = {};  // per kernel: devices with the limit raised
+        SIRIUS_CUDA_TRY(ensure_smem_limit(kd, (int)kHotSmemBytes,
+                                          smem_set[(key_width == 8 ? 2 : 0) + (vec ? 1 : 0)]));
+      }
       int64_t gd = ((n >> 2) + 511) / 512;
       const int64_t most = (int64_t)sm_count() * 3;  // three 64 KB caches per SM
       gd = gd < 1 ? 1 : (gd > most ? most : gd);
@@ -427,7 +431,8 @@ extern "C" sirius_status sirius_groupby_agg(const void* d_keys, int32_t key_widt
         auto kb = key_width == 4 ? (vec ? group_direct_kernel<4, true, true> : group_direct_kernel<4, false, true>)
                                  : (vec ? group_direct_kernel<8, true, true> : group_direct_kernel<8, false, true>);
         const size_t smem = kHotSmemBytes + kBoundsSmemBytes;
-        SIRIUS_CUDA_TRY(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        static std::atomic<uint64_t> smem_set_b[4] = {};
+        SIRIUS_CUDA_TRY(ensure_smem_limit(kb, (int)smem, smem_set_b[(key_width == 8 ? 2 : 0) + (vec ? 1 : 0)]));
         const int64_t most2 = (int64_t)sm_count() * 2;
         const int64_t gd2 = gd > most2 ? most2 : gd;
         kb<<<(unsigned)gd2, 512, smem, s>>>(static_cast<const char*>(d_keys) + n0 * kw, d_vals + n0, n - n0, aggs,
