@@ -5,10 +5,12 @@
                                                   [--load-factor LF] [--runs R]
     python -m paper_2508_04701_gb300.profile_case --workload plain_1M --variant single
     python -m paper_2508_04701_gb300.profile_case --op sort --n ROWS --m DISTINCT_KEYS
+    python -m paper_2508_04701_gb300.profile_case --op groupby --n ROWS --m DISTINCT_KEYS
     python -m paper_2508_04701_gb300.profile_case --op strings --n ROWS --m DISTINCT_STRINGS
     python -m paper_2508_04701_gb300.profile_case --op operators [--n ROWS] [--m DIM_ROWS]
 
---op sort runs the sort-based group-by on int32 keys U[0, m) with int64 values; --op strings
+--op sort runs the sort-based group-by on int32 keys U[0, m) with int64 values; --op groupby the
+hash group-by (SUM, COUNT, MIN, MAX) on the same inputs; --op strings
 dictionary-encodes a seeded string column of n rows over m distinct strings; --op operators
 runs the query's unfused C-ABI operators on the 600M-row query's distributions at n rows:
 filter (pred < 30), join build over the dim keys, probe of the selected rows, gathers of their
@@ -37,12 +39,24 @@ def main():
     p.add_argument("--join-mode", default="auto", choices=["auto", "hash"])
     p.add_argument("--agg-mode", default="auto", choices=["auto", "smem", "global", "part", "hot", "routed"])
     p.add_argument("--batch", type=int, default=0, help="run a batch of this many queries instead")
-    p.add_argument("--op", default="pipeline", choices=["pipeline", "sort", "strings", "operators"])
+    p.add_argument("--op", default="pipeline", choices=["pipeline", "sort", "groupby", "strings", "operators"])
     a = p.parse_args()
     import torch
 
     from paper_2508_04701_gb300 import datagen as dg
     from paper_2508_04701_gb300 import sirius as S
+    if a.op == "groupby":
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(1)
+        vals = torch.randint(0, 10**8, (a.n,), dtype=torch.int64, device="cuda", generator=gen)
+        keys = torch.randint(0, a.m, (a.n,), dtype=torch.int32, device="cuda", generator=gen)
+        outs = S.groupby_outputs(S.lib().sirius_groupby_capacity(a.m) + 1, "cuda")
+        scr = torch.empty(S.lib().sirius_groupby_scratch_bytes(a.m), dtype=torch.uint8, device="cuda")
+        for _ in range(a.runs):
+            S.sirius_groupby_agg(keys, vals, "sum,count,min,max", a.m, outputs=outs, scratch=scr, sync=False)
+        torch.cuda.synchronize()
+        print(f"profile case ok: hash group-by of {a.n} rows, {int(outs['groups'].item())} groups")
+        return
     if a.op == "sort":
         gen = torch.Generator(device="cuda")
         gen.manual_seed(1)
