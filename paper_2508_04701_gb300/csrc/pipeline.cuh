@@ -711,7 +711,7 @@ __device__ __forceinline__ void probe_quad(const ProbeArgs& a, const SmemAggs& T
 // array): every column read of both, then every direct-array read of both, in flight together
 // before any aggregate update -- twice the memory parallelism of probe_quad for kernels with
 // registers to spare (the single-launch kernel runs one block per SM).
-template <int kMode, bool kFresh = false>
+template <int kMode, bool kFresh = false, bool kBounded = false>
 __device__ __forceinline__ void probe_quad_pair_direct(const ProbeArgs& a, const SmemAggs& T, const Lookup& L,
                                                        int64_t qa, int64_t qb) {
   const int4 pa = __ldcs(reinterpret_cast<const int4*>(a.pred) + qa);
@@ -739,10 +739,10 @@ __device__ __forceinline__ void probe_quad_pair_direct(const ProbeArgs& a, const
   }
 #pragma unroll
   for (int r = 0; r < 4; ++r)
-    if (ga[r] != kEmpty32) aggregate<kMode>(a, T, ga[r], va[r]);
+    if (ga[r] != kEmpty32) aggregate<kMode, false, kBounded>(a, T, ga[r], va[r]);
 #pragma unroll
   for (int r = 0; r < 4; ++r)
-    if (gb[r] != kEmpty32) aggregate<kMode>(a, T, gb[r], vb[r]);
+    if (gb[r] != kEmpty32) aggregate<kMode, false, kBounded>(a, T, gb[r], vb[r]);
 }
 
 // Filter, probe and aggregate one single row r (< n): the ragged tail after the quads.
