@@ -192,8 +192,11 @@ sirius_status sirius_gather_group_key(const int32_t* d_grp, const int8_t* d_flag
  * slots), a key's slot is its offset from the smallest key (no hashing; only those slots are
  * cleared and scanned), else keys are hashed.  Small tables are pre-aggregated per thread block
  * in shared memory; large ones aggregate with global atomics, behind a per-block cache of hot
- * groups (direct slots) or after a warp-level combine of equal keys (hashed keys).  The table
- * holds sirius_groupby_capacity(hint)
+ * groups (direct slots) or after a warp-level combine of equal keys (hashed keys).  With direct
+ * slots, MIN or MAX asked for, at least 2^24 rows and at least 256 rows per table slot, the
+ * pass is split: the first 1/16 of the rows aggregate in full, then the smallest MAX and the
+ * largest MIN over the groups seen (and which groups those were) let the other rows skip the
+ * MIN / MAX updates they cannot change (exact).  The table holds sirius_groupby_capacity(hint)
  * slots; more distinct keys than it can take -> TABLE_FULL (retry with a larger hint).
  * Outputs (device, out_cap each, NULL for aggregates not requested): keys, sums, counts, mins,
  * maxs, in unspecified order; the group count G goes to *d_groups / *h_groups
