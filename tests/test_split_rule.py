@@ -72,8 +72,8 @@ def test_rule_is_exact_at_int64_edges_and_for_late_groups():
     keys = rng.integers(0, 30, size=n)
     keys[:n0] = rng.integers(0, 15, size=n0)          # groups 15..29 first appear after the split
     vals = rng.integers(-1000, 1000, size=n)
-    vals[n0:n0 + 40] = np.iinfo(np.int64).min // 4     # below every floor, above no ceiling
-    vals[n0 + 40:n0 + 80] = np.iinfo(np.int64).max // 4
+    vals[n0:n0 + 40] = np.iinfo(np.int64).min // 64    # below every floor (sums stay in int64)
+    vals[n0 + 40:n0 + 80] = np.iinfo(np.int64).max // 64
     check(keys, vals, n0)
 
 
