@@ -141,7 +141,6 @@ struct SemiView {
   int key_width;
 };
 
-// Everything the probe pass reads for one query.
 // Extreme bounds for the second phase of a split probe pass (taken after the first phase over
 // the group table): every slot whose bit is set had joined rows, its MAX at least max_floor and
 // its MIN at most min_ceil -- and both only move outwards, so a later row of such a slot whose
@@ -165,6 +164,7 @@ __host__ __device__ __forceinline__ long long bound_decode(unsigned long long e)
 // The decoded bounds of the running block (set at the start of a second-phase launch).
 __shared__ long long s_bound_floor, s_bound_ceil;
 
+// Everything the probe pass reads for one query.
 struct ProbeArgs {
   const int32_t* fk;
   const int32_t* fk_hi;
@@ -343,12 +343,12 @@ __device__ __forceinline__ void agg_update_global_bounded(const ProbeArgs& a, ui
   agg_update_global(&a.tab[gs], v, aggs);
 }
 
-// The extreme bounds after the first phase of a split pass (the fused probe, the group-by): one thread per group slot
-// below kBoundSlots (a bit per slot that has joined rows, by ballot), the smallest MAX and the
-// largest MIN over those slots by block reductions and one atomicMin per block on their
-// encodings (set to all-ones before the launch).
-static __global__ void __launch_bounds__(256) extreme_bounds_kernel(const Agg* __restrict__ tab, uint32_t gslots,
-                                                           ExtremeBounds* b) {
+// The extreme bounds after the first phase of a split pass (the fused probe, the group-by): one
+// thread per group slot below kBoundSlots (a bit per slot that has joined rows, by ballot), the
+// smallest MAX and the largest MIN over those slots by block reductions and one atomicMin per
+// block on their encodings (set to all-ones before the launch).
+static __global__ void __launch_bounds__(256)
+extreme_bounds_kernel(const Agg* __restrict__ tab, uint32_t gslots, ExtremeBounds* b) {
   __shared__ unsigned long long s_floor, s_ceil;  // encoded MAX floor, complemented MIN ceiling
   if (threadIdx.x == 0) {
     s_floor = ~0ull;
